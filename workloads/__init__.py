@@ -1,0 +1,231 @@
+"""Seeded synthetic inputs for the support-graph PCG path.
+
+This module is shared by the CPU oracle (``oracle/``), the tests and the
+benchmark.  It draws positions, radii, forces and per-contact friction
+coefficients and holds none of the method's arithmetic: no contact test, no
+friction block, no spanning tree, no factorisation and no solve.
+
+Input laws (the paper's cell model, Section 2 Steps 1-4 and eq. (1)):
+
+* ``cube``   N cells, centres uniform in a cube of side L, radii U[0.45, 0.55].
+* ``ball``   N cells, centres uniform in a ball (a spheroid of cells at a
+             given packing fraction), radii U[0.45, 0.55].
+* ``hex_sheet``  a monolayer: centres on a jittered hexagonal lattice in the
+             z = 0 plane (jitter U[-j, j] on all three coordinates).
+* ``batch``  many independent balls of log-uniform size.
+
+Per-contact friction coefficients gamma_par and gamma_perp (eq. (1)) are
+drawn log-uniformly per unordered pair {i, j} by a counter-based generator:
+SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) applied to a key built from (seed, i, j, stream).
+The top 16 bits of the hash select one of 65536 equally spaced levels of
+log(gamma); the level table is computed once on the host and handed to both
+sides, so the coefficient of a pair is bit-identical on the CPU and on the
+GPU.  ``pair_gamma_np`` (numpy, uint64) and ``pair_gamma_torch`` (torch,
+int64 with wrap-around) implement the same integer arithmetic.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# SplitMix64 (published constants of the SplitMix64 finaliser)
+# ---------------------------------------------------------------------------
+_SM_INC = 0x9E3779B97F4A7C15
+_SM_M1 = 0xBF58476D1CE4E5B9
+_SM_M2 = 0x94D049BB133111EB
+_MASK64 = (1 << 64) - 1
+GAMMA_LEVELS_LOG2 = 16
+GAMMA_LEVELS = 1 << GAMMA_LEVELS_LOG2
+
+
+def splitmix64_np(x: np.ndarray) -> np.ndarray:
+    """One SplitMix64 step on a uint64 array (wrap-around arithmetic)."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(_SM_INC)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_SM_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_SM_M2)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def _s64(c: int) -> int:
+    """Reinterpret an unsigned 64-bit constant as a signed int64."""
+    c &= _MASK64
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _lsr_torch(z, k: int):
+    """Logical right shift of an int64 tensor (torch's >> is arithmetic)."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def splitmix64_torch(z):
+    """Same SplitMix64 step on an int64 torch tensor (two's-complement wrap)."""
+    z = z + _s64(_SM_INC)
+    z = (z ^ _lsr_torch(z, 30)) * _s64(_SM_M1)
+    z = (z ^ _lsr_torch(z, 27)) * _s64(_SM_M2)
+    return z ^ _lsr_torch(z, 31)
+
+
+def _stream_key(seed: int, stream: int) -> int:
+    """Per-(seed, stream) 64-bit salt, computed with Python integers."""
+    x = (int(seed) * 2 + int(stream)) & _MASK64
+    return int(splitmix64_np(np.array([x], dtype=np.uint64))[0])
+
+
+def gamma_table(lo: float, hi: float) -> np.ndarray:
+    """Level table of a log-uniform law on [lo, hi]: level k sits at the
+    midpoint of the k-th of GAMMA_LEVELS equal bins of log(gamma)."""
+    k = np.arange(GAMMA_LEVELS, dtype=np.float64)
+    return lo * np.exp((k + 0.5) / GAMMA_LEVELS * math.log(hi / lo))
+
+
+def pair_gamma_np(seed: int, i: np.ndarray, j: np.ndarray, table_par: np.ndarray,
+                  table_perp: np.ndarray):
+    """(gamma_par, gamma_perp) for pairs (i, j); symmetric in i and j."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    a = np.minimum(i, j).astype(np.uint64)
+    b = np.maximum(i, j).astype(np.uint64)
+    key = (a << np.uint64(32)) | b
+    out = []
+    for s, tab in ((0, table_par), (1, table_perp)):
+        h = splitmix64_np(key ^ np.uint64(_stream_key(seed, s)))
+        lvl = (h >> np.uint64(64 - GAMMA_LEVELS_LOG2)).astype(np.int64)
+        out.append(tab[lvl])
+    return out[0], out[1]
+
+
+def pair_gamma_torch(seed: int, ij, table_par, table_perp):
+    """Torch twin of ``pair_gamma_np`` for an (m, 2) int32/int64 tensor of
+    pairs; the tables are float64 tensors on the same device as ``ij``."""
+    import torch
+    ij = ij.to(torch.int64)
+    a = torch.minimum(ij[:, 0], ij[:, 1])
+    b = torch.maximum(ij[:, 0], ij[:, 1])
+    key = (a << 32) | b
+    out = []
+    for s, tab in ((0, table_par), (1, table_perp)):
+        h = splitmix64_torch(key ^ _s64(_stream_key(seed, s)))
+        lvl = _lsr_torch(h, 64 - GAMMA_LEVELS_LOG2)
+        out.append(tab[lvl])
+    return out[0], out[1]
+
+
+# ---------------------------------------------------------------------------
+# Cell configurations
+# ---------------------------------------------------------------------------
+@dataclass
+class Cells:
+    """A synthetic cell configuration and the laws of its per-pair data."""
+    name: str
+    pos: np.ndarray              # (N, 3) float64, C-contiguous
+    radii: np.ndarray            # (N,) float64
+    seed: int
+    gamma_lo: float
+    gamma_hi: float
+    gamma0: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+    def tables(self):
+        t = gamma_table(self.gamma_lo, self.gamma_hi)
+        return t, t.copy()
+
+    def gammas_np(self, ij: np.ndarray):
+        tp, tq = self.tables()
+        return pair_gamma_np(self.seed, ij[:, 0], ij[:, 1], tp, tq)
+
+    def forces(self, k: int = 0) -> np.ndarray:
+        """F ~ N(0, 1) per component; ``k`` selects an independent draw."""
+        rng = np.random.Generator(np.random.PCG64([self.seed, 7919, k]))
+        return np.ascontiguousarray(rng.standard_normal((self.n, 3)))
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([seed, stream]))
+
+
+def cube(n: int = 1000, side: float = 8.886, seed: int = 1000,
+         r_lo: float = 0.45, r_hi: float = 0.55, gamma_lo: float = 0.1,
+         gamma_hi: float = 10.0, gamma0: float = 1e-2) -> Cells:
+    """Centres uniform in [0, side]^3.  side = 8.886 at N = 1000 gives a
+    number density of 1.4253, i.e. a mean contact degree near 6 before
+    boundary losses."""
+    g = _rng(seed, 1)
+    pos = np.ascontiguousarray(g.uniform(0.0, side, size=(n, 3)))
+    radii = g.uniform(r_lo, r_hi, size=n)
+    return Cells("cube", pos, radii, seed, gamma_lo, gamma_hi, gamma0,
+                 {"side": side})
+
+
+def ball_radius(n: int, packing: float = 0.6, mean_r3: float = 0.12625) -> float:
+    """Ball radius that holds n cells at volume fraction ``packing``;
+    mean_r3 = E[R^3] of the radius law (0.12625 for U[0.45, 0.55])."""
+    return (n * mean_r3 / packing) ** (1.0 / 3.0)
+
+
+def ball(n: int = 1_000_000, seed: int = 2000, radius: float | None = None,
+         packing: float = 0.6, r_lo: float = 0.45, r_hi: float = 0.55,
+         gamma_lo: float = 0.1, gamma_hi: float = 10.0,
+         gamma0: float = 1e-3) -> Cells:
+    """Centres uniform (Poisson) in a ball; the default radius gives the
+    requested packing fraction for the radius law."""
+    if radius is None:
+        radius = ball_radius(n, packing)
+    g = _rng(seed, 2)
+    d = g.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = radius * np.cbrt(g.uniform(0.0, 1.0, size=n))
+    pos = np.ascontiguousarray(d * r[:, None])
+    radii = g.uniform(r_lo, r_hi, size=n)
+    return Cells("ball", pos, radii, seed, gamma_lo, gamma_hi, gamma0,
+                 {"radius": radius})
+
+
+def hex_sheet(nx: int = 2000, ny: int = 2000, spacing: float = 0.9,
+              jitter: float = 0.05, seed: int = 3000, r_lo: float = 0.48,
+              r_hi: float = 0.52, gamma_lo: float = 0.01,
+              gamma_hi: float = 100.0, gamma0: float = 1e-4) -> Cells:
+    """A monolayer: a rhombic nx-by-ny patch of the hexagonal lattice with
+    spacing ``spacing`` in the z = 0 plane, every coordinate jittered by
+    U[-jitter, jitter]."""
+    g = _rng(seed, 3)
+    p, q = np.meshgrid(np.arange(nx, dtype=np.float64),
+                       np.arange(ny, dtype=np.float64), indexing="xy")
+    x = spacing * (p + 0.5 * q)
+    y = spacing * (math.sqrt(3.0) / 2.0) * q
+    pos = np.stack([x.ravel(), y.ravel(), np.zeros(nx * ny)], axis=1)
+    pos = np.ascontiguousarray(pos + g.uniform(-jitter, jitter, size=pos.shape))
+    radii = g.uniform(r_lo, r_hi, size=nx * ny)
+    return Cells("hex_sheet", pos, radii, seed, gamma_lo, gamma_hi, gamma0,
+                 {"nx": nx, "ny": ny, "spacing": spacing})
+
+
+def batch_sizes(count: int = 512, lo: float = 1e3, hi: float = 1e5,
+                seed: int = 4000) -> np.ndarray:
+    """Instance sizes log-uniform in [lo, hi]."""
+    g = _rng(seed, 4)
+    return np.floor(np.exp(g.uniform(math.log(lo), math.log(hi), size=count))).astype(np.int64)
+
+
+def batch_instance(n: int, s: int, density: float = 1.4253, seed0: int = 4000,
+                   gamma0: float = 1e-2) -> Cells:
+    """Instance s of the batch: a ball at the cube workload's number density."""
+    radius = (3.0 * n / (4.0 * math.pi * density)) ** (1.0 / 3.0)
+    return ball(n, seed=seed0 + s, radius=radius, gamma0=gamma0)
+
+
+def sphere_offsets(sizes: np.ndarray) -> np.ndarray:
+    """Exclusive prefix sums of instance sizes (length count + 1)."""
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    return off
