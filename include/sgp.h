@@ -1,0 +1,205 @@
+/*
+ * sgp.h -- C ABI of the GB300 support-graph preconditioned CG library.
+ *
+ * Solves the overdamped equation of motion of an off-lattice cell model,
+ * Gamma v = F (arXiv 2410.04512, Section 2, eq. (2)), by conjugate gradients
+ * preconditioned with the block Laplacian of a maximum spanning forest of the
+ * collision graph (Section 3.1).  Every step runs in CUDA kernels built for
+ * sm_103a.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named *_dev are DEVICE pointers on the context's device; the
+ *   caller owns them, keeps them alive for the duration of the call and the
+ *   library never frees or retains them.  Vectors of cells are n x 3 float64
+ *   arrays, row-major and contiguous (cell i at [3i, 3i+3)).
+ * - Handles (sgp_graph, sgp_matrix, sgp_tree, sgp_factor) are opaque and own
+ *   their device memory.  A call that produces a handle takes a pointer to a
+ *   handle variable: if it holds NULL a new handle is created; if it holds a
+ *   handle produced earlier by the same call kind, that handle's memory is
+ *   reused (grown when needed).  Free handles with the matching *_destroy.
+ * - All work is ordered on the context's CUDA stream.  Calls that return host
+ *   values (sizes, solve statistics) synchronise that stream.
+ * - Every call returns an sgp_status; on failure sgp_last_error(ctx) holds a
+ *   one-line reason.  No call aborts the process.
+ */
+#ifndef SGP_H
+#define SGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SGP_OK = 0,
+    SGP_ERR_INVALID_ARG = 1,    /* bad size, NULL pointer, non-positive or non-finite input */
+    SGP_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    SGP_ERR_OOM = 3,            /* device allocation failed */
+    SGP_ERR_DEGENERATE = 4,     /* two cells in contact share a centre: u of eq. (1) undefined */
+    SGP_ERR_NOT_SPD = 5,        /* a pivot block or p^T Gamma p was not positive */
+    SGP_ERR_NO_CONVERGENCE = 6, /* maxit reached; v holds the last iterate */
+    SGP_ERR_TIMEOUT = 7         /* a bounded device wait gave up */
+} sgp_status;
+
+typedef enum {
+    SGP_PREC_F64 = 0,   /* everything in FP64 */
+    SGP_PREC_MIXED = 1  /* FP32 blocks and inner PCG inside FP64 iterative refinement */
+} sgp_precision;
+
+typedef enum {
+    SGP_PRECOND_TREE = 0,          /* spanning-forest preconditioner (Section 3.1) */
+    SGP_PRECOND_BLOCK_JACOBI = 1,  /* inverses of Gamma's 3x3 diagonal blocks (Section 5) */
+    SGP_PRECOND_NONE = 2           /* plain CG */
+} sgp_precond;
+
+typedef struct sgp_ctx sgp_ctx;
+typedef struct sgp_graph sgp_graph;
+typedef struct sgp_matrix sgp_matrix;
+typedef struct sgp_tree sgp_tree;
+typedef struct sgp_factor sgp_factor;
+
+typedef struct {
+    double tol;          /* stop when |F - Gamma v|_2 <= tol |F|_2 (recursive residual) */
+    int64_t maxit;       /* iteration cap (inner iterations in total for MIXED) */
+    int32_t precond;     /* sgp_precond */
+    int32_t precision;   /* sgp_precision; MIXED needs a matrix assembled with MIXED */
+    int32_t x0_given;    /* 0: start from v = 0; 1: v holds the initial guess on entry */
+    int32_t max_outer;   /* MIXED: refinement steps cap (<= 0 means 30) */
+    double inner_tol;    /* MIXED: relative residual target of each FP32 inner solve (<= 0: 1e-4) */
+} sgp_solve_opts;
+
+typedef struct {
+    int64_t iterations;        /* PCG iterations (FP32 inner iterations summed for MIXED) */
+    int32_t outer_iterations;  /* MIXED refinement steps; 0 otherwise */
+    int32_t status;            /* sgp_status of the solve */
+    double rel_residual;       /* final recursive |r|/|F| (FP64 outer residual for MIXED) */
+    double true_rel_residual;  /* |F - Gamma v|/|F| recomputed in FP64 at exit */
+} sgp_solve_info;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` whose work is ordered on `stream`
+ * (a cudaStream_t; NULL means the legacy default stream). */
+sgp_status sgp_create(sgp_ctx **ctx, int device, void *stream);
+void sgp_destroy(sgp_ctx *ctx);
+/* Reason for the last failure on this context ("" if none); owned by ctx. */
+const char *sgp_last_error(const sgp_ctx *ctx);
+/* Library version string, e.g. "sgp 0.1 sm_103a". */
+const char *sgp_version(void);
+/* Stream-ordered copy of `bytes` between two device buffers (for reading
+ * arrays owned by handles, e.g. the edge list, into caller memory). */
+sgp_status sgp_copy(sgp_ctx *ctx, void *dst_dev, const void *src_dev, int64_t bytes);
+
+/* ---- Section 2, Steps 1-2: collision graph --------------------------------
+ * Cells i < j are in contact iff |r_j - r_i| < R_i + R_j, evaluated in FP64
+ * as sqrt((dx*dx + dy*dy) + dz*dz) with dx = x_j - x_i, round-to-nearest and
+ * no fused multiply-add (Section 1.1: an edge wherever the contact area is
+ * nonzero).  The edge list is canonical: pairs (i, j) with i < j, sorted by i
+ * then j, so the result is independent of how the search is scheduled.
+ * pos_dev: n x 3 float64; radii_dev: n float64, each > 0 and finite.
+ * INVALID_ARG for n < 0, NULL pointers with n > 0, non-finite input or a
+ * non-positive radius.  Synchronises (to size the edge list). */
+sgp_status sgp_collision_graph(sgp_ctx *ctx, int64_t n, const double *pos_dev,
+                               const double *radii_dev, sgp_graph **graph);
+/* n, m and the device edge list (m x 2 int32, owned by the graph). */
+sgp_status sgp_graph_info(const sgp_graph *graph, int64_t *n, int64_t *m,
+                          const int32_t **ij_dev);
+void sgp_graph_destroy(sgp_graph *graph);
+
+/* ---- Section 2, Step 3, eq. (1): friction blocks --------------------------
+ * Upsilon_e = g_par u u^T + g_perp (I - u u^T), u = (r_j - r_i)/|r_j - r_i|,
+ * for every edge e = (i, j) of the graph, in edge order; gamma_par_dev and
+ * gamma_perp_dev hold m positive coefficients each (the contact area A_ij of
+ * eq. (1) folded in).  Gamma is the block Laplacian of the collision graph
+ * with self-loops gamma0 I (Section 2, Definition "Block Laplacian"):
+ *   Gamma_ij = -Upsilon_e,  Gamma_ii = gamma0 I + sum_j Upsilon_ij.
+ * The matrix keeps the blocks per directed edge (block-sparse rows, both
+ * directions) in FP64, plus FP32 copies when precision is MIXED, and the
+ * spanning-tree weight of Section 3.1, min(g_par, g_perp) = lambda_min
+ * (Lemma 2.1).  gamma0 > 0.  DEGENERATE if two cells in contact coincide.
+ * pos_dev must be the positions the graph was built from. */
+sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *graph, const double *pos_dev,
+                                 const double *gamma_par_dev, const double *gamma_perp_dev,
+                                 double gamma0, int32_t precision, sgp_matrix **matrix);
+/* Appendix B.2 matrix-free product y = Gamma v in FP64:
+ *   y_i = gamma0 v_i + sum_{j ~ i} Upsilon_ij (v_i - v_j).
+ * v_dev, y_dev: n x 3 float64, distinct buffers. */
+sgp_status sgp_spmv(sgp_ctx *ctx, const sgp_matrix *matrix, const double *v_dev, double *y_dev);
+/* Copy the FP64 block of edge e (row-major 3x3) for every edge into
+ * blocks_dev (m x 9 float64) and the tree weights into w_dev (m float64);
+ * either pointer may be NULL. */
+sgp_status sgp_matrix_edge_blocks(sgp_ctx *ctx, const sgp_matrix *matrix, double *blocks_dev,
+                                  double *w_dev);
+void sgp_matrix_destroy(sgp_matrix *matrix);
+
+/* ---- Section 3.1: maximum spanning forest ----------------------------------
+ * Boruvka's algorithm on the weights min(g_par, g_perp) under the strict
+ * order (weight descending, then edge index ascending); under that order the
+ * maximum spanning forest is unique.  A disconnected graph gives a forest
+ * (one tree per connected component; isolated cells are single-vertex trees).
+ * Synchronises (the round count is data dependent). */
+sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *matrix, sgp_tree **tree);
+/* Number of tree edges (n - components), the number of components and the
+ * tree's edge ids (ascending, device int32 array owned by the tree). */
+sgp_status sgp_tree_info(const sgp_tree *tree, int64_t *n_edges, int64_t *n_components,
+                         const int32_t **edge_ids_dev);
+void sgp_tree_destroy(sgp_tree *tree);
+
+/* ---- Section 3.3 (Algorithm 2) and Appendix B.1: tree factor ----------------
+ * P = gamma0 I + block Laplacian of the spanning forest (the self-loops kept,
+ * Section 3.1) is factored P = L D L^T by block elimination.  The elimination
+ * order comes from rake/compress tree contraction: each round eliminates every
+ * leaf, then an independent set of degree-2 vertices, so any tree takes
+ * O(log n) rounds.  Pivots D and their inverses are computed in FP64; MIXED
+ * matrices also get FP32 copies of L and D^-1 for the inner solves.
+ * NOT_SPD if a pivot is not positive definite.  Synchronises (the round count
+ * is data dependent). */
+sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_tree *tree,
+                           sgp_factor **factor);
+/* x = P^{-1} b in FP64 (forward substitution, diagonal solve, backward
+ * substitution, Appendix B.1).  b_dev, x_dev: n x 3 float64; may alias. */
+sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *factor, const double *b_dev,
+                          double *x_dev);
+/* Contraction rounds and elimination levels (two per round) of the factor. */
+sgp_status sgp_factor_info(const sgp_factor *factor, int32_t *rounds, int32_t *levels);
+void sgp_factor_destroy(sgp_factor *factor);
+
+/* ---- Section 1.1: preconditioned conjugate gradients ------------------------
+ * Solves Gamma v = F.  r = F - Gamma v0, z = H r, p = z, rho = r^T z; each
+ * iteration: q = Gamma p, alpha = rho / p^T q, v += alpha p, r -= alpha q,
+ * stop when |r|_2 <= tol |F|_2, z = H r, beta = r^T z / rho, p = z + beta p.
+ * H is P^{-1} from `factor` (required for SGP_PRECOND_TREE), the block-Jacobi
+ * inverse (computed inside the call) or I.  MIXED runs FP64 iterative
+ * refinement: r = F - Gamma v in FP64, an FP32 inner PCG on r/|r| to
+ * inner_tol (FP64 dot products), v += |r| d, until |r| <= tol |F|.
+ * F_dev, v_dev: n x 3 float64.  A zero F returns v = 0 after 0 iterations.
+ * On NO_CONVERGENCE v holds the last iterate and info is filled.
+ * info (host, may be NULL) receives the statistics.  Synchronises. */
+sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_factor *factor,
+                         const double *F_dev, double *v_dev, const sgp_solve_opts *opts,
+                         sgp_solve_info *info);
+
+/* ---- kernel timing ----------------------------------------------------------
+ * When enabled, the library brackets every launch of the named kernel class
+ * with CUDA events on the context stream and accumulates the elapsed time,
+ * read back at the next synchronising call.  For roofline reporting. */
+typedef enum {
+    SGP_KT_SPMV = 0,       /* Gamma p products inside PCG (FP64 or FP32) */
+    SGP_KT_TREE_SOLVE = 1, /* one whole P^{-1} r application */
+    SGP_KT_PCG_VECTOR = 2, /* PCG vector updates and reductions */
+    SGP_KT_COUNT = 3
+} sgp_kernel_class;
+sgp_status sgp_set_kernel_timing(sgp_ctx *ctx, int32_t enable);
+/* Total milliseconds and launch count since the last reset. */
+sgp_status sgp_kernel_time(sgp_ctx *ctx, int32_t kernel_class, double *total_ms,
+                           int64_t *launches, int32_t reset);
+/* Number of kernels this context has launched (every kernel of every call,
+ * counted on the host at launch); reset to 0 when `reset` is nonzero. */
+sgp_status sgp_launch_count(sgp_ctx *ctx, int64_t *count, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGP_H */

@@ -1,0 +1,301 @@
+"""Python binding of libsgp.so, the sm_103a support-graph PCG library.
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  Device memory comes from torch tensors (contiguous, on the
+context's device); work is ordered on the torch stream given at context
+creation.  Names follow the C ABI in include/sgp.h.
+
+There is no CPU fallback: if libsgp.so is missing or a CUDA device is not
+available, creating a context raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgp.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_TIMEOUT = range(8)
+PREC_F64, PREC_MIXED = 0, 1
+PRECOND_TREE, PRECOND_BLOCK_JACOBI, PRECOND_NONE = 0, 1, 2
+KT_SPMV, KT_TREE_SOLVE, KT_PCG_VECTOR = 0, 1, 2
+
+_STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "DEGENERATE", 5: "NOT_SPD",
+                 6: "NO_CONVERGENCE", 7: "TIMEOUT"}
+
+
+class SgpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sgp error {_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int64), ("precond", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("x0_given", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("outer_iterations", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsgp.so (building it first if it is absent and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "sgp_create": ([PP, ctypes.c_int, P], I32),
+        "sgp_destroy": ([P], None),
+        "sgp_last_error": ([P], ctypes.c_char_p),
+        "sgp_version": ([], ctypes.c_char_p),
+        "sgp_copy": ([P, P, P, I64], I32),
+        "sgp_collision_graph": ([P, I64, P, P, PP], I32),
+        "sgp_graph_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64), PP], I32),
+        "sgp_graph_destroy": ([P], None),
+        "sgp_friction_assemble": ([P, P, P, P, P, D, I32, PP], I32),
+        "sgp_spmv": ([P, P, P, P], I32),
+        "sgp_matrix_edge_blocks": ([P, P, P, P], I32),
+        "sgp_matrix_destroy": ([P], None),
+        "sgp_max_spanning_tree": ([P, P, PP], I32),
+        "sgp_tree_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64), PP], I32),
+        "sgp_tree_destroy": ([P], None),
+        "sgp_tree_factor": ([P, P, P, PP], I32),
+        "sgp_tree_apply": ([P, P, P, P], I32),
+        "sgp_factor_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], I32),
+        "sgp_factor_destroy": ([P], None),
+        "sgp_pcg_solve": ([P, P, P, P, P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)], I32),
+        "sgp_set_kernel_timing": ([P, I32], I32),
+        "sgp_kernel_time": ([P, I32, ctypes.POINTER(D), ctypes.POINTER(I64), I32], I32),
+        "sgp_launch_count": ([P, ctypes.POINTER(I64), I32], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C ABI entry points this binding expects."""
+    import re
+    with open(os.path.join(os.path.dirname(_HERE), "include", "sgp.h")) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:sgp_status|void|const char \*)\s*\*?(sgp_\w+)\s*\(", txt, re.M)))
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_vec(t: torch.Tensor, n: int, dtype=torch.float64, cols: int = 3, name: str = "tensor"):
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    want = (n, cols) if cols else (n,)
+    if tuple(t.shape) != want:
+        raise ValueError(f"{name} must have shape {want}, got {tuple(t.shape)}")
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ctx: "Context"):
+        self.ctx = ctx
+        self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        if self.ptr and self.ptr.value and self._destroy and _lib is not None:
+            getattr(_lib, self._destroy)(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+
+class Graph(_Handle):
+    _destroy = "sgp_graph_destroy"
+
+    def info(self):
+        n, m, ij = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_void_p()
+        self.ctx._ok(_lib.sgp_graph_info(self.ptr, ctypes.byref(n), ctypes.byref(m), ctypes.byref(ij)))
+        return n.value, m.value, ij.value
+
+    @property
+    def n(self):
+        return self.info()[0]
+
+    @property
+    def m(self):
+        return self.info()[1]
+
+    def edges(self) -> torch.Tensor:
+        n, m, ij = self.info()
+        out = torch.empty((m, 2), dtype=torch.int32, device=self.ctx.device)
+        if m:
+            self.ctx._ok(_lib.sgp_copy(self.ctx.ptr, _ptr(out), ctypes.c_void_p(ij), 8 * m))
+        return out
+
+
+class Matrix(_Handle):
+    _destroy = "sgp_matrix_destroy"
+
+    def __init__(self, ctx, n, m, precision):
+        super().__init__(ctx)
+        self.n, self.m, self.precision = n, m, precision
+
+    def edge_blocks(self):
+        blocks = torch.empty((self.m, 3, 3), dtype=torch.float64, device=self.ctx.device)
+        w = torch.empty((self.m,), dtype=torch.float64, device=self.ctx.device)
+        self.ctx._ok(_lib.sgp_matrix_edge_blocks(self.ctx.ptr, self.ptr, _ptr(blocks), _ptr(w)))
+        return blocks, w
+
+
+class Tree(_Handle):
+    _destroy = "sgp_tree_destroy"
+
+    def info(self):
+        ne, nc, ids = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_void_p()
+        self.ctx._ok(_lib.sgp_tree_info(self.ptr, ctypes.byref(ne), ctypes.byref(nc), ctypes.byref(ids)))
+        return ne.value, nc.value, ids.value
+
+    def edge_ids(self) -> torch.Tensor:
+        ne, nc, ids = self.info()
+        out = torch.empty((ne,), dtype=torch.int32, device=self.ctx.device)
+        if ne:
+            self.ctx._ok(_lib.sgp_copy(self.ctx.ptr, _ptr(out), ctypes.c_void_p(ids), 4 * ne))
+        return out
+
+
+class Factor(_Handle):
+    _destroy = "sgp_factor_destroy"
+
+    def info(self):
+        r, l = ctypes.c_int32(), ctypes.c_int32()
+        self.ctx._ok(_lib.sgp_factor_info(self.ptr, ctypes.byref(r), ctypes.byref(l)))
+        return r.value, l.value
+
+
+@dataclass
+class Info:
+    iterations: int
+    outer_iterations: int
+    status: int
+    rel_residual: float
+    true_rel_residual: float
+
+
+class Context:
+    """An sgp context on one CUDA device, ordered on a torch stream."""
+
+    def __init__(self, device: int | torch.device = 0, stream: torch.cuda.Stream | None = None):
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise SgpError(ERR_CUDA, "no CUDA device: this library has no CPU path")
+        dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ptr = ctypes.c_void_p()
+        rc = lib.sgp_create(ctypes.byref(self.ptr), dev.index or 0, ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != OK:
+            raise SgpError(rc, "sgp_create failed")
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.sgp_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def _ok(self, rc: int):
+        if rc != OK:
+            raise SgpError(rc, _lib.sgp_last_error(self.ptr).decode())
+
+    # -- calls of include/sgp.h ------------------------------------------
+    def collision_graph(self, pos: torch.Tensor, radii: torch.Tensor, graph: Graph | None = None) -> Graph:
+        n = pos.shape[0]
+        _check_vec(pos, n, name="pos")
+        _check_vec(radii, n, cols=0, name="radii")
+        g = graph if graph is not None else Graph(self)
+        self._ok(_lib.sgp_collision_graph(self.ptr, n, _ptr(pos), _ptr(radii), ctypes.byref(g.ptr)))
+        return g
+
+    def friction_assemble(self, graph: Graph, pos, gamma_par, gamma_perp, gamma0: float,
+                          precision: int = PREC_F64, matrix: Matrix | None = None) -> Matrix:
+        n, m, _ = graph.info()
+        _check_vec(pos, n, name="pos")
+        _check_vec(gamma_par, m, cols=0, name="gamma_par")
+        _check_vec(gamma_perp, m, cols=0, name="gamma_perp")
+        M = matrix if matrix is not None else Matrix(self, n, m, precision)
+        M.n, M.m, M.precision = n, m, precision
+        self._ok(_lib.sgp_friction_assemble(self.ptr, graph.ptr, _ptr(pos), _ptr(gamma_par),
+                                            _ptr(gamma_perp), float(gamma0), precision,
+                                            ctypes.byref(M.ptr)))
+        return M
+
+    def spmv(self, M: Matrix, v: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        _check_vec(v, M.n, name="v")
+        y = torch.empty_like(v) if y is None else y
+        self._ok(_lib.sgp_spmv(self.ptr, M.ptr, _ptr(v), _ptr(y)))
+        return y
+
+    def max_spanning_tree(self, M: Matrix, tree: Tree | None = None) -> Tree:
+        T = tree if tree is not None else Tree(self)
+        self._ok(_lib.sgp_max_spanning_tree(self.ptr, M.ptr, ctypes.byref(T.ptr)))
+        return T
+
+    def tree_factor(self, M: Matrix, T: Tree, factor: Factor | None = None) -> Factor:
+        Fh = factor if factor is not None else Factor(self)
+        self._ok(_lib.sgp_tree_factor(self.ptr, M.ptr, T.ptr, ctypes.byref(Fh.ptr)))
+        return Fh
+
+    def tree_apply(self, Fh: Factor, b: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
+        x = torch.empty_like(b) if x is None else x
+        self._ok(_lib.sgp_tree_apply(self.ptr, Fh.ptr, _ptr(b), _ptr(x)))
+        return x
+
+    def pcg_solve(self, M: Matrix, Fh: Factor | None, F: torch.Tensor, v: torch.Tensor | None = None,
+                  tol: float = 1e-8, maxit: int = 100000, precond: int = PRECOND_TREE,
+                  precision: int = PREC_F64, x0_given: bool = False, max_outer: int = 0,
+                  inner_tol: float = 0.0, raise_on_error: bool = True):
+        _check_vec(F, M.n, name="F")
+        v = torch.zeros_like(F) if v is None else v
+        _check_vec(v, M.n, name="v")
+        o = SolveOpts(tol, maxit, precond, precision, int(x0_given), max_outer, inner_tol)
+        inf = SolveInfo()
+        rc = _lib.sgp_pcg_solve(self.ptr, M.ptr, Fh.ptr if Fh is not None else None, _ptr(F), _ptr(v),
+                                ctypes.byref(o), ctypes.byref(inf))
+        info = Info(inf.iterations, inf.outer_iterations, inf.status, inf.rel_residual,
+                    inf.true_rel_residual)
+        if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
+            self._ok(rc)
+        return v, info
+
+    # -- instrumentation ---------------------------------------------------
+    def set_kernel_timing(self, enable: bool):
+        self._ok(_lib.sgp_set_kernel_timing(self.ptr, int(enable)))
+
+    def kernel_time(self, kclass: int, reset: bool = False):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._ok(_lib.sgp_kernel_time(self.ptr, kclass, ctypes.byref(ms), ctypes.byref(n), int(reset)))
+        return ms.value, n.value
+
+    def launch_count(self, reset: bool = False) -> int:
+        c = ctypes.c_int64()
+        self._ok(_lib.sgp_launch_count(self.ptr, ctypes.byref(c), int(reset)))
+        return c.value
+
+
+def version() -> str:
+    return load_library().sgp_version().decode()

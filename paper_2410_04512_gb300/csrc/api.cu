@@ -1,0 +1,326 @@
+// api.cu -- context, errors, device buffers, scans and kernel timing.
+#include "sgp_internal.cuh"
+
+sgp_status sgp_fail(sgp_ctx *ctx, sgp_status code, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+sgp_status buf_ensure(sgp_ctx *ctx, DBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return SGP_OK;
+    if (b.p) {
+        cudaFreeAsync(b.p, ctx->stream);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = (bytes + 255) & ~size_t(255);
+    cudaError_t e = cudaMallocAsync(&b.p, want, ctx->stream);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return sgp_fail(ctx, SGP_ERR_OOM, "device allocation of %zu bytes failed: %s", want,
+                        cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    return SGP_OK;
+}
+
+void buf_release(DBuf &b, cudaStream_t s)
+{
+    if (b.p) cudaFreeAsync(b.p, s);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+sgp_status scratch_ensure(sgp_ctx *ctx, size_t bytes)
+{
+    if (ctx->d_scratch && ctx->d_scratch_bytes >= bytes) return SGP_OK;
+    if (ctx->d_scratch) cudaFreeAsync(ctx->d_scratch, ctx->stream);
+    ctx->d_scratch = nullptr;
+    size_t want = (bytes + 4095) & ~size_t(4095);
+    cudaError_t e = cudaMallocAsync(&ctx->d_scratch, want, ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->d_scratch = nullptr;
+        ctx->d_scratch_bytes = 0;
+        cudaGetLastError();
+        return sgp_fail(ctx, SGP_ERR_OOM, "scratch allocation of %zu bytes failed", want);
+    }
+    SGP_CUDA(ctx, cudaMemsetAsync(ctx->d_scratch, 0, want, ctx->stream));
+    ctx->d_scratch_bytes = want;
+    return SGP_OK;
+}
+
+sgp_status read_back(sgp_ctx *ctx, void *host, const void *dev, size_t bytes)
+{
+    if (bytes > ctx->h_stage_bytes) {
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        size_t want = bytes < 4096 ? 4096 : bytes;
+        SGP_CUDA(ctx, cudaMallocHost(&ctx->h_stage, want));
+        ctx->h_stage_bytes = want;
+    }
+    SGP_CUDA(ctx, cudaMemcpyAsync(ctx->h_stage, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    memcpy(host, ctx->h_stage, bytes);
+    SGP_TRY(kt_collect(ctx));
+    return SGP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (int32): per-block scans, a recursive scan of the block
+// totals, then a uniform add.  1024 items per block of 256 threads.
+// ---------------------------------------------------------------------------
+#define SCAN_ITEMS 4
+#define SCAN_TILE (SGP_BLOCK * SCAN_ITEMS)
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *sh, int32_t *total)
+{
+    int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (l >= o) x += y;
+    }
+    if (l == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int32_t t = (l < SGP_BLOCK / 32) ? sh[l] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (l >= o) t += y;
+        }
+        if (l < SGP_BLOCK / 32) sh[l] = t;
+    }
+    __syncthreads();
+    int32_t before = (w > 0 ? sh[w - 1] : 0) + x - v;
+    *total = sh[SGP_BLOCK / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_scan_tiles(const int32_t *in, int32_t *out, int32_t *tile_sums, int64_t n)
+{
+    __shared__ int32_t sh[SGP_BLOCK / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    int32_t tot;
+    int32_t run = block_excl_scan(s, sh, &tot);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int32_t *out, const int32_t *tile_off, int64_t n)
+{
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t add = tile_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < n) out[base + k] += add;
+}
+
+__global__ void k_scan_total(const int32_t *in, int32_t *out, int64_t n)
+{
+    // out[n] = out[n-1] + in[n-1] (in is read before out is overwritten when
+    // they alias: the caller saves the last input first)
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = (n > 0 ? out[n - 1] + in[0] : 0);
+}
+
+static sgp_status scan_rec(sgp_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *work)
+{
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int32_t *sums = work;  // tiles + 1 entries
+    LAUNCH(ctx, k_scan_tiles, (unsigned)tiles, SGP_BLOCK, 0, in, out, sums, n);
+    if (tiles > 1) {
+        SGP_TRY(scan_rec(ctx, sums, sums, tiles, work + tiles + 1));
+        LAUNCH(ctx, k_scan_add, (unsigned)tiles, SGP_BLOCK, 0, out, (const int32_t *)sums, n);
+    }
+    return SGP_OK;
+}
+
+sgp_status scan_exclusive_i32(sgp_ctx *ctx, const int32_t *in, int32_t *out, int64_t n)
+{
+    if (n <= 0) {
+        SGP_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(int32_t), ctx->stream));
+        return SGP_OK;
+    }
+    // workspace for all recursion levels, plus one slot to save in[n-1]
+    int64_t need = 8, t = n;
+    while (t > 1) { t = (t + SCAN_TILE - 1) / SCAN_TILE; need += t + 1; }
+    const size_t bytes = (size_t)(need + 64) * sizeof(int32_t) + 4096;
+    if (!ctx->d_scan || ctx->d_scan_bytes < bytes) {
+        if (ctx->d_scan) cudaFreeAsync(ctx->d_scan, ctx->stream);
+        ctx->d_scan = nullptr;
+        ctx->d_scan_bytes = 0;
+        size_t want = std::max<size_t>(bytes, size_t(1) << 18);
+        SGP_CUDA(ctx, cudaMallocAsync(&ctx->d_scan, want, ctx->stream));
+        ctx->d_scan_bytes = want;
+    }
+    int32_t *work = reinterpret_cast<int32_t *>(ctx->d_scan) + 16;
+    int32_t *last = reinterpret_cast<int32_t *>(ctx->d_scan) + 8;
+    SGP_CUDA(ctx, cudaMemcpyAsync(last, in + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    SGP_TRY(scan_rec(ctx, in, out, n, work));
+    LAUNCH(ctx, k_scan_total, 1, 32, 0, (const int32_t *)last, out, n);
+    return SGP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing
+// ---------------------------------------------------------------------------
+static cudaEvent_t ev_get(sgp_ctx *ctx)
+{
+    if (!ctx->ev_free.empty()) {
+        cudaEvent_t e = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev)
+{
+    *ev = nullptr;
+    if (!ctx->timing) return SGP_OK;
+    *ev = ev_get(ctx);
+    SGP_CUDA(ctx, cudaEventRecord(*ev, ctx->stream));
+    (void)kclass;
+    return SGP_OK;
+}
+
+sgp_status kt_end(sgp_ctx *ctx, int kclass, cudaEvent_t start)
+{
+    if (!ctx->timing || !start) return SGP_OK;
+    cudaEvent_t e = ev_get(ctx);
+    SGP_CUDA(ctx, cudaEventRecord(e, ctx->stream));
+    ctx->ev_pending[kclass].push_back(start);
+    ctx->ev_pending[kclass].push_back(e);
+    return SGP_OK;
+}
+
+sgp_status kt_collect(sgp_ctx *ctx)
+{
+    for (int k = 0; k < SGP_KT_COUNT; ++k) {
+        auto &v = ctx->ev_pending[k];
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
+            float ms = 0.f;
+            SGP_CUDA(ctx, cudaEventElapsedTime(&ms, v[i], v[i + 1]));
+            ctx->kt_ms[k] += ms;
+            ctx->kt_n[k] += 1;
+            ctx->ev_free.push_back(v[i]);
+            ctx->ev_free.push_back(v[i + 1]);
+        }
+        v.clear();
+    }
+    return SGP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: context
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *sgp_version(void) { return "sgp 0.1 sm_103a"; }
+
+sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
+{
+    if (!out) return SGP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SGP_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SGP_ERR_CUDA;
+    sgp_ctx *ctx = new sgp_ctx();
+    ctx->device = device;
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (scratch_ensure(ctx, 1 << 20) != SGP_OK || cudaMalloc(&ctx->d_flags, 4096) != cudaSuccess ||
+        cudaMemset(ctx->d_flags, 0, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+        delete ctx;
+        return SGP_ERR_OOM;
+    }
+    *out = ctx;
+    return SGP_OK;
+}
+
+void sgp_destroy(sgp_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    if (ctx->d_scan) cudaFree(ctx->d_scan);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    for (auto e : ctx->ev_free) cudaEventDestroy(e);
+    for (int k = 0; k < SGP_KT_COUNT; ++k)
+        for (auto e : ctx->ev_pending[k]) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char *sgp_last_error(const sgp_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+sgp_status sgp_copy(sgp_ctx *ctx, void *dst, const void *src, int64_t bytes)
+{
+    if (!ctx || bytes < 0 || (bytes > 0 && (!dst || !src))) return SGP_ERR_INVALID_ARG;
+    if (bytes == 0) return SGP_OK;
+    SGP_CUDA(ctx, cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    return SGP_OK;
+}
+
+sgp_status sgp_set_kernel_timing(sgp_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return SGP_ERR_INVALID_ARG;
+    ctx->timing = enable ? 1 : 0;
+    return SGP_OK;
+}
+
+sgp_status sgp_kernel_time(sgp_ctx *ctx, int32_t kclass, double *total_ms, int64_t *launches,
+                           int32_t reset)
+{
+    if (!ctx || kclass < 0 || kclass >= SGP_KT_COUNT) return SGP_ERR_INVALID_ARG;
+    SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    SGP_TRY(kt_collect(ctx));
+    if (total_ms) *total_ms = ctx->kt_ms[kclass];
+    if (launches) *launches = ctx->kt_n[kclass];
+    if (reset) {
+        ctx->kt_ms[kclass] = 0;
+        ctx->kt_n[kclass] = 0;
+    }
+    return SGP_OK;
+}
+
+sgp_status sgp_launch_count(sgp_ctx *ctx, int64_t *count, int32_t reset)
+{
+    if (!ctx) return SGP_ERR_INVALID_ARG;
+    if (count) *count = ctx->launches;
+    if (reset) ctx->launches = 0;
+    return SGP_OK;
+}
+
+}  // extern "C"

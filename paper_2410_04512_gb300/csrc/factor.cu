@@ -1,0 +1,697 @@
+// factor.cu -- block LDL^T of the spanning-forest preconditioner and its
+// solve (Section 3.3, Algorithm 2; Appendix B.1), scheduled by rake/compress
+// tree contraction.
+//
+// P = gamma0 I + block Laplacian of the forest (self-loops kept, Section 3.1).
+// Eliminating a vertex c whose current neighbours are q (one or two of them)
+// is a block Gaussian elimination step:
+//     D_c       = A_cc                         (pivot, final once c's turn comes)
+//     L_qc      = A_qc D_c^-1
+//     A_qq     -= A_qc D_c^-1 A_cq             (Schur complement)
+//     A_q0q1    = -A_q0c D_c^-1 A_cq1          (fill, only when c had two neighbours)
+// Algorithm 2 eliminates children before parents, one vertex at a time.  Here
+// a round eliminates every leaf at once (rake), then an independent set of
+// degree-2 vertices (compress, each splicing its two neighbours together with
+// the fill block).  The set of compressed vertices is the local minima of a
+// per-round hash among degree-2 neighbours, so chains shrink by a constant
+// fraction per round and any tree needs O(log n) rounds.  Every elimination
+// keeps the graph a forest, so the factor is exact: P^-1 is the same operator
+// as with the paper's order (only rounding differs).
+//
+// Structure (which vertex goes when, with which neighbours) is computed first
+// with integer kernels, level by level (a level = the rake or the compress half
+// of a round).  The numeric factorisation then replays the levels; the solve
+// replays them forward (receivers gather L_qc z_c) and backward (each
+// eliminated vertex gathers from its receivers).  All sums run in a fixed
+// order, so results are bitwise reproducible.
+#include "sgp_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ adjacency
+__global__ void k_tdeg(const int32_t *__restrict__ ij, const int32_t *__restrict__ edges, int64_t nt,
+                       int32_t *deg)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int32_t e = edges[t];
+    atomicAdd(deg + ij[2 * e], 1);
+    atomicAdd(deg + ij[2 * e + 1], 1);
+}
+
+__global__ void k_adj_fill(const int32_t *__restrict__ ij, const int32_t *__restrict__ edges,
+                           int64_t nt, const int32_t *__restrict__ adj_ptr, int32_t *cursor,
+                           int32_t *nbr, int32_t *eref)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int32_t e = edges[t];
+    int32_t a = ij[2 * e], b = ij[2 * e + 1];
+    int32_t sa = adj_ptr[a] + atomicAdd(cursor + a, 1);
+    int32_t sb = adj_ptr[b] + atomicAdd(cursor + b, 1);
+    nbr[sa] = b;
+    eref[sa] = (int32_t)t;
+    nbr[sb] = a;
+    eref[sb] = (int32_t)t;
+}
+
+__global__ void k_adj_sort(const int32_t *__restrict__ adj_ptr, int64_t n, int32_t *nbr,
+                           int32_t *eref)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t b0 = adj_ptr[v], k = adj_ptr[v + 1] - b0;
+    for (int32_t a = 1; a < k; ++a) {
+        int32_t x = nbr[b0 + a], y = eref[b0 + a];
+        int32_t b = a - 1;
+        while (b >= 0 && nbr[b0 + b] > x) {
+            nbr[b0 + b + 1] = nbr[b0 + b];
+            eref[b0 + b + 1] = eref[b0 + b];
+            --b;
+        }
+        nbr[b0 + b + 1] = x;
+        eref[b0 + b + 1] = y;
+    }
+}
+
+// twin[s] = the entry of the same edge in the neighbour's (sorted) list
+__global__ void k_twin(const int32_t *__restrict__ adj_ptr, int64_t n, const int32_t *__restrict__ nbr,
+                       int32_t *twin)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int32_t s = adj_ptr[v]; s < adj_ptr[v + 1]; ++s) {
+        int32_t u = nbr[s];
+        int32_t lo = adj_ptr[u], hi = adj_ptr[u + 1] - 1;
+        while (lo < hi) {
+            int32_t mid = (lo + hi) >> 1;
+            if (nbr[mid] < (int32_t)v) lo = mid + 1;
+            else hi = mid;
+        }
+        twin[s] = lo;
+    }
+}
+
+// A_vv = gamma0 I + sum of the tree blocks at v (sym6), in list order
+__global__ void k_acc_init(const int32_t *__restrict__ adj_ptr, int64_t n,
+                           const int32_t *__restrict__ eref, const int32_t *__restrict__ edges,
+                           const int32_t *__restrict__ edge_slot, const double *__restrict__ blk,
+                           double gamma0, double *acc, int32_t *deg, int32_t *lev, int32_t *alive)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double S[6] = {gamma0, 0.0, 0.0, gamma0, 0.0, gamma0};
+    for (int32_t s = adj_ptr[v]; s < adj_ptr[v + 1]; ++s) {
+        const double *U = blk + 6 * (int64_t)edge_slot[edges[eref[s]]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) S[k] += U[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[6 * v + k] = S[k];
+    deg[v] = adj_ptr[v + 1] - adj_ptr[v];
+    lev[v] = -1;
+    alive[v] = (int32_t)v;
+}
+
+// -------------------------------------------------------- structure: select
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ bool key_less(int32_t a, int32_t b, uint32_t salt)
+{
+    uint32_t ha = mix32((uint32_t)a ^ salt), hb = mix32((uint32_t)b ^ salt);
+    return ha < hb || (ha == hb && a < b);
+}
+
+struct Sim {
+    const int32_t *adj_ptr;
+    int32_t *nbr, *twin, *eref, *deg, *lev, *nrec;
+    int2 *rq, *re, *ren;
+};
+
+// Rake: every alive vertex of degree 0 (final) or 1 (leaf).  Of two adjacent
+// leaves (a two-vertex tree) only the larger id goes.
+__global__ void k_select_rake(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    int32_t v = A[k];
+    int32_t d = S.deg[v];
+    if (d == 0) {
+        S.lev[v] = level;
+        S.nrec[v] = 0;
+    } else if (d == 1) {
+        int32_t e = -1;
+        for (int32_t s = S.adj_ptr[v]; s < S.adj_ptr[v + 1]; ++s)
+            if (S.nbr[s] >= 0) { e = s; break; }
+        int32_t a = S.nbr[e];
+        if (S.deg[a] == 1 && a > v) return;
+        S.lev[v] = level;
+        S.nrec[v] = 1;
+        S.rq[v] = make_int2(a, -1);
+        S.re[v] = make_int2(S.eref[e], -1);
+        S.ren[v] = make_int2(e, -1);
+    }
+}
+
+// Compress: alive degree-2 vertices that beat both neighbours which are
+// themselves of degree 2 (an independent set).
+__global__ void k_select_compress(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level,
+                                  uint32_t salt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    int32_t v = A[k];
+    if (S.lev[v] != -1 || S.deg[v] != 2) return;
+    int32_t e1 = -1, e2 = -1;
+    for (int32_t s = S.adj_ptr[v]; s < S.adj_ptr[v + 1]; ++s)
+        if (S.nbr[s] >= 0) {
+            if (e1 < 0) e1 = s;
+            else { e2 = s; break; }
+        }
+    int32_t a = S.nbr[e1], b = S.nbr[e2];
+    if (S.deg[a] == 2 && key_less(a, v, salt)) return;
+    if (S.deg[b] == 2 && key_less(b, v, salt)) return;
+    if (a > b) {
+        int32_t t = a; a = b; b = t;
+        t = e1; e1 = e2; e2 = t;
+    }
+    S.lev[v] = level;
+    S.nrec[v] = 2;
+    S.rq[v] = make_int2(a, b);
+    S.re[v] = make_int2(S.eref[e1], S.eref[e2]);
+    S.ren[v] = make_int2(e1, e2);
+}
+
+// ----------------------------------------------------- structure: bookkeeping
+// mode 0: eliminated at `level`; mode 1: flagged receiver; mode 2: still alive
+__global__ void k_flags(const int32_t *__restrict__ A, int32_t na, int mode, int32_t level,
+                        const int32_t *__restrict__ lev, const int32_t *__restrict__ rflag,
+                        int32_t *flag)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    int32_t v = A[k];
+    int32_t f;
+    if (mode == 0) f = (lev[v] == level);
+    else if (mode == 1) f = (rflag[v] != 0);
+    else f = (lev[v] == -1);
+    flag[k] = f;
+}
+
+// Stable scatter of flagged list entries to dst[base + off]; mode 0 also
+// records each vertex's position, mode 1 clears the receiver flag.
+__global__ void k_scatter_list(const int32_t *__restrict__ A, int32_t na,
+                               const int32_t *__restrict__ flag, const int32_t *__restrict__ off,
+                               int32_t *dst, int32_t base, int mode, int32_t *pos, int32_t *rflag)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na || !flag[k]) return;
+    int32_t v = A[k];
+    int32_t at = base + off[k];
+    dst[at] = v;
+    if (mode == 0) pos[v] = at;
+    if (mode == 1) rflag[v] = 0;
+}
+
+// pairs of this level's eliminated vertices: nrec -> tmp (to be scanned)
+__global__ void k_level_nrec(const int32_t *__restrict__ ord, int32_t p0, int32_t cnt,
+                             const int32_t *__restrict__ nrec, int32_t *tmp)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < cnt) tmp[k] = nrec[ord[p0 + k]];
+}
+
+__global__ void k_level_pairs(const int32_t *__restrict__ ord, int32_t p0, int32_t cnt,
+                              const int32_t *__restrict__ off, int32_t pair0,
+                              const int32_t *__restrict__ nrec, const int2 *__restrict__ rq,
+                              int32_t *pr_ptr, int32_t *pr_q, int32_t *pr_c, int32_t *rflag)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    int32_t c = ord[p0 + k];
+    int32_t p = pair0 + off[k];
+    pr_ptr[p0 + k] = p;
+    int32_t r = nrec[c];
+    int2 q = rq[c];
+    if (r > 0) { pr_q[p] = q.x; pr_c[p] = c; rflag[q.x] = 1; }
+    if (r > 1) { pr_q[p + 1] = q.y; pr_c[p + 1] = c; rflag[q.y] = 1; }
+}
+
+// Contributors of each receiver: its live entries whose neighbour goes at
+// this level, in list order.  COUNT pass, then FILL pass.
+template <bool FILL>
+__global__ void k_contrib(Sim S, const int32_t *__restrict__ rv, int32_t r0, int32_t cnt,
+                          int32_t level, const int32_t *__restrict__ pos,
+                          const int32_t *__restrict__ pr_ptr, int32_t *count,
+                          const int32_t *__restrict__ off, int32_t ct0, int32_t *rc_ptr, int32_t *ct)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    int32_t q = rv[r0 + k];
+    int32_t c_n = 0;
+    int32_t at = FILL ? ct0 + off[k] : 0;
+    if (FILL) rc_ptr[r0 + k] = at;
+    for (int32_t s = S.adj_ptr[q]; s < S.adj_ptr[q + 1]; ++s) {
+        int32_t c = S.nbr[s];
+        if (c < 0 || S.lev[c] != level) continue;
+        if (FILL) {
+            int32_t which = (S.rq[c].x == q) ? 0 : 1;
+            ct[at + c_n] = pr_ptr[pos[c]] + which;
+        }
+        ++c_n;
+    }
+    if (!FILL) count[k] = c_n;
+}
+
+__global__ void k_apply_rake(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    int32_t v = ord[p0 + k];
+    if (S.nrec[v] != 1) return;
+    int32_t t = S.twin[S.ren[v].x];
+    S.nbr[t] = -1;
+    atomicSub(S.deg + S.rq[v].x, 1);
+}
+
+__global__ void k_apply_compress(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt,
+                                 int32_t nt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    int32_t v = ord[p0 + k];
+    int2 q = S.rq[v], en = S.ren[v];
+    int32_t ta = S.twin[en.x], tb = S.twin[en.y];
+    S.nbr[ta] = q.y;
+    S.nbr[tb] = q.x;
+    S.twin[ta] = tb;
+    S.twin[tb] = ta;
+    S.eref[ta] = nt + v;
+    S.eref[tb] = nt + v;
+}
+
+// ------------------------------------------------------------------ numerics
+struct Num {
+    const int32_t *ord, *nrec, *pr_ptr, *edges, *edge_slot;
+    const int2 *rq, *re;
+    const double *blk;
+    double *acc, *fill, *L, *Dinv, *sbuf;
+    int32_t nt;
+    int *err;
+};
+
+// B = A_{q c} for the current edge `er` between q and c.
+__device__ __forceinline__ void edge_block(const Num &N, int32_t er, int32_t q, double *B)
+{
+    if (er < N.nt) {
+        const double *U = N.blk + 6 * (int64_t)N.edge_slot[N.edges[er]];
+        B[0] = -U[0]; B[1] = -U[1]; B[2] = -U[2];
+        B[3] = -U[1]; B[4] = -U[3]; B[5] = -U[4];
+        B[6] = -U[2]; B[7] = -U[4]; B[8] = -U[5];
+    } else {
+        int32_t x = er - N.nt;
+        const double *F = N.fill + 9 * (int64_t)x;
+        if (N.rq[x].x == q) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) B[k] = F[k];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) B[3 * r + c] = F[3 * c + r];
+        }
+    }
+}
+
+__global__ void k_factor_elim(Num N, int32_t p0, int32_t cnt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    int32_t t = p0 + k;
+    int32_t c = N.ord[t];
+    double D[6], Di[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) D[a] = N.acc[6 * (int64_t)c + a];
+    if (!sym_inv(D, Di)) {
+        atomicOr(N.err, 1);
+        Di[0] = Di[3] = Di[5] = 1.0;
+        Di[1] = Di[2] = Di[4] = 0.0;
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) N.Dinv[6 * (int64_t)t + a] = Di[a];
+    int32_t r = N.nrec[c];
+    if (r == 0) return;
+    int2 q = N.rq[c], er = N.re[c];
+    int32_t p = N.pr_ptr[t];
+    double B0[9], L0[9], C[9];
+    edge_block(N, er.x, q.x, B0);
+    full_mul_sym(B0, Di, L0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) N.L[9 * (int64_t)p + a] = L0[a];
+    full_mul_bt(L0, B0, C);
+    double *S0 = N.sbuf + 6 * (int64_t)p;
+    S0[0] = C[0]; S0[1] = C[1]; S0[2] = C[2]; S0[3] = C[4]; S0[4] = C[5]; S0[5] = C[8];
+    if (r == 2) {
+        double B1[9], L1[9];
+        edge_block(N, er.y, q.y, B1);
+        full_mul_sym(B1, Di, L1);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) N.L[9 * (int64_t)(p + 1) + a] = L1[a];
+        full_mul_bt(L1, B1, C);
+        double *S1 = N.sbuf + 6 * (int64_t)(p + 1);
+        S1[0] = C[0]; S1[1] = C[1]; S1[2] = C[2]; S1[3] = C[4]; S1[4] = C[5]; S1[5] = C[8];
+        // fill A_{q0 q1} = -A_{q0 c} D^-1 A_{c q1} = -L0 B1^T
+        full_mul_bt(L0, B1, C);
+        double *Fo = N.fill + 9 * (int64_t)c;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) Fo[a] = -C[a];
+    }
+}
+
+__global__ void k_factor_recv(Num N, const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
+                              const int32_t *__restrict__ ct, int32_t r0, int32_t cnt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    int32_t q = rv[r0 + k];
+    double A[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) A[a] = N.acc[6 * (int64_t)q + a];
+    for (int32_t j = rc_ptr[r0 + k]; j < rc_ptr[r0 + k + 1]; ++j) {
+        const double *S = N.sbuf + 6 * (int64_t)ct[j];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) A[a] -= S[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) N.acc[6 * (int64_t)q + a] = A[a];
+}
+
+__global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) b[k] = (float)a[k];
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------- solve
+// Forward substitution of one level: each receiver q subtracts
+// sum_c L_qc w_c over this level's contributors c (fixed order).
+template <typename T>
+__global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
+                           const int32_t *__restrict__ ct, const int32_t *__restrict__ pr_c,
+                           const T *__restrict__ L, int32_t r0, int32_t cnt, T *w, const int *done)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt || (done && *done)) return;
+    int32_t q = rv[r0 + k];
+    T s[3] = {0, 0, 0};
+    for (int32_t j = rc_ptr[r0 + k]; j < rc_ptr[r0 + k + 1]; ++j) {
+        int32_t p = ct[j];
+        int32_t c = pr_c[p];
+        T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
+        T y[3];
+        full_mv(L + 9 * (int64_t)p, x, y);
+        s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+    }
+    w[3 * (int64_t)q] -= s[0];
+    w[3 * (int64_t)q + 1] -= s[1];
+    w[3 * (int64_t)q + 2] -= s[2];
+}
+
+// Diagonal solve and backward substitution of one level:
+// z_c = D_c^-1 w_c - sum_q L_qc^T z_q, in place.
+template <typename T>
+__global__ void k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__restrict__ pr_ptr,
+                           const int32_t *__restrict__ pr_q, const T *__restrict__ L,
+                           const T *__restrict__ Dinv, int32_t p0, int32_t cnt, T *w, const int *done)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt || (done && *done)) return;
+    int32_t t = p0 + k;
+    int32_t c = ord[t];
+    T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
+    T z[3];
+    sym_mv(Dinv + 6 * (int64_t)t, x, z);
+    for (int32_t p = pr_ptr[t]; p < pr_ptr[t + 1]; ++p) {
+        int32_t q = pr_q[p];
+        T y[3] = {w[3 * (int64_t)q], w[3 * (int64_t)q + 1], w[3 * (int64_t)q + 2]};
+        T u[3];
+        full_mtv(L + 9 * (int64_t)p, y, u);
+        z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+    }
+    w[3 * (int64_t)c] = z[0];
+    w[3 * (int64_t)c + 1] = z[1];
+    w[3 * (int64_t)c + 2] = z[2];
+}
+
+// In-place P^-1 w (T = double uses the FP64 factor, float the FP32 copies).
+template <typename T>
+sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done)
+{
+    const T *L = reinterpret_cast<const T *>(sizeof(T) == 8 ? F->L.p : F->L32.p);
+    const T *Dinv = reinterpret_cast<const T *>(sizeof(T) == 8 ? F->Dinv.p : F->Dinv32.p);
+    const int32_t *rv = bp<const int32_t>(F->rv), *rc = bp<const int32_t>(F->rc_ptr),
+                  *ct = bp<const int32_t>(F->ct), *prc = bp<const int32_t>(F->pr_c),
+                  *ord = bp<const int32_t>(F->ord), *prp = bp<const int32_t>(F->pr_ptr),
+                  *prq = bp<const int32_t>(F->pr_q);
+    const int B = 128;
+    for (int l = 0; l < F->levels; ++l) {
+        int32_t r0 = F->rl_ptr[l], cnt = F->rl_ptr[l + 1] - r0;
+        if (cnt > 0) LAUNCH(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ct, prc, L, r0, cnt, w, done);
+    }
+    for (int l = F->levels - 1; l >= 0; --l) {
+        int32_t p0 = F->lvl_ptr[l], cnt = F->lvl_ptr[l + 1] - p0;
+        if (cnt > 0) LAUNCH(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
+    }
+    return SGP_OK;
+}
+template sgp_status tree_apply_inplace<double>(sgp_ctx *, const sgp_factor *, double *, const int *);
+template sgp_status tree_apply_inplace<float>(sgp_ctx *, const sgp_factor *, float *, const int *);
+
+// ------------------------------------------------------------------- factor
+static sgp_status compact(sgp_ctx *ctx, const int32_t *A, int32_t na, int mode, int32_t level,
+                          const int32_t *lev, int32_t *rflag, int32_t *flag, int32_t *off,
+                          int32_t *dst, int32_t base, int32_t *pos, int32_t *count)
+{
+    *count = 0;
+    if (na == 0) return SGP_OK;
+    LAUNCH(ctx, k_flags, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, A, na, mode, level, lev,
+           (const int32_t *)rflag, flag);
+    SGP_TRY(scan_exclusive_i32(ctx, flag, off, na));
+    LAUNCH(ctx, k_scatter_list, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, A, na, (const int32_t *)flag,
+           (const int32_t *)off, dst, base, mode, pos, rflag);
+    SGP_TRY(read_back(ctx, count, off + na, sizeof(int32_t)));
+    return SGP_OK;
+}
+
+extern "C" {
+
+sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sgp_factor **out)
+{
+    if (!ctx || !M || !T || !out) return SGP_ERR_INVALID_ARG;
+    if (T->n != M->n) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "tree_factor: size mismatch");
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = M->n, nt = T->nt;
+    sgp_factor *F = *out ? *out : new sgp_factor();
+    *out = F;
+    F->n = n;
+    F->precision = M->precision;
+    F->levels = 0;
+    F->rounds = 0;
+    F->lvl_ptr.assign(1, 0);
+    F->rl_ptr.assign(1, 0);
+    const size_t n1 = (size_t)n + 1, P = 2 * (size_t)n + 2;
+    SGP_TRY(buf_ensure(ctx, F->adj_ptr, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->nbr, sizeof(int32_t) * (2 * nt + 1)));
+    SGP_TRY(buf_ensure(ctx, F->twin, sizeof(int32_t) * (2 * nt + 1)));
+    SGP_TRY(buf_ensure(ctx, F->eref, sizeof(int32_t) * (2 * nt + 1)));
+    SGP_TRY(buf_ensure(ctx, F->deg, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->lev, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->nrec, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->rq, sizeof(int2) * n1));
+    SGP_TRY(buf_ensure(ctx, F->re, sizeof(int2) * n1));
+    SGP_TRY(buf_ensure(ctx, F->ren, sizeof(int2) * n1));
+    SGP_TRY(buf_ensure(ctx, F->pos, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->flag, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->tmp, sizeof(int32_t) * (n1 + 1)));
+    SGP_TRY(buf_ensure(ctx, F->alive_a, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->alive_b, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->rflag, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->cnt, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->acc, sizeof(double) * 6 * n1));
+    SGP_TRY(buf_ensure(ctx, F->fill, sizeof(double) * 9 * n1));
+    SGP_TRY(buf_ensure(ctx, F->sbuf, sizeof(double) * 6 * P));
+    SGP_TRY(buf_ensure(ctx, F->ord, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->pr_ptr, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->pr_q, sizeof(int32_t) * P));
+    SGP_TRY(buf_ensure(ctx, F->pr_c, sizeof(int32_t) * P));
+    SGP_TRY(buf_ensure(ctx, F->rv, sizeof(int32_t) * P));
+    SGP_TRY(buf_ensure(ctx, F->rc_ptr, sizeof(int32_t) * (P + 1)));
+    SGP_TRY(buf_ensure(ctx, F->ct, sizeof(int32_t) * P));
+    SGP_TRY(buf_ensure(ctx, F->L, sizeof(double) * 9 * P));
+    SGP_TRY(buf_ensure(ctx, F->Dinv, sizeof(double) * 6 * n1));
+    SGP_TRY(buf_ensure(ctx, F->work, sizeof(double) * 3 * n1));
+    if (n == 0) return SGP_OK;
+
+    int32_t *adj_ptr = bp<int32_t>(F->adj_ptr), *deg = bp<int32_t>(F->deg);
+    int32_t *nbr = bp<int32_t>(F->nbr), *twin = bp<int32_t>(F->twin), *eref = bp<int32_t>(F->eref);
+    int32_t *lev = bp<int32_t>(F->lev), *nrec = bp<int32_t>(F->nrec), *pos = bp<int32_t>(F->pos);
+    int32_t *flag = bp<int32_t>(F->flag), *tmp = bp<int32_t>(F->tmp), *rflag = bp<int32_t>(F->rflag);
+    int32_t *cnt = bp<int32_t>(F->cnt);
+    int32_t *A = bp<int32_t>(F->alive_a), *Bl = bp<int32_t>(F->alive_b);
+    int32_t *ord = bp<int32_t>(F->ord), *pr_ptr = bp<int32_t>(F->pr_ptr), *pr_q = bp<int32_t>(F->pr_q),
+            *pr_c = bp<int32_t>(F->pr_c), *rv = bp<int32_t>(F->rv), *rc_ptr = bp<int32_t>(F->rc_ptr),
+            *ct = bp<int32_t>(F->ct);
+    const int32_t *ij = bp<const int32_t>(M->ij), *edges = bp<const int32_t>(T->edges);
+
+    // adjacency of the forest, sorted by neighbour, with twin entries
+    SGP_CUDA(ctx, cudaMemsetAsync(deg, 0, sizeof(int32_t) * n1, ctx->stream));
+    LAUNCH(ctx, k_tdeg, grid_for(nt, SGP_BLOCK), SGP_BLOCK, 0, ij, edges, nt, deg);
+    SGP_TRY(scan_exclusive_i32(ctx, deg, adj_ptr, n));
+    SGP_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n1, ctx->stream));
+    LAUNCH(ctx, k_adj_fill, grid_for(nt, SGP_BLOCK), SGP_BLOCK, 0, ij, edges, nt,
+           (const int32_t *)adj_ptr, cnt, nbr, eref);
+    LAUNCH(ctx, k_adj_sort, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr, n, nbr, eref);
+    LAUNCH(ctx, k_twin, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr, n,
+           (const int32_t *)nbr, twin);
+    LAUNCH(ctx, k_acc_init, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr, n,
+           (const int32_t *)eref, edges, bp<const int32_t>(M->edge_slot), bp<const double>(M->blk),
+           M->gamma0, bp<double>(F->acc), deg, lev, A);
+    SGP_CUDA(ctx, cudaMemsetAsync(rflag, 0, sizeof(int32_t) * n1, ctx->stream));
+
+    Sim S{adj_ptr, nbr, twin, eref, deg, lev, nrec, bp<int2>(F->rq), bp<int2>(F->re), bp<int2>(F->ren)};
+    int32_t na = (int32_t)n, npos = 0, npair = 0, nrecv = 0, ncontrib = 0, level = 0;
+    const int max_phases = 4 * 64 + 8 * 32;
+    for (int phase = 0; na > 0; ++phase) {
+        if (phase > max_phases)
+            return sgp_fail(ctx, SGP_ERR_TIMEOUT, "tree_factor: contraction did not finish");
+        const bool rake = (phase % 2) == 0;
+        if (rake) {
+            LAUNCH(ctx, k_select_rake, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level);
+            F->rounds++;
+        } else {
+            uint32_t salt = 0x9E3779B9u * (uint32_t)(phase / 2 + 1);
+            LAUNCH(ctx, k_select_compress, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A,
+                   na, level, salt);
+        }
+        int32_t ne = 0;
+        SGP_TRY(compact(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, &ne));
+        if (ne == 0) continue;
+        // pairs (receivers) of the eliminated vertices
+        LAUNCH(ctx, k_level_nrec, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, npos, ne,
+               (const int32_t *)nrec, flag);
+        SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, ne));
+        LAUNCH(ctx, k_level_pairs, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, npos, ne,
+               (const int32_t *)tmp, npair, (const int32_t *)nrec, (const int2 *)S.rq, pr_ptr, pr_q,
+               pr_c, rflag);
+        int32_t lp = 0;
+        SGP_TRY(read_back(ctx, &lp, tmp + ne, sizeof(int32_t)));
+        // receivers, ascending id, and their contributors
+        int32_t nr = 0;
+        SGP_TRY(compact(ctx, A, na, 1, level, lev, rflag, flag, tmp, rv, nrecv, pos, &nr));
+        if (nr > 0) {
+            LAUNCH(ctx, k_contrib<false>, grid_for(nr, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)rv,
+                   nrecv, nr, level, (const int32_t *)pos, (const int32_t *)pr_ptr, flag,
+                   (const int32_t *)nullptr, 0, (int32_t *)nullptr, (int32_t *)nullptr);
+            SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, nr));
+            LAUNCH(ctx, k_contrib<true>, grid_for(nr, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)rv,
+                   nrecv, nr, level, (const int32_t *)pos, (const int32_t *)pr_ptr, flag,
+                   (const int32_t *)tmp, ncontrib, rc_ptr, ct);
+            int32_t lc = 0;
+            SGP_TRY(read_back(ctx, &lc, tmp + nr, sizeof(int32_t)));
+            if (lc != lp)
+                return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent contraction (%d/%d)", lc, lp);
+            ncontrib += lc;
+        }
+        // structural update
+        if (rake) LAUNCH(ctx, k_apply_rake, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)ord, npos, ne);
+        else LAUNCH(ctx, k_apply_compress, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)ord, npos, ne, (int32_t)nt);
+        npos += ne;
+        npair += lp;
+        nrecv += nr;
+        F->lvl_ptr.push_back(npos);
+        F->rl_ptr.push_back(nrecv);
+        level++;
+        int32_t nalive = 0;
+        SGP_TRY(compact(ctx, A, na, 2, level, lev, rflag, flag, tmp, Bl, 0, pos, &nalive));
+        std::swap(A, Bl);
+        na = nalive;
+    }
+    if (npos != n) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: %d of %lld eliminated", npos, (long long)n);
+    F->levels = level;
+    F->npairs = npair;
+    // closing entries of the pointer arrays
+    const int32_t np32 = npair;
+    SGP_CUDA(ctx, cudaMemcpyAsync(pr_ptr + n, &np32, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    SGP_CUDA(ctx, cudaMemcpyAsync(rc_ptr + nrecv, &ncontrib, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+
+    // numeric factorisation, level by level
+    int *err = ctx->d_flags;
+    SGP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    Num N{ord, nrec, pr_ptr, edges, bp<const int32_t>(M->edge_slot), bp<const int2>(F->rq),
+          bp<const int2>(F->re), bp<const double>(M->blk), bp<double>(F->acc), bp<double>(F->fill),
+          bp<double>(F->L), bp<double>(F->Dinv), bp<double>(F->sbuf), (int32_t)nt, err};
+    for (int l = 0; l < F->levels; ++l) {
+        int32_t p0 = F->lvl_ptr[l], c = F->lvl_ptr[l + 1] - p0;
+        LAUNCH(ctx, k_factor_elim, grid_for(c, 128), 128, 0, N, p0, c);
+        int32_t r0 = F->rl_ptr[l], rc = F->rl_ptr[l + 1] - r0;
+        if (rc > 0)
+            LAUNCH(ctx, k_factor_recv, grid_for(rc, 128), 128, 0, N, (const int32_t *)rv,
+                   (const int32_t *)rc_ptr, (const int32_t *)ct, r0, rc);
+    }
+    if (F->precision == SGP_PREC_MIXED) {
+        SGP_TRY(buf_ensure(ctx, F->L32, sizeof(float) * 9 * P));
+        SGP_TRY(buf_ensure(ctx, F->Dinv32, sizeof(float) * 6 * n1));
+        LAUNCH(ctx, k_to_f32, grid_for(9 * (int64_t)npair, SGP_BLOCK), SGP_BLOCK, 0,
+               bp<const double>(F->L), bp<float>(F->L32), 9 * (int64_t)npair);
+        LAUNCH(ctx, k_to_f32, grid_for(6 * n, SGP_BLOCK), SGP_BLOCK, 0, bp<const double>(F->Dinv),
+               bp<float>(F->Dinv32), 6 * n);
+    }
+    int herr = 0;
+    SGP_TRY(read_back(ctx, &herr, err, sizeof(int)));
+    if (herr) return sgp_fail(ctx, SGP_ERR_NOT_SPD, "tree_factor: a pivot block is not positive definite");
+    return SGP_OK;
+}
+
+sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *F, const double *b, double *x)
+{
+    if (!ctx || !F || (F->n > 0 && (!b || !x))) return SGP_ERR_INVALID_ARG;
+    if (F->n == 0) return SGP_OK;
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (x != b)
+        SGP_CUDA(ctx, cudaMemcpyAsync(x, b, sizeof(double) * 3 * F->n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return tree_apply_inplace<double>(ctx, F, x, nullptr);
+}
+
+sgp_status sgp_factor_info(const sgp_factor *F, int32_t *rounds, int32_t *levels)
+{
+    if (!F) return SGP_ERR_INVALID_ARG;
+    if (rounds) *rounds = F->rounds;
+    if (levels) *levels = F->levels;
+    return SGP_OK;
+}
+
+void sgp_factor_destroy(sgp_factor *F)
+{
+    if (!F) return;
+    cudaDeviceSynchronize();
+    DBuf *bufs[] = {&F->ord, &F->pr_ptr, &F->pr_q, &F->pr_c, &F->rv, &F->rc_ptr, &F->ct, &F->L,
+                    &F->Dinv, &F->L32, &F->Dinv32, &F->work, &F->adj_ptr, &F->nbr, &F->twin,
+                    &F->eref, &F->deg, &F->lev, &F->nrec, &F->rq, &F->re, &F->ren, &F->pos,
+                    &F->flag, &F->alive_a, &F->alive_b, &F->acc, &F->fill, &F->sbuf, &F->tmp,
+                    &F->rflag, &F->cnt};
+    for (DBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    delete F;
+}
+
+}  // extern "C"

@@ -1,0 +1,277 @@
+// graph.cu -- collision graph by a uniform cell list (Section 2, Steps 1-2).
+//
+// Cells i < j are in contact iff |r_j - r_i| < R_i + R_j.  The distance is
+// evaluated with explicit round-to-nearest FP64 operations in a fixed order,
+// sqrt((dx*dx + dy*dy) + dz*dz), so the result does not depend on the
+// compiler's contraction choices.  Grid cells have side >= 2 max R, so every
+// contact lies in one of the 27 grid cells around a cell's own.
+//
+// Output: canonical edge list (i < j), sorted by i then j, and the row
+// pointer up_ptr of that "upper" adjacency.
+#include "sgp_internal.cuh"
+
+namespace {
+
+struct BBox {
+    double lo[3], hi[3], rmax;
+    int bad;
+};
+
+__global__ void k_bbox(const double *__restrict__ pos, const double *__restrict__ radii, int64_t n,
+                       double *partials, unsigned *counter, double *out)
+{
+    __shared__ double sh[SGP_BLOCK / 32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double rmax = 0.0, bad = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double r = radii[i];
+        if (!(r > 0.0) || !isfinite(r)) bad = 1.0;
+        rmax = fmax(rmax, r);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double x = pos[3 * i + a];
+            if (!isfinite(x)) bad = 1.0;
+            lo[a] = fmin(lo[a], x);
+            hi[a] = fmax(hi[a], x);
+        }
+    }
+    // reduce 8 quantities: min as -max(-x)
+    double vals[8] = {-lo[0], -lo[1], -lo[2], hi[0], hi[1], hi[2], rmax, bad};
+    for (int q = 0; q < 8; ++q) {
+        double v = vals[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = sh[0];
+            for (int w = 1; w < SGP_BLOCK / 32; ++w) t = fmax(t, sh[w]);
+            partials[8 * blockIdx.x + q] = t;
+        }
+    }
+    if (last_block(counter)) {
+        if (threadIdx.x < 8) {
+            double t = -INFINITY;
+            for (unsigned b = 0; b < gridDim.x; ++b) t = fmax(t, __ldcg(partials + 8 * b + threadIdx.x));
+            out[threadIdx.x] = t;
+        }
+    }
+}
+
+struct Grid {
+    double lo[3];
+    double h, inv_h;
+    int dim[3];
+};
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_h, int dim)
+{
+    int c = (int)floor((x - lo) * inv_h);
+    return c < 0 ? 0 : (c >= dim ? dim - 1 : c);
+}
+
+__global__ void k_cell_id(const double *__restrict__ pos, int64_t n, Grid g, int32_t *cell_id,
+                          int32_t *cell_cnt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cx = cell_coord(pos[3 * i + 0], g.lo[0], g.inv_h, g.dim[0]);
+    int cy = cell_coord(pos[3 * i + 1], g.lo[1], g.inv_h, g.dim[1]);
+    int cz = cell_coord(pos[3 * i + 2], g.lo[2], g.inv_h, g.dim[2]);
+    int32_t c = (int32_t)(((int64_t)cx * g.dim[1] + cy) * g.dim[2] + cz);
+    cell_id[i] = c;
+    atomicAdd(cell_cnt + c, 1);
+}
+
+// Scatter cells into grid-cell order.  The order inside a grid cell is not
+// deterministic; nothing downstream depends on it (rows are sorted).
+__global__ void k_scatter(const double *__restrict__ pos, const double *__restrict__ radii, int64_t n,
+                          const int32_t *__restrict__ cell_id, const int32_t *__restrict__ cell_start,
+                          int32_t *cursor, int32_t *perm, double4_32a *spos)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = cell_id[i];
+    int32_t s = cell_start[c] + atomicAdd(cursor + c, 1);
+    perm[s] = (int32_t)i;
+    spos[s] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], radii[i]);
+}
+
+// The contact predicate, with explicit round-to-nearest operations in the
+// order sqrt((dx*dx + dy*dy) + dz*dz) < R_i + R_j, dx = x_j - x_i.
+__device__ __forceinline__ bool contact(double4_32a pi, double4_32a pj)
+{
+    double dx = __dsub_rn(pj.x, pi.x);
+    double dy = __dsub_rn(pj.y, pi.y);
+    double dz = __dsub_rn(pj.z, pi.z);
+    double s = __dmul_rn(dx, dx);
+    s = __dadd_rn(s, __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    double d = __dsqrt_rn(s);
+    return d < __dadd_rn(pi.w, pj.w);
+}
+
+// One thread per cell (in grid-cell order).  EMIT = false: count the
+// contacts j > i of cell i; EMIT = true: write them at up_ptr[i] and sort.
+template <bool EMIT>
+__global__ void k_contacts(int64_t n, Grid g, const int32_t *__restrict__ perm,
+                           const double4_32a *__restrict__ spos, const int32_t *__restrict__ cell_start,
+                           int32_t *cnt, const int32_t *__restrict__ up_ptr, int32_t *ij)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t i = perm[t];
+    const double4_32a pi = spos[t];
+    int cx = cell_coord(pi.x, g.lo[0], g.inv_h, g.dim[0]);
+    int cy = cell_coord(pi.y, g.lo[1], g.inv_h, g.dim[1]);
+    int cz = cell_coord(pi.z, g.lo[2], g.inv_h, g.dim[2]);
+    int32_t k = 0;
+    int64_t base = EMIT ? (int64_t)up_ptr[i] : 0;
+    for (int ax = max(cx - 1, 0); ax <= min(cx + 1, g.dim[0] - 1); ++ax)
+        for (int ay = max(cy - 1, 0); ay <= min(cy + 1, g.dim[1] - 1); ++ay) {
+            int64_t row = ((int64_t)ax * g.dim[1] + ay) * g.dim[2];
+            int z0 = max(cz - 1, 0), z1 = min(cz + 1, g.dim[2] - 1);
+            // grid cells (ax, ay, z0..z1) are contiguous in grid-cell order
+            int32_t s0 = cell_start[row + z0], s1 = cell_start[row + z1 + 1];
+            for (int32_t s = s0; s < s1; ++s) {
+                int32_t j = perm[s];
+                if (j <= i) continue;
+                if (contact(pi, spos[s])) {
+                    if (EMIT) {
+                        ij[2 * (base + k)] = i;
+                        ij[2 * (base + k) + 1] = j;
+                    }
+                    ++k;
+                }
+            }
+        }
+    if (!EMIT) {
+        cnt[i] = k;
+    } else {
+        // insertion sort of this row's j values
+        for (int32_t a = 1; a < k; ++a) {
+            int32_t v = ij[2 * (base + a) + 1];
+            int32_t b = a - 1;
+            while (b >= 0 && ij[2 * (base + b) + 1] > v) {
+                ij[2 * (base + b + 1) + 1] = ij[2 * (base + b) + 1];
+                --b;
+            }
+            ij[2 * (base + b + 1) + 1] = v;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+sgp_status sgp_collision_graph(sgp_ctx *ctx, int64_t n, const double *pos, const double *radii,
+                               sgp_graph **out)
+{
+    if (!ctx || !out) return SGP_ERR_INVALID_ARG;
+    if (n < 0 || n >= (int64_t(1) << 30) || (n > 0 && (!pos || !radii)))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "collision_graph: bad n=%lld or NULL input",
+                        (long long)n);
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    sgp_graph *G = *out ? *out : new sgp_graph();
+    *out = G;
+    G->n = n;
+    G->m = 0;
+    SGP_TRY(buf_ensure(ctx, G->up_ptr, sizeof(int32_t) * (size_t)(n + 1)));
+    if (n == 0) {
+        SGP_CUDA(ctx, cudaMemsetAsync(G->up_ptr.p, 0, sizeof(int32_t), ctx->stream));
+        SGP_TRY(buf_ensure(ctx, G->ij, 16));
+        return SGP_OK;
+    }
+    // bounding box, max radius, input validity
+    const int bb_blocks = 296;
+    SGP_TRY(buf_ensure(ctx, G->bbox, sizeof(double) * (8 * bb_blocks + 8) + 64));
+    double *partials = bp<double>(G->bbox);
+    double *bbout = partials + 8 * bb_blocks;
+    unsigned *counter = reinterpret_cast<unsigned *>(bbout + 8);
+    SGP_CUDA(ctx, cudaMemsetAsync(counter, 0, 64, ctx->stream));
+    unsigned nb = (unsigned)std::min<int64_t>(bb_blocks, (n + SGP_BLOCK - 1) / SGP_BLOCK);
+    LAUNCH(ctx, k_bbox, nb, SGP_BLOCK, 0, pos, radii, n, partials, counter, bbout);
+    double hb[8];
+    SGP_TRY(read_back(ctx, hb, bbout, sizeof(hb)));
+    if (hb[7] != 0.0)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG,
+                        "collision_graph: non-finite position or non-positive radius");
+    Grid g;
+    double ext[3];
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = -hb[a];
+        ext[a] = hb[3 + a] - g.lo[a];
+    }
+    // side >= 2 max R with a margin against rounding of the cell index
+    double h = 2.0 * hb[6] * (1.0 + 1e-6);
+    const double max_cells = std::max<double>(2.0 * (double)n, 4096.0);
+    for (;;) {
+        double tot = 1.0;
+        for (int a = 0; a < 3; ++a) tot *= std::floor(ext[a] / h) + 1.0;
+        if (tot <= max_cells) break;
+        h *= std::max(1.0001, std::cbrt(tot / max_cells));
+    }
+    g.h = h;
+    g.inv_h = 1.0 / h;
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.dim[a] = (int)(std::floor(ext[a] / h) + 1.0);
+        ncell *= g.dim[a];
+    }
+    // cells whose index rounds up past floor(ext/h) are clamped into the last
+    // layer; the margin on h keeps every contact within the 27-cell stencil.
+    SGP_TRY(buf_ensure(ctx, G->cell_id, sizeof(int32_t) * n));
+    SGP_TRY(buf_ensure(ctx, G->cell_cnt, sizeof(int32_t) * (ncell + 1)));
+    SGP_TRY(buf_ensure(ctx, G->cell_start, sizeof(int32_t) * (ncell + 1)));
+    SGP_TRY(buf_ensure(ctx, G->perm, sizeof(int32_t) * n));
+    SGP_TRY(buf_ensure(ctx, G->spos, sizeof(double4_32a) * n));
+    SGP_TRY(buf_ensure(ctx, G->cnt, sizeof(int32_t) * (n + 1)));
+    int32_t *cell_id = bp<int32_t>(G->cell_id), *cell_cnt = bp<int32_t>(G->cell_cnt);
+    int32_t *cell_start = bp<int32_t>(G->cell_start), *perm = bp<int32_t>(G->perm);
+    double4_32a *spos = bp<double4_32a>(G->spos);
+    int32_t *cnt = bp<int32_t>(G->cnt), *up = bp<int32_t>(G->up_ptr);
+    SGP_CUDA(ctx, cudaMemsetAsync(cell_cnt, 0, sizeof(int32_t) * (ncell + 1), ctx->stream));
+    LAUNCH(ctx, k_cell_id, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, pos, n, g, cell_id, cell_cnt);
+    SGP_TRY(scan_exclusive_i32(ctx, cell_cnt, cell_start, ncell));
+    SGP_CUDA(ctx, cudaMemsetAsync(cell_cnt, 0, sizeof(int32_t) * (ncell + 1), ctx->stream));
+    LAUNCH(ctx, k_scatter, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, pos, radii, n,
+           (const int32_t *)cell_id, (const int32_t *)cell_start, cell_cnt, perm, spos);
+    LAUNCH(ctx, k_contacts<false>, grid_for(n, 128), 128, 0, n, g, (const int32_t *)perm,
+           (const double4_32a *)spos, (const int32_t *)cell_start, cnt, (const int32_t *)nullptr,
+           (int32_t *)nullptr);
+    SGP_TRY(scan_exclusive_i32(ctx, cnt, up, n));
+    int32_t m32 = 0;
+    SGP_TRY(read_back(ctx, &m32, up + n, sizeof(int32_t)));
+    if (m32 < 0) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "collision_graph: edge count overflow");
+    G->m = m32;
+    SGP_TRY(buf_ensure(ctx, G->ij, sizeof(int32_t) * 2 * (size_t)G->m));
+    LAUNCH(ctx, k_contacts<true>, grid_for(n, 128), 128, 0, n, g, (const int32_t *)perm,
+           (const double4_32a *)spos, (const int32_t *)cell_start, cnt, (const int32_t *)up,
+           bp<int32_t>(G->ij));
+    return SGP_OK;
+}
+
+sgp_status sgp_graph_info(const sgp_graph *G, int64_t *n, int64_t *m, const int32_t **ij)
+{
+    if (!G) return SGP_ERR_INVALID_ARG;
+    if (n) *n = G->n;
+    if (m) *m = G->m;
+    if (ij) *ij = bp<const int32_t>(G->ij);
+    return SGP_OK;
+}
+
+void sgp_graph_destroy(sgp_graph *G)
+{
+    if (!G) return;
+    cudaDeviceSynchronize();
+    DBuf *bufs[] = {&G->ij, &G->up_ptr, &G->cell_id, &G->cell_cnt, &G->cell_start,
+                    &G->perm, &G->spos, &G->cnt, &G->bbox};
+    for (DBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    delete G;
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// msf.cu -- maximum spanning forest by Boruvka's algorithm (Section 3.1).
+//
+// Edges are ordered strictly: weight descending, then edge index ascending.
+// Under a strict total order the maximum spanning forest is unique, so the
+// result equals Prim's (the paper's choice) edge for edge.
+//
+// Each round: every component finds its best outgoing edge (a 64-bit atomic
+// max on the weight bits -- positive doubles order like their bit patterns --
+// then an atomic min on the index among the edges with that weight); each
+// component hooks onto the component across its best edge (of a mutual pair
+// the smaller label stays the root); labels are compressed by pointer
+// jumping.  Rounds repeat until no component has an outgoing edge.
+#include "sgp_internal.cuh"
+
+namespace {
+
+__global__ void k_init_comp(int32_t *comp, int64_t n)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) comp[v] = (int32_t)v;
+}
+
+__global__ void k_reset_best(unsigned long long *bestw, int32_t *beste, int64_t n)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) {
+        bestw[v] = 0ull;
+        beste[v] = INT32_MAX;
+    }
+}
+
+// Live edges: endpoints in different components.  `live` lists edge ids;
+// edges found internal are dropped from the next round's list.
+__global__ void k_best_weight(const int32_t *__restrict__ ij, const double *__restrict__ w,
+                              const int32_t *__restrict__ live, int32_t nlive,
+                              const int32_t *__restrict__ comp, unsigned long long *bestw)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nlive) return;
+    int32_t e = live[k];
+    int32_t a = comp[ij[2 * e]], b = comp[ij[2 * e + 1]];
+    if (a == b) return;
+    unsigned long long wb = (unsigned long long)__double_as_longlong(w[e]);
+    atomicMax(bestw + a, wb);
+    atomicMax(bestw + b, wb);
+}
+
+__global__ void k_best_edge(const int32_t *__restrict__ ij, const double *__restrict__ w,
+                            const int32_t *__restrict__ live, int32_t nlive,
+                            const int32_t *__restrict__ comp,
+                            const unsigned long long *__restrict__ bestw, int32_t *beste,
+                            int32_t *keep)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nlive) return;
+    int32_t e = live[k];
+    int32_t a = comp[ij[2 * e]], b = comp[ij[2 * e + 1]];
+    keep[k] = (a != b);
+    if (a == b) return;
+    unsigned long long wb = (unsigned long long)__double_as_longlong(w[e]);
+    if (wb == bestw[a]) atomicMin(beste + a, e);
+    if (wb == bestw[b]) atomicMin(beste + b, e);
+}
+
+// Roots choose their hook target.  Writes hook[c] (not comp) so that the
+// labels read by other threads stay those of the round's start.
+__global__ void k_hook(const int32_t *__restrict__ ij, const int32_t *__restrict__ comp,
+                       const int32_t *__restrict__ beste, int64_t n, int32_t *hook,
+                       uint8_t *intree, int *any)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int32_t h = comp[c];
+    if (h == (int32_t)c) {
+        int32_t e = beste[c];
+        if (e != INT32_MAX) {
+            int32_t a = comp[ij[2 * e]], b = comp[ij[2 * e + 1]];
+            int32_t d = (a == (int32_t)c) ? b : a;
+            intree[e] = 1;
+            *any = 1;
+            bool mutual = (beste[d] == e);
+            if (!(mutual && (int32_t)c < d)) h = d;
+        }
+    }
+    hook[c] = h;
+}
+
+__global__ void k_apply_hook(const int32_t *__restrict__ hook, int32_t *comp, int64_t n)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n && comp[v] == (int32_t)v) comp[v] = hook[v];
+}
+
+__global__ void k_jump(int32_t *comp, int64_t n)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t c = comp[v];
+    int32_t cc = comp[c];
+    while (c != cc) {
+        c = cc;
+        cc = comp[c];
+    }
+    comp[v] = c;
+}
+
+__global__ void k_iota(int32_t *a, int64_t n)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) a[v] = (int32_t)v;
+}
+
+__global__ void k_compact(const int32_t *__restrict__ src, const int32_t *__restrict__ keep,
+                          const int32_t *__restrict__ off, int64_t n, int32_t *dst)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n && keep[k]) dst[off[k]] = src ? src[k] : (int32_t)k;
+}
+
+__global__ void k_u8_to_i32(const uint8_t *__restrict__ a, int32_t *b, int64_t n)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) b[k] = a[k];
+}
+
+}  // namespace
+
+extern "C" {
+
+sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *M, sgp_tree **out)
+{
+    if (!ctx || !M || !out) return SGP_ERR_INVALID_ARG;
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = M->n, m = M->m;
+    sgp_tree *T = *out ? *out : new sgp_tree();
+    *out = T;
+    T->n = n;
+    SGP_TRY(buf_ensure(ctx, T->comp, sizeof(int32_t) * (n + 1)));
+    SGP_TRY(buf_ensure(ctx, T->bestw, sizeof(unsigned long long) * (n + 1)));
+    SGP_TRY(buf_ensure(ctx, T->beste, sizeof(int32_t) * (n + 1)));
+    SGP_TRY(buf_ensure(ctx, T->hook, sizeof(int32_t) * (n + 1)));
+    SGP_TRY(buf_ensure(ctx, T->intree, (size_t)m + 16));
+    // idx holds: live list A, live list B, keep flags, offsets (m + 1 each)
+    SGP_TRY(buf_ensure(ctx, T->idx, sizeof(int32_t) * 4 * (size_t)(m + 1)));
+    SGP_TRY(buf_ensure(ctx, T->flag, 64));
+    int32_t *comp = bp<int32_t>(T->comp), *beste = bp<int32_t>(T->beste),
+            *hook = bp<int32_t>(T->hook);
+    unsigned long long *bestw = bp<unsigned long long>(T->bestw);
+    uint8_t *intree = bp<uint8_t>(T->intree);
+    int32_t *liveA = bp<int32_t>(T->idx), *liveB = liveA + (m + 1), *keep = liveB + (m + 1),
+            *off = keep + (m + 1);
+    int *any = bp<int>(T->flag);
+    const int32_t *ij = bp<const int32_t>(M->ij);
+    const double *w = bp<const double>(M->w);
+
+    LAUNCH(ctx, k_init_comp, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n);
+    if (m > 0) SGP_CUDA(ctx, cudaMemsetAsync(intree, 0, (size_t)m, ctx->stream));
+    LAUNCH(ctx, k_iota, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, liveA, m);
+    int64_t nlive = m;
+    int rounds = 0;
+    while (nlive > 0) {
+        if (++rounds > 64) return sgp_fail(ctx, SGP_ERR_TIMEOUT, "spanning forest: too many rounds");
+        SGP_CUDA(ctx, cudaMemsetAsync(any, 0, sizeof(int), ctx->stream));
+        LAUNCH(ctx, k_reset_best, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, bestw, beste, n);
+        LAUNCH(ctx, k_best_weight, grid_for(nlive, SGP_BLOCK), SGP_BLOCK, 0, ij, w,
+               (const int32_t *)liveA, (int32_t)nlive, (const int32_t *)comp, bestw);
+        LAUNCH(ctx, k_best_edge, grid_for(nlive, SGP_BLOCK), SGP_BLOCK, 0, ij, w,
+               (const int32_t *)liveA, (int32_t)nlive, (const int32_t *)comp,
+               (const unsigned long long *)bestw, beste, keep);
+        LAUNCH(ctx, k_hook, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, ij, (const int32_t *)comp,
+               (const int32_t *)beste, n, hook, intree, any);
+        LAUNCH(ctx, k_apply_hook, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)hook,
+               comp, n);
+        LAUNCH(ctx, k_jump, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n);
+        // drop edges that were internal at the start of this round
+        SGP_TRY(scan_exclusive_i32(ctx, keep, off, nlive));
+        LAUNCH(ctx, k_compact, grid_for(nlive, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)liveA,
+               (const int32_t *)keep, (const int32_t *)off, nlive, liveB);
+        int32_t h[2] = {0, 0};
+        SGP_TRY(read_back(ctx, &h[0], off + nlive, sizeof(int32_t)));
+        SGP_TRY(read_back(ctx, &h[1], any, sizeof(int)));
+        std::swap(liveA, liveB);
+        nlive = h[0];
+        if (!h[1]) break;
+    }
+    // tree edge ids, ascending
+    LAUNCH(ctx, k_u8_to_i32, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, (const uint8_t *)intree, keep, m);
+    SGP_TRY(scan_exclusive_i32(ctx, keep, off, m));
+    int32_t nt = 0;
+    SGP_TRY(read_back(ctx, &nt, off + m, sizeof(int32_t)));
+    T->nt = nt;
+    T->ncomp = n - nt;
+    SGP_TRY(buf_ensure(ctx, T->edges, sizeof(int32_t) * (size_t)(nt + 1)));
+    LAUNCH(ctx, k_compact, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)nullptr,
+           (const int32_t *)keep, (const int32_t *)off, m, bp<int32_t>(T->edges));
+    return SGP_OK;
+}
+
+sgp_status sgp_tree_info(const sgp_tree *T, int64_t *n_edges, int64_t *n_comp,
+                         const int32_t **edge_ids)
+{
+    if (!T) return SGP_ERR_INVALID_ARG;
+    if (n_edges) *n_edges = T->nt;
+    if (n_comp) *n_comp = T->ncomp;
+    if (edge_ids) *edge_ids = bp<const int32_t>(T->edges);
+    return SGP_OK;
+}
+
+void sgp_tree_destroy(sgp_tree *T)
+{
+    if (!T) return;
+    cudaDeviceSynchronize();
+    DBuf *bufs[] = {&T->edges, &T->comp, &T->bestw, &T->beste, &T->hook, &T->intree,
+                    &T->flag, &T->idx};
+    for (DBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    delete T;
+}
+
+}  // extern "C"

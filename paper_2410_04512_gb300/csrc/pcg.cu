@@ -1,0 +1,590 @@
+// pcg.cu -- products with Gamma and preconditioned conjugate gradients
+// (Section 1.1; Appendix B.2 for the product).
+//
+// y = Gamma v is evaluated in the difference form of Appendix B.2,
+//   y_i = gamma0 v_i + sum_{j ~ i} Upsilon_ij (v_i - v_j),
+// which annihilates rigid translations exactly and never forms the diagonal
+// block (whose FP32 rounding would swamp a small gamma0).
+//
+// PCG scalars (rho, alpha, beta, convergence) live on the device; each
+// reduction kernel ends with a "last block" step that sums the per-block
+// partials in a fixed order and updates them, so no host round trip is
+// needed per iteration and results are bitwise reproducible.  The host
+// launches iterations in chunks and polls the `done` word between chunks.
+#include "sgp_internal.cuh"
+
+template <typename T>
+sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
+
+namespace {
+
+constexpr int RB = 256;        // block size of reduction kernels
+constexpr int MAXP = 4096;     // max blocks (partials) of a reduction kernel
+
+struct Scal {
+    double rho, alpha, beta, FF, stop2, rr, rz, pq;
+    long long it, maxit;
+    int done, status;
+    unsigned cnt;
+    int pad;
+};
+
+// -------------------------------------------------------------- block loads
+template <typename T> struct Blk;
+template <> struct Blk<double> {
+    const int32_t *col;
+    const double *blk;
+    __device__ __forceinline__ void load(int32_t s, double *S, int32_t &j) const
+    {
+        const double2 *b2 = reinterpret_cast<const double2 *>(blk + 6 * (int64_t)s);
+        double2 a = b2[0], b = b2[1], c = b2[2];
+        S[0] = a.x; S[1] = a.y; S[2] = b.x; S[3] = b.y; S[4] = c.x; S[5] = c.y;
+        j = col[s];
+    }
+};
+template <> struct Blk<float> {
+    const int32_t *col;
+    const float *blk;
+    __device__ __forceinline__ void load(int32_t s, float *S, int32_t &j) const
+    {
+        const float4 *b4 = reinterpret_cast<const float4 *>(blk + 8 * (int64_t)s);
+        float4 a = b4[0], b = b4[1];
+        S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w; S[4] = b.x; S[5] = b.y;
+        j = __float_as_int(b.z);
+    }
+};
+
+// y_i of the Appendix B.2 product for row i
+template <typename T>
+__device__ __forceinline__ void row_product(const Blk<T> &B, const int32_t *__restrict__ row_ptr,
+                                            T gamma0, const T *__restrict__ v, int64_t i, T *vi, T *y)
+{
+    vi[0] = v[3 * i]; vi[1] = v[3 * i + 1]; vi[2] = v[3 * i + 2];
+    y[0] = gamma0 * vi[0]; y[1] = gamma0 * vi[1]; y[2] = gamma0 * vi[2];
+    int32_t s1 = row_ptr[i + 1];
+    for (int32_t s = row_ptr[i]; s < s1; ++s) {
+        T S[6];
+        int32_t j;
+        B.load(s, S, j);
+        T d[3] = {vi[0] - v[3 * (int64_t)j], vi[1] - v[3 * (int64_t)j + 1], vi[2] - v[3 * (int64_t)j + 2]};
+        T t[3];
+        sym_mv(S, d, t);
+        y[0] += t[0]; y[1] += t[1]; y[2] += t[2];
+    }
+}
+
+// y = Gamma v  (plain)
+template <typename T>
+__global__ void k_spmv(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, int64_t n,
+                       const T *__restrict__ v, T *y)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T vi[3], yi[3];
+    row_product(B, row_ptr, gamma0, v, i, vi, yi);
+    y[3 * i] = yi[0]; y[3 * i + 1] = yi[1]; y[3 * i + 2] = yi[2];
+}
+
+// PCG product q = Gamma p with p^T q; the last block sets alpha = rho / p^T q.
+template <typename T>
+__global__ void k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, int64_t n,
+                          const T *__restrict__ p, T *q, double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T vi[3], yi[3];
+        row_product(B, row_ptr, gamma0, p, i, vi, yi);
+        q[3 * i] = yi[0]; q[3 * i + 1] = yi[1]; q[3 * i + 2] = yi[2];
+        acc += (double)vi[0] * (double)yi[0] + (double)vi[1] * (double)yi[1] + (double)vi[2] * (double)yi[2];
+    }
+    double s = block_sum<RB>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->cnt)) {
+        double pq = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            sc->pq = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                sc->status = SGP_ERR_NOT_SPD;
+                sc->done = 1;
+            } else {
+                sc->alpha = sc->rho / pq;
+            }
+        }
+    }
+}
+
+// Start of a solve: r = F - Gamma x (or r = F when x starts at 0), w = H r
+// for the diagonal preconditioners (w = r for the tree, applied after),
+// |F|^2 and |r|^2; the last block sets the stopping threshold.
+// PREC: 0 tree (w = r), 1 block Jacobi, 2 none.
+template <typename T, int PREC>
+__global__ void k_init(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, int64_t n,
+                       const T *__restrict__ F, const T *__restrict__ x, int x_given, T *r, T *w,
+                       const T *__restrict__ jac, double tol2, long long maxit, double *partials,
+                       Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    double ff = 0.0, rr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T ri[3] = {F[3 * i], F[3 * i + 1], F[3 * i + 2]};
+        ff += (double)ri[0] * ri[0] + (double)ri[1] * ri[1] + (double)ri[2] * ri[2];
+        if (x_given) {
+            T vi[3], yi[3];
+            row_product(B, row_ptr, gamma0, x, i, vi, yi);
+            ri[0] -= yi[0]; ri[1] -= yi[1]; ri[2] -= yi[2];
+        }
+        rr += (double)ri[0] * ri[0] + (double)ri[1] * ri[1] + (double)ri[2] * ri[2];
+        r[3 * i] = ri[0]; r[3 * i + 1] = ri[1]; r[3 * i + 2] = ri[2];
+        T zi[3] = {ri[0], ri[1], ri[2]};
+        if (PREC == 1) sym_mv(jac + 6 * i, ri, zi);
+        w[3 * i] = zi[0]; w[3 * i + 1] = zi[1]; w[3 * i + 2] = zi[2];
+    }
+    double s1 = block_sum<RB>(ff, sh);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x] = s1;
+    double s2 = block_sum<RB>(rr, sh);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x + 1] = s2;
+    if (last_block(&sc->cnt)) {
+        double a = 0.0, b = 0.0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += RB) {
+            a += __ldcg(partials + 2 * k);
+            b += __ldcg(partials + 2 * k + 1);
+        }
+        a = block_sum<RB>(a, sh);
+        b = block_sum<RB>(b, sh);
+        if (threadIdx.x == 0) {
+            sc->FF = a;
+            sc->rr = b;
+            sc->stop2 = tol2 * a;
+            sc->it = 0;
+            sc->maxit = maxit;
+            sc->status = 0;
+            sc->done = (a == 0.0 || b <= tol2 * a) ? 1 : 0;
+        }
+    }
+}
+
+// rho = r^T w, p = w (after the first preconditioner application)
+template <typename T>
+__global__ void k_rz_init(int64_t n, const T *__restrict__ r, const T *__restrict__ w, T *p,
+                          double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        T wk = w[k];
+        acc += (double)r[k] * (double)wk;
+        p[k] = wk;
+    }
+    double s = block_sum<RB>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->cnt)) {
+        double rz = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            sc->rho = rz;
+            sc->rz = rz;
+            if (!(rz > 0.0) || !isfinite(rz)) {
+                sc->status = SGP_ERR_NOT_SPD;
+                sc->done = 1;
+            }
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, then w = H r (PREC 1, 2) or w = r (PREC 0);
+// |r|^2 (and r^T w for PREC 1, 2).  Last block: iteration count,
+// convergence test, and for PREC 1, 2 also beta and rho.
+template <typename T, typename X, int PREC>
+__global__ void k_update(int64_t n, X *x, const T *__restrict__ p, T *r, const T *__restrict__ q, T *w,
+                         const T *__restrict__ jac, double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    const T a = (T)alpha;
+    double rr = 0.0, rz = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T ri[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int64_t k = 3 * i + c;
+            x[k] += (X)alpha * (X)p[k];
+            ri[c] = r[k] - a * q[k];
+            r[k] = ri[c];
+            rr += (double)ri[c] * (double)ri[c];
+        }
+        T zi[3] = {ri[0], ri[1], ri[2]};
+        if (PREC == 1) sym_mv(jac + 6 * i, ri, zi);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w[3 * i + c] = zi[c];
+            rz += (double)ri[c] * (double)zi[c];
+        }
+    }
+    double s1 = block_sum<RB>(rr, sh);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x] = s1;
+    double s2 = block_sum<RB>(rz, sh);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x + 1] = s2;
+    if (last_block(&sc->cnt)) {
+        double A = 0.0, Bz = 0.0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += RB) {
+            A += __ldcg(partials + 2 * k);
+            Bz += __ldcg(partials + 2 * k + 1);
+        }
+        A = block_sum<RB>(A, sh);
+        Bz = block_sum<RB>(Bz, sh);
+        if (threadIdx.x == 0) {
+            sc->rr = A;
+            sc->it += 1;
+            if (A <= sc->stop2) sc->done = 1;
+            else if (sc->it >= sc->maxit) {
+                sc->done = 1;
+                sc->status = SGP_ERR_NO_CONVERGENCE;
+            } else if (PREC != 0) {
+                sc->beta = Bz / sc->rho;
+                sc->rho = Bz;
+                sc->rz = Bz;
+            }
+        }
+    }
+}
+
+// rho' = r^T w after the tree solve; beta = rho'/rho.
+template <typename T>
+__global__ void k_rz(int64_t n, const T *__restrict__ r, const T *__restrict__ w, double *partials,
+                     Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)r[k] * (double)w[k];
+    double s = block_sum<RB>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->cnt)) {
+        double rz = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            if (!(rz > 0.0) || !isfinite(rz)) {
+                sc->status = SGP_ERR_NOT_SPD;
+                sc->done = 1;
+            } else {
+                sc->beta = rz / sc->rho;
+                sc->rho = rz;
+                sc->rz = rz;
+            }
+        }
+    }
+}
+
+// p = w + beta p
+template <typename T>
+__global__ void k_pupd(int64_t n, const T *__restrict__ w, T *p, const Scal *sc)
+{
+    if (sc->done) return;
+    const T beta = (T)sc->beta;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        p[k] = w[k] + beta * p[k];
+}
+
+// FP64 residual r = F - Gamma x with |r|^2 and |F|^2 (exit check, outer loop)
+__global__ void k_resid64(Blk<double> B, const int32_t *__restrict__ row_ptr, double gamma0, int64_t n,
+                          const double *__restrict__ F, const double *__restrict__ x, double *r,
+                          double *partials, double *out2)
+{
+    __shared__ double sh[RB / 32];
+    double rr = 0.0, ff = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double vi[3], yi[3];
+        row_product(B, row_ptr, gamma0, x, i, vi, yi);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double f = F[3 * i + c];
+            double rc = f - yi[c];
+            if (r) r[3 * i + c] = rc;
+            rr += rc * rc;
+            ff += f * f;
+        }
+    }
+    double s1 = block_sum<RB>(rr, sh);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x] = s1;
+    double s2 = block_sum<RB>(ff, sh);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x + 1] = s2;
+    unsigned *cnt = reinterpret_cast<unsigned *>(out2 + 2);
+    if (last_block(cnt)) {
+        double A = 0.0, Bf = 0.0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += RB) {
+            A += __ldcg(partials + 2 * k);
+            Bf += __ldcg(partials + 2 * k + 1);
+        }
+        A = block_sum<RB>(A, sh);
+        Bf = block_sum<RB>(Bf, sh);
+        if (threadIdx.x == 0) {
+            out2[0] = A;
+            out2[1] = Bf;
+        }
+    }
+}
+
+// mixed: r32 = r64 * s, d = 0
+__global__ void k_scale_to32(int64_t n3, const double *__restrict__ r64, double s, float *r32, float *d)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n3) {
+        r32[k] = (float)(r64[k] * s);
+        d[k] = 0.f;
+    }
+}
+
+// mixed: v += scale * d
+__global__ void k_accumulate(int64_t n3, const float *__restrict__ d, double scale, double *v)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n3) v[k] += scale * (double)d[k];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+namespace {
+
+static unsigned red_grid(int64_t n)
+{
+    int64_t g = (n + RB - 1) / RB;
+    if (g > 4 * 152) g = 4 * 152;  // a few blocks per SM; grid-stride beyond
+    return (unsigned)std::max<int64_t>(g, 1);
+}
+
+template <typename T>
+Blk<T> make_blk(const sgp_matrix *M);
+template <>
+Blk<double> make_blk<double>(const sgp_matrix *M)
+{
+    return Blk<double>{bp<const int32_t>(M->col), bp<const double>(M->blk)};
+}
+template <>
+Blk<float> make_blk<float>(const sgp_matrix *M)
+{
+    return Blk<float>{bp<const int32_t>(M->col), bp<const float>(M->blk32)};
+}
+
+// One PCG run in precision T on Gamma(T) x = F(T).  X is the type of the
+// iterate x.  Returns the device scalar block's final state in *hs.
+template <typename T, typename X>
+sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int precond,
+                   const T *F, X *x, int x_given, double tol, int64_t maxit, T *r, T *p, T *q, T *w,
+                   double *partials, Scal *sc, Scal *hs)
+{
+    const int64_t n = M->n;
+    Blk<T> B = make_blk<T>(M);
+    const int32_t *row_ptr = bp<const int32_t>(M->row_ptr);
+    const T g0 = (T)M->gamma0;
+    const T *jac = nullptr;
+    if (precond == SGP_PRECOND_BLOCK_JACOBI) {
+        SGP_TRY(matrix_block_jacobi(ctx, const_cast<sgp_matrix *>(M)));
+        jac = reinterpret_cast<const T *>(sizeof(T) == 8 ? M->jac.p : M->jac32.p);
+    }
+    const unsigned G = red_grid(n);
+    SGP_CUDA(ctx, cudaMemsetAsync(sc, 0, sizeof(Scal), ctx->stream));
+    if (!x_given) SGP_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(X) * 3 * n, ctx->stream));
+    const T *xin = reinterpret_cast<const T *>(x);
+    if (x_given && sizeof(X) != sizeof(T))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: initial guess precision mismatch");
+    cudaEvent_t ev;
+    SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+    if (precond == SGP_PRECOND_TREE)
+        LAUNCH(ctx, (k_init<T, 0>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol * tol,
+               (long long)maxit, partials, sc);
+    else if (precond == SGP_PRECOND_BLOCK_JACOBI)
+        LAUNCH(ctx, (k_init<T, 1>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol * tol,
+               (long long)maxit, partials, sc);
+    else
+        LAUNCH(ctx, (k_init<T, 2>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol * tol,
+               (long long)maxit, partials, sc);
+    SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
+    SGP_TRY(read_back(ctx, hs, sc, sizeof(Scal)));
+    if (hs->done) return SGP_OK;
+    if (precond == SGP_PRECOND_TREE) {
+        SGP_TRY(kt_begin(ctx, SGP_KT_TREE_SOLVE, &ev));
+        SGP_TRY(tree_apply_inplace<T>(ctx, Fac, w, &sc->done));
+        SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
+    }
+    LAUNCH(ctx, k_rz_init<T>, G, RB, 0, n, (const T *)r, (const T *)w, p, partials, sc);
+    const int chunk = 16;
+    for (;;) {
+        for (int it = 0; it < chunk; ++it) {
+            SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
+            LAUNCH(ctx, k_spmv_pq<T>, G, RB, 0, B, row_ptr, g0, n, (const T *)p, q, partials, sc);
+            SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
+            SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+            if (precond == SGP_PRECOND_TREE)
+                LAUNCH(ctx, (k_update<T, X, 0>), G, RB, 0, n, x, (const T *)p, r, (const T *)q, w, jac,
+                       partials, sc);
+            else if (precond == SGP_PRECOND_BLOCK_JACOBI)
+                LAUNCH(ctx, (k_update<T, X, 1>), G, RB, 0, n, x, (const T *)p, r, (const T *)q, w, jac,
+                       partials, sc);
+            else
+                LAUNCH(ctx, (k_update<T, X, 2>), G, RB, 0, n, x, (const T *)p, r, (const T *)q, w, jac,
+                       partials, sc);
+            SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
+            if (precond == SGP_PRECOND_TREE) {
+                SGP_TRY(kt_begin(ctx, SGP_KT_TREE_SOLVE, &ev));
+                SGP_TRY(tree_apply_inplace<T>(ctx, Fac, w, &sc->done));
+                SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
+                SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+                LAUNCH(ctx, k_rz<T>, G, RB, 0, n, (const T *)r, (const T *)w, partials, sc);
+            } else {
+                SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+            }
+            LAUNCH(ctx, k_pupd<T>, G, RB, 0, n, (const T *)w, p, (const Scal *)sc);
+            SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
+        }
+        SGP_TRY(read_back(ctx, hs, sc, sizeof(Scal)));
+        if (hs->done) break;
+    }
+    return SGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sgp_status sgp_spmv(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *y)
+{
+    if (!ctx || !M || (M->n > 0 && (!v || !y))) return SGP_ERR_INVALID_ARG;
+    if (v == y) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "spmv: v and y must differ");
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaEvent_t ev;
+    SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
+    LAUNCH(ctx, k_spmv<double>, grid_for(M->n, 128), 128, 0, make_blk<double>(M),
+           bp<const int32_t>(M->row_ptr), M->gamma0, M->n, v, y);
+    SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
+    return SGP_OK;
+}
+
+sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, const double *F,
+                         double *v, const sgp_solve_opts *opts, sgp_solve_info *info)
+{
+    if (!ctx || !M || !opts) return SGP_ERR_INVALID_ARG;
+    const int64_t n = M->n;
+    if (n > 0 && (!F || !v)) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: NULL vector");
+    if (!(opts->tol > 0.0) || opts->maxit <= 0)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: tol must be > 0 and maxit >= 1");
+    if (opts->precond < 0 || opts->precond > 2)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: bad preconditioner");
+    if (opts->precond == SGP_PRECOND_TREE && (!Fac || Fac->n != n))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: the tree preconditioner needs a factor of this matrix");
+    const bool mixed = opts->precision == SGP_PREC_MIXED;
+    if (mixed && M->precision != SGP_PREC_MIXED)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: MIXED needs a matrix assembled with MIXED");
+    if (mixed && opts->precond == SGP_PRECOND_TREE && Fac->precision != SGP_PREC_MIXED)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: MIXED needs a factor of a MIXED matrix");
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    sgp_solve_info inf{};
+    if (n == 0) {
+        if (info) *info = inf;
+        return SGP_OK;
+    }
+    // workspace: FP64 r, p, q, w (4 x 3n), FP32 rhs, r, p, q, w, d (6 x 3n),
+    // partials, scalars
+    const size_t v64 = sizeof(double) * 3 * n, v32 = sizeof(float) * 3 * n;
+    size_t need = 4 * v64 + (mixed ? 6 * v32 : 0) + sizeof(double) * 2 * MAXP + 2 * sizeof(Scal) + 4096;
+    SGP_TRY(scratch_ensure(ctx, need + 4096));
+    char *base = reinterpret_cast<char *>(ctx->d_scratch) + 256;
+    auto take = [&](size_t b) {
+        char *p = base;
+        base += (b + 255) & ~size_t(255);
+        return p;
+    };
+    double *partials = reinterpret_cast<double *>(take(sizeof(double) * 2 * MAXP));
+    Scal *sc = reinterpret_cast<Scal *>(take(sizeof(Scal)));
+    double *o2 = reinterpret_cast<double *>(take(64));
+    double *r = reinterpret_cast<double *>(take(v64));
+    double *p = reinterpret_cast<double *>(take(v64));
+    double *q = reinterpret_cast<double *>(take(v64));
+    double *w = reinterpret_cast<double *>(take(v64));
+    Scal hs{};
+    sgp_status rc = SGP_OK;
+    Blk<double> B64 = make_blk<double>(M);
+    const int32_t *row_ptr = bp<const int32_t>(M->row_ptr);
+    const unsigned G = red_grid(n);
+    double hres[2] = {0, 0};
+    if (!mixed) {
+        SGP_TRY(pcg_run<double, double>(ctx, M, Fac, opts->precond, F, v, opts->x0_given, opts->tol,
+                                        opts->maxit, r, p, q, w, partials, sc, &hs));
+        inf.iterations = hs.it;
+        inf.status = hs.status;
+        inf.rel_residual = hs.FF > 0 ? std::sqrt(hs.rr / hs.FF) : 0.0;
+        if (hs.FF == 0.0) SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
+    } else {
+        float *r32 = reinterpret_cast<float *>(take(v32));
+        float *s32 = reinterpret_cast<float *>(take(v32));
+        float *p32 = reinterpret_cast<float *>(take(v32));
+        float *q32 = reinterpret_cast<float *>(take(v32));
+        float *w32 = reinterpret_cast<float *>(take(v32));
+        float *d32 = reinterpret_cast<float *>(take(v32));
+        const int max_outer = opts->max_outer > 0 ? opts->max_outer : 30;
+        const double itol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+        if (!opts->x0_given) SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
+        int64_t total = 0;
+        int outer = 0;
+        for (;;) {
+            SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
+            LAUNCH(ctx, k_resid64, G, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, r,
+                   partials, o2);
+            SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
+            const double rr = hres[0], ff = hres[1];
+            inf.rel_residual = ff > 0 ? std::sqrt(rr / ff) : 0.0;
+            if (ff == 0.0) {
+                SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
+                break;
+            }
+            if (rr <= opts->tol * opts->tol * ff) break;
+            if (outer >= max_outer || total >= opts->maxit) {
+                inf.status = SGP_ERR_NO_CONVERGENCE;
+                break;
+            }
+            const double nr = std::sqrt(rr);
+            LAUNCH(ctx, k_scale_to32, grid_for(3 * n, SGP_BLOCK), SGP_BLOCK, 0, 3 * n, (const double *)r,
+                   1.0 / nr, r32, d32);
+            // inner solve from d = 0 on the scaled residual (|r32| ~ 1)
+            SGP_TRY(pcg_run<float, float>(ctx, M, Fac, opts->precond, (const float *)r32, d32, 0, itol,
+                                          opts->maxit - total, s32, p32, q32, w32, partials, sc, &hs));
+            total += hs.it;
+            ++outer;
+            if (hs.status == SGP_ERR_NOT_SPD) {
+                inf.status = SGP_ERR_NOT_SPD;
+                break;
+            }
+            LAUNCH(ctx, k_accumulate, grid_for(3 * n, SGP_BLOCK), SGP_BLOCK, 0, 3 * n, (const float *)d32,
+                   nr, v);
+        }
+        inf.iterations = total;
+        inf.outer_iterations = outer;
+    }
+    // true FP64 residual at exit
+    SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
+    LAUNCH(ctx, k_resid64, G, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, (double *)nullptr,
+           partials, o2);
+    SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
+    inf.true_rel_residual = hres[1] > 0 ? std::sqrt(hres[0] / hres[1]) : 0.0;
+    if (info) *info = inf;
+    if (inf.status == SGP_ERR_NOT_SPD)
+        rc = sgp_fail(ctx, SGP_ERR_NOT_SPD, "pcg: breakdown (p^T Gamma p or r^T z not positive)");
+    else if (inf.status == SGP_ERR_NO_CONVERGENCE)
+        rc = sgp_fail(ctx, SGP_ERR_NO_CONVERGENCE, "pcg: no convergence after %lld iterations",
+                      (long long)inf.iterations);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+// sgp_internal.cuh -- shared declarations of the sm_103a library behind sgp.h.
+//
+// Block storage conventions:
+//   sym6: a symmetric 3x3 block as {xx, xy, xz, yy, yz, zz}
+//   full9: a general 3x3 block, row-major
+// Vectors of cells are n x 3, row-major (AoS), in the caller's cell order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/sgp.h"
+
+// ---------------------------------------------------------------------------
+// host side: context, errors, launches, buffers
+// ---------------------------------------------------------------------------
+struct sgp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    // pinned staging for small device->host reads
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    // kernel timing
+    int timing = 0;
+    double kt_ms[SGP_KT_COUNT] = {0, 0, 0};
+    int64_t kt_n[SGP_KT_COUNT] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<cudaEvent_t> ev_pending[SGP_KT_COUNT];  // start,end pairs
+    // device scratch of the solver (vectors, partials, scalars); may grow
+    void *d_scratch = nullptr;
+    size_t d_scratch_bytes = 0;
+    // fixed 4 KB of device flags (error words), never reallocated
+    int *d_flags = nullptr;
+    // scan workspace (grows; only the scan touches it)
+    void *d_scan = nullptr;
+    size_t d_scan_bytes = 0;
+};
+
+sgp_status sgp_fail(sgp_ctx *ctx, sgp_status code, const char *fmt, ...);
+
+#define SGP_TRY(...)                          \
+    do {                                      \
+        sgp_status s_ = (__VA_ARGS__);        \
+        if (s_ != SGP_OK) return s_;          \
+    } while (0)
+
+#define SGP_CUDA(ctx, call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return sgp_fail((ctx), e_ == cudaErrorMemoryAllocation ? SGP_ERR_OOM : SGP_ERR_CUDA, \
+                            "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// Launch a kernel on the context stream, count it and check the launch.
+template <typename... KArgs, typename... Args>
+static inline sgp_status sgp_launch(sgp_ctx *ctx, const char *name, void (*k)(KArgs...), dim3 grid,
+                                    dim3 block, size_t smem, Args... args)
+{
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return SGP_OK;
+    k<<<grid, block, smem, ctx->stream>>>(args...);
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return sgp_fail(ctx, SGP_ERR_CUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
+    return SGP_OK;
+}
+#define LAUNCH(ctx, kern, grid, block, smem, ...) \
+    SGP_TRY(sgp_launch((ctx), #kern, kern, dim3(grid), dim3(block), (smem), __VA_ARGS__))
+
+static inline unsigned grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 0 : g);
+}
+
+// Stream-ordered device buffer owned by a handle.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+sgp_status buf_ensure(sgp_ctx *ctx, DBuf &b, size_t bytes);
+void buf_release(DBuf &b, cudaStream_t s);
+template <typename T>
+static inline T *bp(const DBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+// Copy `bytes` from device to host through the pinned stage and synchronise.
+sgp_status read_back(sgp_ctx *ctx, void *host, const void *dev, size_t bytes);
+// Ensure ctx->d_scratch has at least `bytes` (used by reductions and scans).
+sgp_status scratch_ensure(sgp_ctx *ctx, size_t bytes);
+
+// Device-wide exclusive scan of n int32 values into out[0..n]; out[n] is
+// the total.  `in` and `out` may alias.  Deterministic.
+sgp_status scan_exclusive_i32(sgp_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
+
+// Kernel timing hooks (no-ops unless enabled on the context).
+sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev);
+sgp_status kt_end(sgp_ctx *ctx, int kclass, cudaEvent_t ev);
+sgp_status kt_collect(sgp_ctx *ctx);  // after a stream synchronisation
+
+// ---------------------------------------------------------------------------
+// handle types
+// ---------------------------------------------------------------------------
+struct sgp_graph {
+    int64_t n = 0, m = 0;
+    DBuf ij;       // m x 2 int32, canonical (i < j), sorted
+    DBuf up_ptr;   // n + 1 int32: edges of row i are [up_ptr[i], up_ptr[i+1])
+    // cell-list scratch kept for reuse
+    DBuf cell_id, cell_cnt, cell_start, perm, spos, cnt, bbox;
+};
+
+struct sgp_matrix {
+    int64_t n = 0, m = 0;
+    double gamma0 = 0;
+    int32_t precision = SGP_PREC_F64;
+    DBuf ij;         // m x 2 int32 (copy of the graph's edge list)
+    DBuf row_ptr;    // n + 1 int32 over 2m directed slots, columns ascending in a row
+    DBuf col;        // 2m int32
+    DBuf blk;        // 2m x sym6 float64
+    DBuf blk32;      // 2m x 8 float32: sym6, col (as int bits), pad -- MIXED only
+    DBuf edge_slot;  // m int32: slot of (i, j) in row i
+    DBuf w;          // m float64 tree weight min(g_par, g_perp)
+    DBuf slot_edge;  // 2m int32 (scratch)
+    DBuf lowcnt, cursor;
+    DBuf jac;        // n x sym6 float64 block-Jacobi inverse (built lazily)
+    DBuf jac32;      // n x sym6 float32
+    int jac_valid = 0;
+};
+
+struct sgp_tree {
+    int64_t n = 0, nt = 0, ncomp = 0;
+    DBuf edges;   // nt int32 tree edge ids, ascending
+    DBuf comp;    // n int32 component label
+    DBuf bestw, beste, hook, intree, flag, idx;
+};
+
+struct sgp_factor {
+    int64_t n = 0, npairs = 0;
+    int32_t rounds = 0, levels = 0;
+    int32_t precision = SGP_PREC_F64;
+    std::vector<int32_t> lvl_ptr;   // host, levels + 1: positions of each level in ord
+    std::vector<int32_t> rl_ptr;    // host, levels + 1: receivers of each level in rv
+    DBuf ord;       // n int32 vertex eliminated at each position
+    DBuf pr_ptr;    // n + 1 int32 pairs (receivers) of each position
+    DBuf pr_q;      // npairs int32 receiver vertex of each pair
+    DBuf pr_c;      // npairs int32 contributor vertex of each pair
+    DBuf rv;        // receivers, level by level, ascending vertex id within a level
+    DBuf rc_ptr;    // (#receivers + 1) int32 into ct
+    DBuf ct;        // npairs int32 pair ids grouped by receiver
+    DBuf L, Dinv;   // npairs x full9, n x sym6 (by position), float64
+    DBuf L32, Dinv32;
+    DBuf work;      // n x 3 float64 apply workspace
+    // structure-simulation scratch
+    DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,
+        acc, fill, sbuf, tmp, rflag, cnt;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#define SGP_BLOCK 256
+
+// sym6 y = S x
+template <typename T, typename U>
+__device__ __forceinline__ void sym_mv(const T *S, const U *x, U *y)
+{
+    y[0] = (U)S[0] * x[0] + (U)S[1] * x[1] + (U)S[2] * x[2];
+    y[1] = (U)S[1] * x[0] + (U)S[3] * x[1] + (U)S[4] * x[2];
+    y[2] = (U)S[2] * x[0] + (U)S[4] * x[1] + (U)S[5] * x[2];
+}
+
+// Inverse of a symmetric 3x3 block by its adjugate.  Returns false unless
+// the leading principal minors are positive (positive definiteness).
+__device__ __forceinline__ bool sym_inv(const double *S, double *R)
+{
+    double a = S[0], b = S[1], c = S[2], d = S[3], e = S[4], f = S[5];
+    double c00 = d * f - e * e;
+    double c01 = c * e - b * f;
+    double c02 = b * e - c * d;
+    double c11 = a * f - c * c;
+    double c12 = b * c - a * e;
+    double c22 = a * d - b * b;
+    double det = a * c00 + b * c01 + c * c02;
+    if (!(a > 0.0) || !(c22 > 0.0) || !(det > 0.0) || !isfinite(det)) return false;
+    double id = 1.0 / det;
+    R[0] = c00 * id; R[1] = c01 * id; R[2] = c02 * id;
+    R[3] = c11 * id; R[4] = c12 * id; R[5] = c22 * id;
+    return true;
+}
+
+// full9 C = A * S (S sym6)
+__device__ __forceinline__ void full_mul_sym(const double *A, const double *S, double *C)
+{
+    double s[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = A[3 * r] * s[c] + A[3 * r + 1] * s[3 + c] + A[3 * r + 2] * s[6 + c];
+}
+
+// full9 C = A * B^T
+__device__ __forceinline__ void full_mul_bt(const double *A, const double *B, double *C)
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = A[3 * r] * B[3 * c] + A[3 * r + 1] * B[3 * c + 1] + A[3 * r + 2] * B[3 * c + 2];
+}
+
+template <typename T, typename U>
+__device__ __forceinline__ void full_mv(const T *A, const U *x, U *y)
+{
+    y[0] = (U)A[0] * x[0] + (U)A[1] * x[1] + (U)A[2] * x[2];
+    y[1] = (U)A[3] * x[0] + (U)A[4] * x[1] + (U)A[5] * x[2];
+    y[2] = (U)A[6] * x[0] + (U)A[7] * x[1] + (U)A[8] * x[2];
+}
+template <typename T, typename U>
+__device__ __forceinline__ void full_mtv(const T *A, const U *x, U *y)
+{
+    y[0] = (U)A[0] * x[0] + (U)A[3] * x[1] + (U)A[6] * x[2];
+    y[1] = (U)A[1] * x[0] + (U)A[4] * x[1] + (U)A[7] * x[2];
+    y[2] = (U)A[2] * x[0] + (U)A[5] * x[1] + (U)A[8] * x[2];
+}
+
+// Deterministic block sum (fixed shuffle tree, fixed warp order).
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = (l < BS / 32) ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// "Last block done": every block calls this after writing its partial;
+// returns true in exactly one block (the last to arrive), which may then
+// read every partial.  The counter is reset by the last block.
+__device__ __forceinline__ bool last_block(unsigned *counter)
+{
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+        if (am_last) *counter = 0u;
+    }
+    __syncthreads();
+    return am_last;
+}
+
+// Sum of partials[0..n) in a fixed order by one block.
+template <int BS>
+__device__ __forceinline__ double sum_partials(const double *partials, int n, double *sh)
+{
+    double v = 0.0;
+    for (int k = threadIdx.x; k < n; k += BS) v += __ldcg(partials + k);
+    return block_sum<BS>(v, sh);
+}
+
+// internal entry points shared between translation units
+sgp_status matrix_block_jacobi(sgp_ctx *ctx, sgp_matrix *M);
