@@ -1,0 +1,385 @@
+"""Benchmark: PCG solves/sec to relative residual 1e-8 on one GB300.
+
+One step = one pass of the whole path on one synthetic cell configuration:
+collision graph -> per-contact friction coefficients -> friction blocks ->
+maximum spanning forest -> tree factor -> PCG solve of Gamma v = F.
+Inputs are resident in HBM when the timed region starts (``value``); the
+``e2e`` figure repeats the step through the public API from pinned host
+buffers, with the host<->device copies inside the timed region.
+
+Default workload: a spheroid of 1,000,000 cells (centres uniform in a ball
+at packing fraction 0.6, radii U[0.45, 0.55]), per-pair gamma_par and
+gamma_perp log-uniform in [0.1, 10], gamma0 = 1e-3, F ~ N(0, 1), FP64,
+spanning-forest preconditioner.
+
+``--impl reference`` times the CPU oracle instead (host cores, a bounded
+sample of the same workload).  Under torchrun each rank solves its own
+independent replica (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "PCG solves/sec to rel-res 1e-8 (% HBM roofline); chosen form vs plain FP64, 1 GB300"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    "ball1m": dict(desc="spheroid of 1,000,000 cells, ball at packing 0.6, radii U[0.45,0.55], "
+                        "gamma log-uniform [0.1,10] per pair, gamma0=1e-3, F~N(0,1)",
+                   make=lambda seed: workloads.ball(n=1_000_000, seed=seed, gamma0=1e-3)),
+    "cube1k": dict(desc="1,000 cells uniform in a cube of side 8.886, radii U[0.45,0.55], "
+                        "gamma log-uniform [0.1,10], gamma0=1e-2",
+                   make=lambda seed: workloads.cube(n=1000, side=8.886, seed=seed)),
+    "hex4m": dict(desc="monolayer of 4,000,000 cells, 2000x2000 jittered hexagonal lattice a=0.9, "
+                       "radii U[0.48,0.52], gamma log-uniform [0.01,100], gamma0=1e-4",
+                  make=lambda seed: workloads.hex_sheet(nx=2000, ny=2000, seed=seed)),
+}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2410_04512_gb300 as sgp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peaks_src = load_peaks()
+
+    wl = WORKLOADS[args.workload]
+    cells = wl["make"](2000 + rank)          # each rank: its own independent replica
+    n = cells.n
+    F_host = cells.forces()
+    tp, tq = cells.tables()
+    pos = torch.from_numpy(cells.pos).to(dev)
+    radii = torch.from_numpy(cells.radii).to(dev)
+    F = torch.from_numpy(F_host).to(dev)
+    tpd, tqd = torch.from_numpy(tp).to(dev), torch.from_numpy(tq).to(dev)
+    v = torch.zeros_like(F)
+    precision = sgp.PREC_MIXED if args.precision == "mixed" else sgp.PREC_F64
+    precond = {"tree": sgp.PRECOND_TREE, "jacobi": sgp.PRECOND_BLOCK_JACOBI,
+               "none": sgp.PRECOND_NONE}[args.precond]
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgp.Context(local, stream)
+    H = {"g": None, "M": None, "T": None, "Fh": None}
+    last = {}
+
+    def step(pos_d, radii_d, F_d, out_v):
+        H["g"] = ctx.collision_graph(pos_d, radii_d, H["g"])
+        ij = H["g"].edges()
+        gp, gq = workloads.pair_gamma_torch(cells.seed, ij, tpd, tqd)
+        H["M"] = ctx.friction_assemble(H["g"], pos_d, gp.contiguous(), gq.contiguous(), cells.gamma0,
+                                       precision, H["M"])
+        if precond == sgp.PRECOND_TREE:
+            H["T"] = ctx.max_spanning_tree(H["M"], H["T"])
+            H["Fh"] = ctx.tree_factor(H["M"], H["T"], H["Fh"])
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, info = ctx.pcg_solve(H["M"], H["Fh"], F_d, out_v, tol=args.tol, precond=precond,
+                                precision=precision)
+        ev1.record(stream)
+        last["info"], last["solve_ev"] = info, (ev0, ev1)
+        return info
+
+    for _ in range(args.warmup):
+        step(pos, radii, F, v)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # ---- timed region: device-resident inputs -----------------------------
+    ctx.set_kernel_timing(True)
+    for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR):
+        ctx.kernel_time(k, reset=True)
+    ctx.launch_count(reset=True)
+    solve_ms, iters = [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            info = step(pos, radii, F, v)
+            iters.append(info.iterations)
+            a, b = last["solve_ev"]
+            b.synchronize()
+            solve_ms.append(a.elapsed_time(b))
+        t1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    launches = ctx.launch_count()
+    kt = {k: ctx.kernel_time(k) for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR)}
+    ctx.set_kernel_timing(False)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    info = last["info"]
+
+    # ---- end to end through the public API from pinned host buffers -------
+    pos_h = torch.from_numpy(cells.pos).pin_memory()
+    rad_h = torch.from_numpy(cells.radii).pin_memory()
+    F_h = torch.from_numpy(F_host).pin_memory()
+    v_h = torch.empty_like(F_h).pin_memory()
+    pos_e, rad_e, F_e, v_e = torch.empty_like(pos), torch.empty_like(radii), torch.empty_like(F), torch.empty_like(F)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        pos_e.copy_(pos_h, non_blocking=True)
+        rad_e.copy_(rad_h, non_blocking=True)
+        F_e.copy_(F_h, non_blocking=True)
+        step(pos_e, rad_e, F_e, v_e)
+        v_h.copy_(v_e, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_steps / e2e_s
+    h2d = pos.numel() * 8 + radii.numel() * 8 + F.numel() * 8
+    d2h = F.numel() * 8
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    m = H["M"].m
+    dbar = 2.0 * m / n
+    it_mean = float(np.mean(iters))
+    spmv_ms, spmv_n = kt[sgp.KT_SPMV]
+    tree_ms, tree_n = kt[sgp.KT_TREE_SOLVE]
+    vec_ms, vec_n = kt[sgp.KT_PCG_VECTOR]
+    fp = 8 if precision == sgp.PREC_F64 else 4
+    # SpMV q = Gamma p (+ p^T q): per directed slot a symmetric block (6 words)
+    # and a column index; per row the row pointer, p_i and q_i.
+    spmv_bytes = 2 * m * (6 * fp + 4) + n * (4 + 3 * fp + 3 * fp)
+    spmv_avg_s = (spmv_ms / max(spmv_n, 1)) / 1e3
+    spmv_gbs = spmv_bytes / spmv_avg_s / 1e9 if spmv_avg_s > 0 else 0.0
+    spmv_flops = 2 * m * (3 + 18) + n * 6       # v_i - v_j, S d (9 FMA), gamma0 v_i
+    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    roof = {"kernel": "k_spmv_pq<double>" if fp == 8 else "k_spmv_pq<float>",
+            "bound": "hbm", "achieved": round(spmv_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(spmv_gbs / hbm_peak, 4), "traffic": None,
+            "peak_source": f"{peaks_src} (MEASURED_PEAKS.json hbm_gbs)" if peaks_src == "measured" else "fallback",
+            "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": round(spmv_avg_s * 1e6, 2),
+            "launches": spmv_n,
+            "fp64_alu_frac": round(spmv_flops / spmv_avg_s / (FP64_NOMINAL_TFLOPS * 1e12), 4) if fp == 8 else None}
+    share = {"spmv_ms": round(spmv_ms, 2), "tree_solve_ms": round(tree_ms, 2), "pcg_vector_ms": round(vec_ms, 2),
+             "timed_ms": round(elapsed * 1e3, 2)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == sgp.PREC_F64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_cells": n, "edges": int(m), "mean_degree": round(dbar, 3),
+                   "precond": args.precond, "precision": args.precision, "tol": args.tol,
+                   "step": "collision graph + friction blocks + spanning forest + tree factor + PCG solve",
+                   "l2": "working set > L2 (friction blocks alone %.0f MB)" % (2 * m * 6 * fp / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iterations": int(round(it_mean)), "true_rel_residual": info.true_rel_residual,
+        "solve_only": {"value": round(1e3 / float(np.median(solve_ms)), 4), "unit": "solves/s",
+                       "ms_median": round(float(np.median(solve_ms)), 3)},
+        "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": roof, "time_share": share,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, n, run_seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle: cpu_baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+def oracle_sample(n_sample: int, seed: int, tol: float):
+    """One oracle pass over a ball of n_sample cells of the default law:
+    brute-force contacts, eq. (1) blocks, Prim, TreeLDLT, PCG."""
+    import oracle
+    c = workloads.ball(n=n_sample, seed=seed, gamma0=1e-3)
+    F = c.forces()
+    t = time.perf_counter()
+    s = oracle.build_system(c.pos, c.radii, c.gammas_np, c.gamma0)
+    res, _ = oracle.solve_system(s, F, tol=tol)
+    return time.perf_counter() - t, res.iters
+
+
+def cpu_baseline(args, n_full: int, run_seconds: float = 15.0):
+    n_s = args.cpu_sample_cells
+    times, its = [], []
+    t0 = time.perf_counter()
+    while True:
+        dt, it = oracle_sample(n_s, 2000, args.tol)
+        times.append(dt)
+        its.append(it)
+        if time.perf_counter() - t0 > run_seconds or len(times) >= 20:
+            break
+    per = float(np.median(times)) * (n_full / n_s)
+    return {"value": round(1.0 / per, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} oracle passes on a {n_s}-cell ball of the same law (brute-force "
+                      f"contacts, Prim, TreeLDLT, PCG to {args.tol:g}; {int(np.median(its))} iterations), "
+                      f"median {np.median(times):.3f} s, scaled by N ({n_full}/{n_s}) to the full workload"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_full = {"ball1m": 1_000_000, "cube1k": 1000, "hex4m": 4_000_000}[args.workload]
+    n_s = min(args.cpu_sample_cells, n_full)
+    for _ in range(args.warmup):
+        oracle_sample(n_s, 2000, args.tol)
+    times, its = [], []
+    for _ in range(args.steps):
+        dt, it = oracle_sample(n_s, 2000, args.tol)
+        times.append(dt)
+        its.append(it)
+    total = float(np.sum(times)) * (n_full / n_s)
+    value = args.steps / total
+    line = {"metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "n_cells": n_full, "tol": args.tol,
+                       "precond": "tree", "precision": "fp64"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one oracle pass on a {n_s}-cell ball of the same law, "
+                                       f"time scaled by N ({n_full}/{n_s})"},
+            "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sgp", choices=["sgp", "reference"])
+    ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--precond", default="tree", choices=["tree", "jacobi", "none"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--cpu-baseline", dest="cpu_baseline", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-sample-cells", type=int, default=20000)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "sgp":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
