@@ -127,6 +127,24 @@ sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *graph, const dou
  *   y_i = gamma0 v_i + sum_{j ~ i} Upsilon_ij (v_i - v_j).
  * v_dev, y_dev: n x 3 float64, distinct buffers. */
 sgp_status sgp_spmv(sgp_ctx *ctx, const sgp_matrix *matrix, const double *v_dev, double *y_dev);
+/* y = Gamma v (as sgp_spmv) and *dot_dev = v^T y, allocating nothing.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run -- code inside a CUDA stream
+ * capture (allocation calls are not allowed there), applications whose
+ * device memory belongs to their own pool, or loops that cannot afford the
+ * synchronisation of cudaMalloc/cudaFree.  Its scratch (one partial sum per
+ * thread block and a counter, 33024 bytes) is a fixed array inside the
+ * library that every GPU which loads the library keeps until the process
+ * exits; hence at most 1,048,576 cells (4096 blocks of 256 rows): larger
+ * matrices get SGP_ERR_INVALID_ARG.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * last call's contents; its counter is cleared at the start of each call.
+ * Calls whose GPU work overlaps (other streams or host threads) race on the
+ * array.  v_dev, y_dev: n x 3 float64, distinct; dot_dev: one float64
+ * (device).  Asynchronous on the context stream. */
+sgp_status sgp_spmv_dot_noalloc(sgp_ctx *ctx, const sgp_matrix *matrix, const double *v_dev,
+                                double *y_dev, double *dot_dev);
 /* Copy the FP64 block of edge e (row-major 3x3) for every edge into
  * blocks_dev (m x 9 float64) and the tree weights into w_dev (m float64);
  * either pointer may be NULL. */

@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "sgp_graph_destroy": ([P], None),
         "sgp_friction_assemble": ([P, P, P, P, P, D, I32, PP], I32),
         "sgp_spmv": ([P, P, P, P], I32),
+        "sgp_spmv_dot_noalloc": ([P, P, P, P, P], I32),
         "sgp_matrix_edge_blocks": ([P, P, P, P], I32),
         "sgp_matrix_destroy": ([P], None),
         "sgp_max_spanning_tree": ([P, P, PP], I32),
