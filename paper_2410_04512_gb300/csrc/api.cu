@@ -1,6 +1,9 @@
 // api.cu -- context, errors, device buffers, scans and kernel timing.
 #include "sgp_internal.cuh"
 
+#include <atomic>
+#include <cstdlib>
+
 sgp_status sgp_fail(sgp_ctx *ctx, sgp_status code, const char *fmt, ...)
 {
     if (ctx) {
@@ -205,19 +208,149 @@ sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev)
 {
     *ev = nullptr;
     if (!ctx->timing) return SGP_OK;
+    if (ctx->capture_sink) {
+        // inside a capture: an event-record node owned by the graph entry;
+        // only the product is timed there, to keep the graph lean
+        if (kclass != SGP_KT_SPMV) return SGP_OK;
+        SGP_CUDA(ctx, cudaEventCreate(ev));
+        SGP_CUDA(ctx, cudaEventRecordWithFlags(*ev, ctx->stream, cudaEventRecordExternal));
+        return SGP_OK;
+    }
     *ev = ev_get(ctx);
     SGP_CUDA(ctx, cudaEventRecord(*ev, ctx->stream));
-    (void)kclass;
     return SGP_OK;
 }
 
 sgp_status kt_end(sgp_ctx *ctx, int kclass, cudaEvent_t start)
 {
     if (!ctx->timing || !start) return SGP_OK;
+    if (ctx->capture_sink) {
+        cudaEvent_t e = nullptr;
+        SGP_CUDA(ctx, cudaEventCreate(&e));
+        SGP_CUDA(ctx, cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal));
+        ctx->capture_sink->push_back(KtRec{kclass, start, e});
+        return SGP_OK;
+    }
     cudaEvent_t e = ev_get(ctx);
     SGP_CUDA(ctx, cudaEventRecord(e, ctx->stream));
     ctx->ev_pending[kclass].push_back(start);
     ctx->ev_pending[kclass].push_back(e);
+    return SGP_OK;
+}
+
+sgp_status resident_grid(sgp_ctx *ctx, const void *kernel, int block, int64_t want, unsigned *grid)
+{
+    if (!ctx->num_sms) SGP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    int per_sm = 0;
+    for (auto &kv : ctx->occupancy)
+        if (kv.first == kernel) per_sm = kv.second;
+    if (!per_sm) {
+        SGP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0));
+        per_sm = std::max(per_sm, 1);
+        ctx->occupancy.push_back({kernel, per_sm});
+    }
+    int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    *grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+    return SGP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph cache
+// ---------------------------------------------------------------------------
+uint64_t next_generation()
+{
+    static std::atomic<uint64_t> g{1};
+    return g.fetch_add(1);
+}
+
+static void graph_free(GraphEntry *ge)
+{
+    if (ge->exec) cudaGraphExecDestroy(ge->exec);
+    for (auto &r : ge->ev) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete ge;
+}
+
+void graph_release_all(sgp_ctx *ctx)
+{
+    for (GraphEntry *ge : ctx->graphs) graph_free(ge);
+    ctx->graphs.clear();
+}
+
+sgp_status graph_lookup(sgp_ctx *ctx, const uint64_t *key, int nkey, GraphEntry **out)
+{
+    if (nkey > 32) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "graph key too long");
+    ++ctx->graph_clock;
+    for (GraphEntry *ge : ctx->graphs)
+        if (ge->nkey == nkey && std::memcmp(ge->key, key, sizeof(uint64_t) * nkey) == 0) {
+            ge->last_use = ctx->graph_clock;
+            *out = ge;
+            return SGP_OK;
+        }
+    const size_t max_entries = 6;
+    if (ctx->graphs.size() >= max_entries) {
+        auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                    [](GraphEntry *a, GraphEntry *b) { return a->last_use < b->last_use; });
+        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        graph_free(*lru);
+        ctx->graphs.erase(lru);
+    }
+    GraphEntry *ge = new GraphEntry();
+    std::memcpy(ge->key, key, sizeof(uint64_t) * nkey);
+    ge->nkey = nkey;
+    ge->last_use = ctx->graph_clock;
+    ctx->graphs.push_back(ge);
+    *out = ge;
+    return SGP_OK;
+}
+
+sgp_status graph_begin(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t *saved, int64_t *l0)
+{
+    if (!ctx->cap_stream) SGP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    *saved = ctx->stream;
+    *l0 = ctx->launches;
+    SGP_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->cap_stream;
+    ctx->capture_sink = &ge->ev;
+    return SGP_OK;
+}
+
+sgp_status graph_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l0, sgp_status st)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->stream = saved;
+    ctx->capture_sink = nullptr;
+    ge->kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    if (st != SGP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess || !g)
+        return sgp_fail(ctx, SGP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ge->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ge->exec = nullptr;
+        return sgp_fail(ctx, SGP_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return SGP_OK;
+}
+
+// After a replay has completed (the caller synchronised): add the replay's
+// event-pair durations to the kernel-time totals.
+sgp_status graph_collect_timing(sgp_ctx *ctx, GraphEntry *ge)
+{
+    if (!ctx->timing) return SGP_OK;
+    for (auto &r : ge->ev) {
+        float ms = 0.f;
+        SGP_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->kt_ms[r.cls] += ms;
+        ctx->kt_n[r.cls] += 1;
+    }
     return SGP_OK;
 }
 
@@ -258,6 +391,10 @@ sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
     sgp_ctx *ctx = new sgp_ctx();
     ctx->device = device;
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    const char *ng = getenv("SGP_NO_GRAPHS");
+    ctx->use_graphs = (ng && ng[0] == '1') ? 0 : 1;
+    const char *lpr = getenv("SGP_SPMV_LPR");
+    if (lpr) ctx->spmv_lpr = atoi(lpr);
     if (scratch_ensure(ctx, 1 << 20) != SGP_OK || cudaMalloc(&ctx->d_flags, 4096) != cudaSuccess ||
         cudaMemset(ctx->d_flags, 0, 4096) != cudaSuccess) {
         cudaGetLastError();
@@ -273,6 +410,8 @@ void sgp_destroy(sgp_ctx *ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    graph_release_all(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->d_scratch) cudaFree(ctx->d_scratch);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     if (ctx->d_scan) cudaFree(ctx->d_scan);

@@ -203,6 +203,7 @@ sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *G, const double 
     M->gamma0 = gamma0;
     M->precision = precision;
     M->jac_valid = 0;
+    M->gen = next_generation();
     const int64_t ns = 2 * m;
     SGP_TRY(buf_ensure(ctx, M->ij, sizeof(int32_t) * 2 * m));
     SGP_TRY(buf_ensure(ctx, M->row_ptr, sizeof(int32_t) * (n + 1)));

@@ -403,22 +403,23 @@ __global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n)
 
 // --------------------------------------------------------------------- solve
 // Forward substitution of one level: each receiver q subtracts
-// sum_c L_qc w_c over this level's contributors c (fixed order).
+// sum_c L_qc w_c over this level's contributors c (fixed order).  Lf holds
+// the L blocks in contributor-list order and ctv the contributor vertices,
+// so the level streams both arrays.
 template <typename T>
 __global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
-                           const int32_t *__restrict__ ct, const int32_t *__restrict__ pr_c,
-                           const T *__restrict__ L, int32_t r0, int32_t cnt, T *w, const int *done)
+                           const int32_t *__restrict__ ctv, const T *__restrict__ Lf, int32_t r0,
+                           int32_t cnt, T *w, const int *done)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt || (done && *done)) return;
     int32_t q = rv[r0 + k];
     T s[3] = {0, 0, 0};
     for (int32_t j = rc_ptr[r0 + k]; j < rc_ptr[r0 + k + 1]; ++j) {
-        int32_t p = ct[j];
-        int32_t c = pr_c[p];
+        int32_t c = ctv[j];
         T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
         T y[3];
-        full_mv(L + 9 * (int64_t)p, x, y);
+        full_mv(Lf + 9 * (int64_t)j, x, y);
         s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
     }
     w[3 * (int64_t)q] -= s[0];
@@ -452,22 +453,118 @@ __global__ void k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__res
     w[3 * (int64_t)c + 2] = z[2];
 }
 
+// The last levels (every vertex at elimination position >= P0; at most
+// TREE_TAIL_MAX of them) in one thread block: their vector entries live in
+// shared memory at local index (position - P0), the forward levels run
+// upwards and the backward levels downwards with a barrier between levels.
+struct Tail {
+    int32_t nlev, n, P0, R0, C0, Q0;
+    const int32_t *lvl_pos;   // nlev + 1 absolute positions
+    const int32_t *lvl_rv;    // nlev + 1 absolute receiver-list offsets
+    const int32_t *tq;        // local receiver index per receiver entry (from R0)
+    const int32_t *tc;        // local contributor index per contributor entry (from C0)
+    const int32_t *tb;        // local receiver index per pair (from Q0)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__restrict__ ord,
+                                                    const int32_t *__restrict__ rc_ptr,
+                                                    const int32_t *__restrict__ pr_ptr,
+                                                    const T *__restrict__ Lf, const T *__restrict__ L,
+                                                    const T *__restrict__ Dinv, T *w, const int *done)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    if (done && *done) return;
+    for (int32_t i = threadIdx.x; i < tl.n; i += blockDim.x) {
+        int64_t v = ord[tl.P0 + i];
+        sw[3 * i] = w[3 * v];
+        sw[3 * i + 1] = w[3 * v + 1];
+        sw[3 * i + 2] = w[3 * v + 2];
+    }
+    __syncthreads();
+    for (int l = 0; l < tl.nlev; ++l) {
+        for (int32_t k = tl.lvl_rv[l] + threadIdx.x; k < tl.lvl_rv[l + 1]; k += blockDim.x) {
+            int32_t q = tl.tq[k - tl.R0];
+            T s[3] = {0, 0, 0};
+            for (int32_t j = rc_ptr[k]; j < rc_ptr[k + 1]; ++j) {
+                int32_t c = tl.tc[j - tl.C0];
+                T y[3];
+                full_mv(Lf + 9 * (int64_t)j, sw + 3 * c, y);
+                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+            }
+            sw[3 * q] -= s[0];
+            sw[3 * q + 1] -= s[1];
+            sw[3 * q + 2] -= s[2];
+        }
+        __syncthreads();
+    }
+    for (int l = tl.nlev - 1; l >= 0; --l) {
+        for (int32_t t = tl.lvl_pos[l] + threadIdx.x; t < tl.lvl_pos[l + 1]; t += blockDim.x) {
+            int32_t i = t - tl.P0;
+            T z[3];
+            sym_mv(Dinv + 6 * (int64_t)t, sw + 3 * i, z);
+            for (int32_t p = pr_ptr[t]; p < pr_ptr[t + 1]; ++p) {
+                int32_t q = tl.tb[p - tl.Q0];
+                T u[3];
+                full_mtv(L + 9 * (int64_t)p, sw + 3 * q, u);
+                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+            }
+            sw[3 * i] = z[0];
+            sw[3 * i + 1] = z[1];
+            sw[3 * i + 2] = z[2];
+        }
+        __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < tl.n; i += blockDim.x) {
+        int64_t v = ord[tl.P0 + i];
+        w[3 * v] = sw[3 * i];
+        w[3 * v + 1] = sw[3 * i + 1];
+        w[3 * v + 2] = sw[3 * i + 2];
+    }
+}
+
+static Tail tail_of(const sgp_factor *F)
+{
+    Tail t;
+    t.nlev = F->levels - F->tail_level;
+    t.n = (int32_t)(F->n - F->tail_P0);
+    t.P0 = F->tail_P0;
+    t.R0 = F->tail_R0;
+    t.C0 = F->tail_C0;
+    t.Q0 = F->tail_Q0;
+    const int32_t *tlp = bp<const int32_t>(F->tail_idx);
+    t.lvl_pos = tlp;
+    t.lvl_rv = tlp + (t.nlev + 1);
+    t.tq = bp<const int32_t>(F->tail_q);
+    t.tc = bp<const int32_t>(F->tail_c);
+    t.tb = bp<const int32_t>(F->tail_b);
+    return t;
+}
+
 // In-place P^-1 w (T = double uses the FP64 factor, float the FP32 copies).
 template <typename T>
 sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done)
 {
-    const T *L = reinterpret_cast<const T *>(sizeof(T) == 8 ? F->L.p : F->L32.p);
-    const T *Dinv = reinterpret_cast<const T *>(sizeof(T) == 8 ? F->Dinv.p : F->Dinv32.p);
+    const bool f64 = sizeof(T) == 8;
+    const T *L = reinterpret_cast<const T *>(f64 ? F->L.p : F->L32.p);
+    const T *Lf = reinterpret_cast<const T *>(f64 ? F->Lf.p : F->Lf32.p);
+    const T *Dinv = reinterpret_cast<const T *>(f64 ? F->Dinv.p : F->Dinv32.p);
     const int32_t *rv = bp<const int32_t>(F->rv), *rc = bp<const int32_t>(F->rc_ptr),
-                  *ct = bp<const int32_t>(F->ct), *prc = bp<const int32_t>(F->pr_c),
-                  *ord = bp<const int32_t>(F->ord), *prp = bp<const int32_t>(F->pr_ptr),
-                  *prq = bp<const int32_t>(F->pr_q);
+                  *ctv = bp<const int32_t>(F->ctv), *ord = bp<const int32_t>(F->ord),
+                  *prp = bp<const int32_t>(F->pr_ptr), *prq = bp<const int32_t>(F->pr_q);
     const int B = 128;
-    for (int l = 0; l < F->levels; ++l) {
+    const int lt = F->tail_level;
+    for (int l = 0; l < lt; ++l) {
         int32_t r0 = F->rl_ptr[l], cnt = F->rl_ptr[l + 1] - r0;
-        if (cnt > 0) LAUNCH(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ct, prc, L, r0, cnt, w, done);
+        if (cnt > 0) LAUNCH(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ctv, Lf, r0, cnt, w, done);
     }
-    for (int l = F->levels - 1; l >= 0; --l) {
+    if (lt < F->levels) {
+        const Tail tl = tail_of(F);
+        const size_t smem = sizeof(T) * 3 * (size_t)std::max(tl.n, 1);
+        LAUNCH(ctx, k_tree_tail<T>, 1, 1024, smem, tl, ord, rc, prp, Lf, L, Dinv, w, done);
+    }
+    for (int l = lt - 1; l >= 0; --l) {
         int32_t p0 = F->lvl_ptr[l], cnt = F->lvl_ptr[l + 1] - p0;
         if (cnt > 0) LAUNCH(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
     }
@@ -475,6 +572,41 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
 }
 template sgp_status tree_apply_inplace<double>(sgp_ctx *, const sgp_factor *, double *, const int *);
 template sgp_status tree_apply_inplace<float>(sgp_ctx *, const sgp_factor *, float *, const int *);
+
+// Shared memory of the tail kernel must be opted in above 48 KB, once.
+static sgp_status tail_smem_optin(sgp_ctx *ctx)
+{
+    static int done_dev[64] = {0};
+    if (ctx->device >= 0 && ctx->device < 64 && done_dev[ctx->device]) return SGP_OK;
+    const int bytes = (int)(sizeof(double) * 3 * TREE_TAIL_MAX);
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (ctx->device >= 0 && ctx->device < 64) done_dev[ctx->device] = 1;
+    return SGP_OK;
+}
+
+namespace {
+// Forward-ordered layout: contributor vertex and L block per contributor entry.
+template <typename T>
+__global__ void k_forward_layout(const int32_t *__restrict__ ct, const int32_t *__restrict__ pr_c,
+                                 const double *__restrict__ L, int32_t nct, int32_t *ctv, T *Lf)
+{
+    int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nct) return;
+    int32_t p = ct[j];
+    if (ctv) ctv[j] = pr_c[p];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Lf[9 * (int64_t)j + a] = (T)L[9 * (int64_t)p + a];
+}
+
+// Local (tail) indices: positions minus P0.
+__global__ void k_tail_index(const int32_t *__restrict__ src, const int32_t *__restrict__ pos,
+                             int32_t first, int32_t count, int32_t P0, int32_t *dst)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) dst[k] = pos[src[first + k]] - P0;
+}
+}  // namespace
 
 // ------------------------------------------------------------------- factor
 static sgp_status compact(sgp_ctx *ctx, const int32_t *A, int32_t na, int mode, int32_t level,
@@ -505,9 +637,13 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     F->n = n;
     F->precision = M->precision;
     F->levels = 0;
+    F->gen = next_generation();
     F->rounds = 0;
     F->lvl_ptr.assign(1, 0);
     F->rl_ptr.assign(1, 0);
+    F->pl_ptr.assign(1, 0);
+    F->cl_ptr.assign(1, 0);
+    F->tail_level = 0;
     const size_t n1 = (size_t)n + 1, P = 2 * (size_t)n + 2;
     SGP_TRY(buf_ensure(ctx, F->adj_ptr, sizeof(int32_t) * n1));
     SGP_TRY(buf_ensure(ctx, F->nbr, sizeof(int32_t) * (2 * nt + 1)));
@@ -619,6 +755,8 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
         nrecv += nr;
         F->lvl_ptr.push_back(npos);
         F->rl_ptr.push_back(nrecv);
+        F->pl_ptr.push_back(npair);
+        F->cl_ptr.push_back(ncontrib);
         level++;
         int32_t nalive = 0;
         SGP_TRY(compact(ctx, A, na, 2, level, lev, rflag, flag, tmp, Bl, 0, pos, &nalive));
@@ -656,6 +794,49 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
         LAUNCH(ctx, k_to_f32, grid_for(6 * n, SGP_BLOCK), SGP_BLOCK, 0, bp<const double>(F->Dinv),
                bp<float>(F->Dinv32), 6 * n);
     }
+    // forward-ordered copies for the solve
+    const size_t nct = (size_t)std::max<int32_t>(ncontrib, 1);
+    SGP_TRY(buf_ensure(ctx, F->ctv, sizeof(int32_t) * nct));
+    SGP_TRY(buf_ensure(ctx, F->Lf, sizeof(double) * 9 * nct));
+    LAUNCH(ctx, k_forward_layout<double>, grid_for(ncontrib, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ct,
+           (const int32_t *)pr_c, bp<const double>(F->L), ncontrib, bp<int32_t>(F->ctv), bp<double>(F->Lf));
+    if (F->precision == SGP_PREC_MIXED) {
+        SGP_TRY(buf_ensure(ctx, F->Lf32, sizeof(float) * 9 * nct));
+        LAUNCH(ctx, k_forward_layout<float>, grid_for(ncontrib, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ct,
+               (const int32_t *)pr_c, bp<const double>(F->L), ncontrib, (int32_t *)nullptr,
+               bp<float>(F->Lf32));
+    }
+    // the tail: the first level from which at most TREE_TAIL_MAX vertices remain
+    int lt = 0;
+    while (lt < F->levels && n - F->lvl_ptr[lt] > TREE_TAIL_MAX) ++lt;
+    F->tail_level = lt;
+    if (lt < F->levels) {
+        SGP_TRY(tail_smem_optin(ctx));
+        const int nl = F->levels - lt;
+        F->tail_P0 = F->lvl_ptr[lt];
+        F->tail_R0 = F->rl_ptr[lt];
+        F->tail_C0 = F->cl_ptr[lt];
+        F->tail_Q0 = F->pl_ptr[lt];
+        std::vector<int32_t> idx(2 * (nl + 1));
+        for (int l = 0; l <= nl; ++l) {
+            idx[l] = F->lvl_ptr[lt + l];
+            idx[nl + 1 + l] = F->rl_ptr[lt + l];
+        }
+        SGP_TRY(buf_ensure(ctx, F->tail_idx, sizeof(int32_t) * idx.size()));
+        SGP_CUDA(ctx, cudaMemcpyAsync(F->tail_idx.p, idx.data(), sizeof(int32_t) * idx.size(),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+        const int32_t nq = nrecv - F->tail_R0, nc = ncontrib - F->tail_C0, nb = npair - F->tail_Q0;
+        SGP_TRY(buf_ensure(ctx, F->tail_q, sizeof(int32_t) * std::max(nq, 1)));
+        SGP_TRY(buf_ensure(ctx, F->tail_c, sizeof(int32_t) * std::max(nc, 1)));
+        SGP_TRY(buf_ensure(ctx, F->tail_b, sizeof(int32_t) * std::max(nb, 1)));
+        LAUNCH(ctx, k_tail_index, grid_for(nq, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv,
+               (const int32_t *)pos, F->tail_R0, nq, F->tail_P0, bp<int32_t>(F->tail_q));
+        LAUNCH(ctx, k_tail_index, grid_for(nc, SGP_BLOCK), SGP_BLOCK, 0, bp<const int32_t>(F->ctv),
+               (const int32_t *)pos, F->tail_C0, nc, F->tail_P0, bp<int32_t>(F->tail_c));
+        LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_q,
+               (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_b));
+        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
+    }
     int herr = 0;
     SGP_TRY(read_back(ctx, &herr, err, sizeof(int)));
     if (herr) return sgp_fail(ctx, SGP_ERR_NOT_SPD, "tree_factor: a pivot block is not positive definite");
@@ -688,7 +869,8 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->Dinv, &F->L32, &F->Dinv32, &F->work, &F->adj_ptr, &F->nbr, &F->twin,
                     &F->eref, &F->deg, &F->lev, &F->nrec, &F->rq, &F->re, &F->ren, &F->pos,
                     &F->flag, &F->alive_a, &F->alive_b, &F->acc, &F->fill, &F->sbuf, &F->tmp,
-                    &F->rflag, &F->cnt};
+                    &F->rflag, &F->cnt, &F->ctv, &F->Lf, &F->Lf32, &F->tail_idx, &F->tail_q,
+                    &F->tail_c, &F->tail_b};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete F;

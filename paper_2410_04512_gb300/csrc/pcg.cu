@@ -86,19 +86,58 @@ __global__ void k_spmv(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, 
 }
 
 // PCG product q = Gamma p with p^T q; the last block sets alpha = rho / p^T q.
-template <typename T>
-__global__ void k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, int64_t n,
-                          const T *__restrict__ p, T *q, double *partials, Scal *sc)
+// LPR lanes share a block row: lane g takes the row's slots g, g+LPR, ...,
+// so a warp's 16-byte block loads cover a contiguous stretch of the slot
+// array; the lanes' partial sums meet by shuffles.  The difference form is
+// accumulated with fused multiply-adds (9 FMA + 3 subtractions per slot).
+// Loops are warp-uniform so the shuffles always see all 32 lanes.
+template <typename T, int LPR>
+__global__ void __launch_bounds__(RB) k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0,
+                                                int64_t n, const T *__restrict__ p, T *q, double *partials,
+                                                Scal *sc)
 {
     __shared__ double sh[RB / 32];
     if (sc->done) return;
+    constexpr int RPW = 32 / LPR;  // rows per warp per sweep
+    const int lane = threadIdx.x & 31, g = lane % LPR;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        T vi[3], yi[3];
-        row_product(B, row_ptr, gamma0, p, i, vi, yi);
-        q[3 * i] = yi[0]; q[3 * i + 1] = yi[1]; q[3 * i + 2] = yi[2];
-        acc += (double)vi[0] * (double)yi[0] + (double)vi[1] * (double)yi[1] + (double)vi[2] * (double)yi[2];
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
+        const int64_t i = base + lane / LPR;
+        const bool active = i < n;
+        T y0 = 0, y1 = 0, y2 = 0, v0 = 0, v1 = 0, v2 = 0;
+        if (active) {
+            v0 = p[3 * i]; v1 = p[3 * i + 1]; v2 = p[3 * i + 2];
+            const int32_t s1 = row_ptr[i + 1];
+            for (int32_t s = row_ptr[i] + g; s < s1; s += LPR) {
+                T S[6];
+                int32_t j;
+                B.load(s, S, j);
+                const T d0 = v0 - p[3 * (int64_t)j], d1 = v1 - p[3 * (int64_t)j + 1],
+                        d2 = v2 - p[3 * (int64_t)j + 2];
+                y0 = fma(S[0], d0, y0); y0 = fma(S[1], d1, y0); y0 = fma(S[2], d2, y0);
+                y1 = fma(S[1], d0, y1); y1 = fma(S[3], d1, y1); y1 = fma(S[4], d2, y1);
+                y2 = fma(S[2], d0, y2); y2 = fma(S[4], d1, y2); y2 = fma(S[5], d2, y2);
+            }
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+        }
+        if (active) {
+            y0 = fma(gamma0, v0, y0);
+            y1 = fma(gamma0, v1, y1);
+            y2 = fma(gamma0, v2, y2);
+            if (LPR >= 3) {
+                if (g < 3) q[3 * i + g] = g == 0 ? y0 : (g == 1 ? y1 : y2);
+            } else if (g == 0) {
+                q[3 * i] = y0; q[3 * i + 1] = y1; q[3 * i + 2] = y2;
+            }
+            if (g == 0) acc += (double)v0 * (double)y0 + (double)v1 * (double)y1 + (double)v2 * (double)y2;
+        }
     }
     double s = block_sum<RB>(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -358,6 +397,27 @@ __global__ void k_accumulate(int64_t n3, const float *__restrict__ d, double sca
 // ---------------------------------------------------------------------------
 namespace {
 
+// Lanes per block row of the product: 4 unless SGP_SPMV_LPR says 1, 2 or 8.
+template <typename T>
+sgp_status launch_spmv_pq(sgp_ctx *ctx, Blk<T> B, const int32_t *row_ptr, T g0, int64_t n, const T *p,
+                          T *q, double *partials, Scal *sc)
+{
+    const int lpr = ctx->spmv_lpr > 0 ? ctx->spmv_lpr : 4;
+    const int64_t want = (n * lpr + RB - 1) / RB;
+    auto go = [&](auto kern) -> sgp_status {
+        unsigned G;
+        SGP_TRY(resident_grid(ctx, (const void *)kern, RB, want, &G));
+        LAUNCH(ctx, kern, G, RB, 0, B, row_ptr, g0, n, p, q, partials, sc);
+        return SGP_OK;
+    };
+    switch (lpr) {
+    case 1: return go(k_spmv_pq<T, 1>);
+    case 2: return go(k_spmv_pq<T, 2>);
+    case 8: return go(k_spmv_pq<T, 8>);
+    default: return go(k_spmv_pq<T, 4>);
+    }
+}
+
 static unsigned red_grid(int64_t n)
 {
     int64_t g = (n + RB - 1) / RB;
@@ -420,11 +480,12 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
         SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
     }
     LAUNCH(ctx, k_rz_init<T>, G, RB, 0, n, (const T *)r, (const T *)w, p, partials, sc);
-    const int chunk = 16;
-    for (;;) {
-        for (int it = 0; it < chunk; ++it) {
+    // One PCG iteration per call; kernels return at once after convergence.
+    auto iterate = [&](int count) -> sgp_status {
+        cudaEvent_t ev;
+        for (int it = 0; it < count; ++it) {
             SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
-            LAUNCH(ctx, k_spmv_pq<T>, G, RB, 0, B, row_ptr, g0, n, (const T *)p, q, partials, sc);
+            SGP_TRY(launch_spmv_pq<T>(ctx, B, row_ptr, g0, n, (const T *)p, q, partials, sc));
             SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
             SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
             if (precond == SGP_PRECOND_TREE)
@@ -449,7 +510,32 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
             LAUNCH(ctx, k_pupd<T>, G, RB, 0, n, (const T *)w, p, (const Scal *)sc);
             SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
         }
+        return SGP_OK;
+    };
+    const int chunk = 8;
+    if (!ctx->use_graphs) {
+        for (;;) {
+            SGP_TRY(iterate(chunk));
+            SGP_TRY(read_back(ctx, hs, sc, sizeof(Scal)));
+            if (hs->done) break;
+        }
+        return SGP_OK;
+    }
+    // Chunks of iterations are captured once into a CUDA graph and replayed;
+    // the graph is keyed by everything its nodes point at.
+    const uint64_t key[] = {(uint64_t)sizeof(T), (uint64_t)sizeof(X), (uint64_t)precond, (uint64_t)n,
+                            M->gen, Fac ? Fac->gen : 0ull, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)r,
+                            (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q, (uint64_t)(uintptr_t)w,
+                            (uint64_t)(uintptr_t)partials, (uint64_t)(uintptr_t)sc,
+                            (uint64_t)(uintptr_t)jac, (uint64_t)ctx->timing, (uint64_t)chunk};
+    GraphEntry *ge = nullptr;
+    SGP_TRY(graph_lookup(ctx, key, sizeof(key) / sizeof(key[0]), &ge));
+    if (!ge->exec) SGP_TRY(graph_capture(ctx, ge, [&]() { return iterate(chunk); }));
+    for (;;) {
+        SGP_CUDA(ctx, cudaGraphLaunch(ge->exec, ctx->stream));
+        ctx->launches += ge->kernels;
         SGP_TRY(read_back(ctx, hs, sc, sizeof(Scal)));
+        SGP_TRY(graph_collect_timing(ctx, ge));
         if (hs->done) break;
     }
     return SGP_OK;

@@ -22,6 +22,21 @@
 // ---------------------------------------------------------------------------
 // host side: context, errors, launches, buffers
 // ---------------------------------------------------------------------------
+struct KtRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+// A captured chunk of solver work, replayed with cudaGraphLaunch.
+struct GraphEntry {
+    uint64_t key[32];
+    int nkey = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;          // kernel nodes per replay
+    std::vector<KtRec> ev;        // timing events recorded by the graph
+    uint64_t last_use = 0;
+};
+
 struct sgp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -44,7 +59,41 @@ struct sgp_ctx {
     // scan workspace (grows; only the scan touches it)
     void *d_scan = nullptr;
     size_t d_scan_bytes = 0;
+    // tuning knobs (0 = built-in default)
+    int spmv_lpr = 0;
+    int num_sms = 0;
+    std::vector<std::pair<const void *, int>> occupancy;  // kernel -> resident blocks/SM
+    // CUDA graphs of solver chunks (captured on a private stream)
+    int use_graphs = 1;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<KtRec> *capture_sink = nullptr;
+    std::vector<GraphEntry *> graphs;
+    uint64_t graph_clock = 0;
 };
+
+// Grid of at most one full wave: min(want, SMs x resident blocks per SM of
+// `kernel` at `block` threads), cached per kernel.
+sgp_status resident_grid(sgp_ctx *ctx, const void *kernel, int block, int64_t want, unsigned *grid);
+
+// Unique generation numbers for rebuilt handles (graph cache keys).
+uint64_t next_generation();
+sgp_status graph_lookup(sgp_ctx *ctx, const uint64_t *key, int nkey, GraphEntry **out);
+sgp_status graph_begin(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t *saved, int64_t *l0);
+sgp_status graph_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l0, sgp_status st);
+sgp_status graph_collect_timing(sgp_ctx *ctx, GraphEntry *ge);
+void graph_release_all(sgp_ctx *ctx);
+
+// Capture the work `fn` enqueues on ctx->stream into ge->exec.
+template <typename Fn>
+sgp_status graph_capture(sgp_ctx *ctx, GraphEntry *ge, Fn fn)
+{
+    cudaStream_t saved;
+    int64_t l0;
+    sgp_status st = graph_begin(ctx, ge, &saved, &l0);
+    if (st != SGP_OK) return st;
+    st = fn();
+    return graph_end(ctx, ge, saved, l0, st);
+}
 
 sgp_status sgp_fail(sgp_ctx *ctx, sgp_status code, const char *fmt, ...);
 
@@ -120,6 +169,7 @@ struct sgp_graph {
 };
 
 struct sgp_matrix {
+    uint64_t gen = 0;
     int64_t n = 0, m = 0;
     double gamma0 = 0;
     int32_t precision = SGP_PREC_F64;
@@ -145,11 +195,14 @@ struct sgp_tree {
 };
 
 struct sgp_factor {
+    uint64_t gen = 0;
     int64_t n = 0, npairs = 0;
     int32_t rounds = 0, levels = 0;
     int32_t precision = SGP_PREC_F64;
     std::vector<int32_t> lvl_ptr;   // host, levels + 1: positions of each level in ord
     std::vector<int32_t> rl_ptr;    // host, levels + 1: receivers of each level in rv
+    std::vector<int32_t> pl_ptr;    // host, levels + 1: pairs of each level
+    std::vector<int32_t> cl_ptr;    // host, levels + 1: contributor entries of each level
     DBuf ord;       // n int32 vertex eliminated at each position
     DBuf pr_ptr;    // n + 1 int32 pairs (receivers) of each position
     DBuf pr_q;      // npairs int32 receiver vertex of each pair
@@ -159,6 +212,12 @@ struct sgp_factor {
     DBuf ct;        // npairs int32 pair ids grouped by receiver
     DBuf L, Dinv;   // npairs x full9, n x sym6 (by position), float64
     DBuf L32, Dinv32;
+    DBuf ctv;       // contributor vertex per contributor entry (ct order)
+    DBuf Lf, Lf32;  // L blocks in ct order (forward pass streams them)
+    // tail: levels >= tail_level run in one thread block (positions >= tail_P0)
+    int32_t tail_level = 0, tail_P0 = 0, tail_R0 = 0, tail_C0 = 0, tail_Q0 = 0;
+    DBuf tail_idx;  // level positions and receiver offsets of the tail levels
+    DBuf tail_q, tail_c, tail_b;  // local indices (position - tail_P0)
     DBuf work;      // n x 3 float64 apply workspace
     // structure-simulation scratch
     DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,
@@ -169,6 +228,9 @@ struct sgp_factor {
 // device helpers
 // ---------------------------------------------------------------------------
 #define SGP_BLOCK 256
+// Largest number of vertices the single-block tail of the tree solve holds
+// in shared memory (3 x 8 B x 8192 = 192 KB for FP64).
+#define TREE_TAIL_MAX 8192
 
 // sym6 y = S x
 template <typename T, typename U>
