@@ -10,17 +10,18 @@
 //     A_qq     -= A_qc D_c^-1 A_cq             (Schur complement)
 //     A_q0q1    = -A_q0c D_c^-1 A_cq1          (fill, only when c had two neighbours)
 // Algorithm 2 eliminates children before parents, one vertex at a time.  Here
-// a round eliminates every leaf at once (rake), then an independent set of
+// each level eliminates, at once, every leaf (rake) and an independent set of
 // degree-2 vertices (compress, each splicing its two neighbours together with
-// the fill block).  The set of compressed vertices is the local minima of a
-// per-round hash among degree-2 neighbours, so chains shrink by a constant
-// fraction per round and any tree needs O(log n) rounds.  Every elimination
+// the fill block): the degree-2 vertices without a leaf neighbour that are
+// local minima of a per-level hash among their degree-2 neighbours.  Chains
+// shrink by a constant fraction per level, so any tree needs O(log n) levels
+// (about 23 for the spanning tree of a 1e6-cell spheroid).  Every elimination
 // keeps the graph a forest, so the factor is exact: P^-1 is the same operator
 // as with the paper's order (only rounding differs).
 //
 // Structure (which vertex goes when, with which neighbours) is computed first
-// with integer kernels, level by level (a level = the rake or the compress half
-// of a round).  The numeric factorisation then replays the levels; the solve
+// with integer kernels, level by level.  The numeric factorisation then
+// replays the levels; the solve
 // replays them forward (receivers gather L_qc z_c) and backward (each
 // eliminated vertex gathers from its receivers).  All sums run in a fixed
 // order, so results are bitwise reproducible.
@@ -135,58 +136,51 @@ struct Sim {
     int2 *rq, *re, *ren;
 };
 
-// Rake: every alive vertex of degree 0 (final) or 1 (leaf).  Of two adjacent
-// leaves (a two-vertex tree) only the larger id goes.
-__global__ void k_select_rake(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level)
+// One level eliminating rake and compress candidates together: every
+// vertex of degree 0, every leaf (of two adjacent leaves only the larger
+// id), and every degree-2 vertex that has no leaf neighbour and beats its
+// degree-2 neighbours by the level's hash.  No two chosen vertices are
+// adjacent, and each has at most two neighbours, so eliminating them all at
+// once equals eliminating them one by one: the forest stays a forest.
+__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= na) return;
-    int32_t v = A[k];
-    int32_t d = S.deg[v];
+    const int32_t v = A[k];
+    const int32_t d = S.deg[v];
     if (d == 0) {
         S.lev[v] = level;
         S.nrec[v] = 0;
-    } else if (d == 1) {
-        int32_t e = -1;
-        for (int32_t s = S.adj_ptr[v]; s < S.adj_ptr[v + 1]; ++s)
-            if (S.nbr[s] >= 0) { e = s; break; }
-        int32_t a = S.nbr[e];
-        if (S.deg[a] == 1 && a > v) return;
-        S.lev[v] = level;
-        S.nrec[v] = 1;
-        S.rq[v] = make_int2(a, -1);
-        S.re[v] = make_int2(S.eref[e], -1);
-        S.ren[v] = make_int2(e, -1);
+        return;
     }
-}
-
-// Compress: alive degree-2 vertices that beat both neighbours which are
-// themselves of degree 2 (an independent set).
-__global__ void k_select_compress(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level,
-                                  uint32_t salt)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= na) return;
-    int32_t v = A[k];
-    if (S.lev[v] != -1 || S.deg[v] != 2) return;
+    if (d > 2) return;
     int32_t e1 = -1, e2 = -1;
     for (int32_t s = S.adj_ptr[v]; s < S.adj_ptr[v + 1]; ++s)
         if (S.nbr[s] >= 0) {
             if (e1 < 0) e1 = s;
             else { e2 = s; break; }
         }
-    int32_t a = S.nbr[e1], b = S.nbr[e2];
-    if (S.deg[a] == 2 && key_less(a, v, salt)) return;
-    if (S.deg[b] == 2 && key_less(b, v, salt)) return;
-    if (a > b) {
-        int32_t t = a; a = b; b = t;
-        t = e1; e1 = e2; e2 = t;
+    const int32_t a = S.nbr[e1];
+    if (d == 1) {
+        if (S.deg[a] == 1 && a > v) return;
+        S.lev[v] = level;
+        S.nrec[v] = 1;
+        S.rq[v] = make_int2(a, -1);
+        S.re[v] = make_int2(S.eref[e1], -1);
+        S.ren[v] = make_int2(e1, -1);
+        return;
     }
+    const int32_t b = S.nbr[e2];
+    const int32_t da = S.deg[a], db = S.deg[b];
+    if (da == 1 || db == 1) return;
+    if (da == 2 && key_less(a, v, salt)) return;
+    if (db == 2 && key_less(b, v, salt)) return;
+    const bool sw = a > b;
     S.lev[v] = level;
     S.nrec[v] = 2;
-    S.rq[v] = make_int2(a, b);
-    S.re[v] = make_int2(S.eref[e1], S.eref[e2]);
-    S.ren[v] = make_int2(e1, e2);
+    S.rq[v] = sw ? make_int2(b, a) : make_int2(a, b);
+    S.re[v] = sw ? make_int2(S.eref[e2], S.eref[e1]) : make_int2(S.eref[e1], S.eref[e2]);
+    S.ren[v] = sw ? make_int2(e2, e1) : make_int2(e1, e2);
 }
 
 // ----------------------------------------------------- structure: bookkeeping
@@ -270,31 +264,27 @@ __global__ void k_contrib(Sim S, const int32_t *__restrict__ rv, int32_t r0, int
     if (!FILL) count[k] = c_n;
 }
 
-__global__ void k_apply_rake(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt)
+// Structural update of a merged level: a leaf leaves its neighbour's list;
+// a degree-2 vertex splices its two neighbours together (fill edge nt + v).
+__global__ void k_apply(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt, int32_t nt)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt) return;
-    int32_t v = ord[p0 + k];
-    if (S.nrec[v] != 1) return;
-    int32_t t = S.twin[S.ren[v].x];
-    S.nbr[t] = -1;
-    atomicSub(S.deg + S.rq[v].x, 1);
-}
-
-__global__ void k_apply_compress(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt,
-                                 int32_t nt)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cnt) return;
-    int32_t v = ord[p0 + k];
-    int2 q = S.rq[v], en = S.ren[v];
-    int32_t ta = S.twin[en.x], tb = S.twin[en.y];
-    S.nbr[ta] = q.y;
-    S.nbr[tb] = q.x;
-    S.twin[ta] = tb;
-    S.twin[tb] = ta;
-    S.eref[ta] = nt + v;
-    S.eref[tb] = nt + v;
+    const int32_t v = ord[p0 + k];
+    const int32_t r = S.nrec[v];
+    if (r == 1) {
+        S.nbr[S.twin[S.ren[v].x]] = -1;
+        atomicSub(S.deg + S.rq[v].x, 1);
+    } else if (r == 2) {
+        int2 q = S.rq[v], en = S.ren[v];
+        int32_t ta = S.twin[en.x], tb = S.twin[en.y];
+        S.nbr[ta] = q.y;
+        S.nbr[tb] = q.x;
+        S.twin[ta] = tb;
+        S.twin[tb] = ta;
+        S.eref[ta] = nt + v;
+        S.eref[tb] = nt + v;
+    }
 }
 
 // ------------------------------------------------------------------ numerics
@@ -402,6 +392,12 @@ __global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n)
 }  // namespace
 
 // --------------------------------------------------------------------- solve
+// Programmatic dependent launch: a level kernel lets the next one start its
+// prologue at once (launch_dependents) and waits for the previous level's
+// results (wait) only before it touches the solution vector.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Forward substitution of one level: each receiver q subtracts
 // sum_c L_qc w_c over this level's contributors c (fixed order).  Lf holds
 // the L blocks in contributor-list order and ctv the contributor vertices,
@@ -411,11 +407,24 @@ __global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__rest
                            const int32_t *__restrict__ ctv, const T *__restrict__ Lf, int32_t r0,
                            int32_t cnt, T *w, const int *done)
 {
+    pdl_trigger();
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt || (done && *done)) return;
-    int32_t q = rv[r0 + k];
-    T s[3] = {0, 0, 0};
-    for (int32_t j = rc_ptr[r0 + k]; j < rc_ptr[r0 + k + 1]; ++j) {
+    const int32_t q = rv[r0 + k];
+    const int32_t j0 = rc_ptr[r0 + k], j1 = rc_ptr[r0 + k + 1];
+    // the first contributor's block and vertex do not depend on the
+    // previous level: load them before waiting
+    T L0[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) L0[a] = Lf[9 * (int64_t)j0 + a];
+    const int32_t c0 = ctv[j0];
+    pdl_wait();
+    T s[3];
+    {
+        T x[3] = {w[3 * (int64_t)c0], w[3 * (int64_t)c0 + 1], w[3 * (int64_t)c0 + 2]};
+        full_mv(L0, x, s);
+    }
+    for (int32_t j = j0 + 1; j < j1; ++j) {
         int32_t c = ctv[j];
         T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
         T y[3];
@@ -434,15 +443,22 @@ __global__ void k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__res
                            const int32_t *__restrict__ pr_q, const T *__restrict__ L,
                            const T *__restrict__ Dinv, int32_t p0, int32_t cnt, T *w, const int *done)
 {
+    pdl_trigger();
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt || (done && *done)) return;
-    int32_t t = p0 + k;
-    int32_t c = ord[t];
+    const int32_t t = p0 + k;
+    const int32_t c = ord[t];
+    const int32_t pa = pr_ptr[t], pb = pr_ptr[t + 1];
+    T Di[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Di[a] = Dinv[6 * (int64_t)t + a];
+    const int32_t q0 = pa < pb ? pr_q[pa] : 0;
+    pdl_wait();
     T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
     T z[3];
-    sym_mv(Dinv + 6 * (int64_t)t, x, z);
-    for (int32_t p = pr_ptr[t]; p < pr_ptr[t + 1]; ++p) {
-        int32_t q = pr_q[p];
+    sym_mv(Di, x, z);
+    for (int32_t p = pa; p < pb; ++p) {
+        int32_t q = p == pa ? q0 : pr_q[p];
         T y[3] = {w[3 * (int64_t)q], w[3 * (int64_t)q + 1], w[3 * (int64_t)q + 2]};
         T u[3];
         full_mtv(L + 9 * (int64_t)p, y, u);
@@ -453,29 +469,65 @@ __global__ void k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__res
     w[3 * (int64_t)c + 2] = z[2];
 }
 
-// The last levels (every vertex at elimination position >= P0; at most
-// TREE_TAIL_MAX of them) in one thread block: their vector entries live in
-// shared memory at local index (position - P0), the forward levels run
-// upwards and the backward levels downwards with a barrier between levels.
+// The last levels (the vertices at elimination positions >= P0) in one
+// thread block with every array they use staged in shared memory: vectors,
+// D^-1 and L blocks by local index (position - P0, pair - Q0), and the local
+// index lists built at factorisation time.  Levels are separated by block
+// barriers; forward upwards, then backward downwards.
 struct Tail {
-    int32_t nlev, n, P0, R0, C0, Q0;
+    int32_t nlev, n, np, nr, P0, Q0, R0, C0;
     const int32_t *lvl_pos;   // nlev + 1 absolute positions
     const int32_t *lvl_rv;    // nlev + 1 absolute receiver-list offsets
-    const int32_t *tq;        // local receiver index per receiver entry (from R0)
-    const int32_t *tc;        // local contributor index per contributor entry (from C0)
-    const int32_t *tb;        // local receiver index per pair (from Q0)
+    const int32_t *tq;        // nr: local receiver of each receiver entry
+    const int32_t *tb;        // np: local receiver of each pair
+    const int32_t *tpc;       // np: local contributor of each pair
+    const int32_t *tct;       // np: local pair of each contributor entry
 };
+
+__host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename T>
+__host__ __device__ inline size_t tail_smem_bytes(int32_t n, int32_t np, int32_t nr)
+{
+    return tail_align(sizeof(T) * 9 * (size_t)n) + tail_align(sizeof(T) * 9 * (size_t)np) +
+           tail_align(4 * (size_t)(n + 1)) + 3 * tail_align(4 * (size_t)np) + tail_align(4 * (size_t)(nr + 1)) +
+           tail_align(4 * (size_t)nr);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__restrict__ ord,
                                                     const int32_t *__restrict__ rc_ptr,
                                                     const int32_t *__restrict__ pr_ptr,
-                                                    const T *__restrict__ Lf, const T *__restrict__ L,
-                                                    const T *__restrict__ Dinv, T *w, const int *done)
+                                                    const T *__restrict__ L, const T *__restrict__ Dinv,
+                                                    T *w, const int *done)
 {
-    extern __shared__ unsigned char smem_raw[];
-    T *sw = reinterpret_cast<T *>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     if (done && *done) return;
+    unsigned char *cur = smem_raw;
+    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
+    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 9 * tl.n));  // w (3) then D^-1 (6) per vertex
+    T *sD = sw + 3 * tl.n;
+    T *sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * tl.np));
+    int32_t *spr = reinterpret_cast<int32_t *>(take(4 * (tl.n + 1)));
+    int32_t *stb = reinterpret_cast<int32_t *>(take(4 * tl.np));
+    int32_t *spc = reinterpret_cast<int32_t *>(take(4 * tl.np));
+    int32_t *sct = reinterpret_cast<int32_t *>(take(4 * tl.np));
+    int32_t *src = reinterpret_cast<int32_t *>(take(4 * (tl.nr + 1)));
+    int32_t *stq = reinterpret_cast<int32_t *>(take(4 * tl.nr));
+    (void)take(0);
+    // stage the factor (independent of the previous kernel)
+    for (int32_t i = threadIdx.x; i < 6 * tl.n; i += blockDim.x) sD[i] = Dinv[6 * (int64_t)tl.P0 + i];
+    for (int32_t i = threadIdx.x; i < 9 * tl.np; i += blockDim.x) sL[i] = L[9 * (int64_t)tl.Q0 + i];
+    for (int32_t i = threadIdx.x; i <= tl.n; i += blockDim.x) spr[i] = pr_ptr[tl.P0 + i] - tl.Q0;
+    for (int32_t i = threadIdx.x; i < tl.np; i += blockDim.x) {
+        stb[i] = tl.tb[i];
+        spc[i] = tl.tpc[i];
+        sct[i] = tl.tct[i];
+    }
+    for (int32_t i = threadIdx.x; i <= tl.nr; i += blockDim.x) src[i] = rc_ptr[tl.R0 + i] - tl.C0;
+    for (int32_t i = threadIdx.x; i < tl.nr; i += blockDim.x) stq[i] = tl.tq[i];
+    pdl_wait();
     for (int32_t i = threadIdx.x; i < tl.n; i += blockDim.x) {
         int64_t v = ord[tl.P0 + i];
         sw[3 * i] = w[3 * v];
@@ -484,15 +536,16 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
     }
     __syncthreads();
     for (int l = 0; l < tl.nlev; ++l) {
-        for (int32_t k = tl.lvl_rv[l] + threadIdx.x; k < tl.lvl_rv[l + 1]; k += blockDim.x) {
-            int32_t q = tl.tq[k - tl.R0];
+        const int32_t k0 = tl.lvl_rv[l] - tl.R0, k1 = tl.lvl_rv[l + 1] - tl.R0;
+        for (int32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             T s[3] = {0, 0, 0};
-            for (int32_t j = rc_ptr[k]; j < rc_ptr[k + 1]; ++j) {
-                int32_t c = tl.tc[j - tl.C0];
+            for (int32_t j = src[k]; j < src[k + 1]; ++j) {
+                const int32_t p = sct[j];
                 T y[3];
-                full_mv(Lf + 9 * (int64_t)j, sw + 3 * c, y);
+                full_mv(sL + 9 * p, sw + 3 * spc[p], y);
                 s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
             }
+            const int32_t q = stq[k];
             sw[3 * q] -= s[0];
             sw[3 * q + 1] -= s[1];
             sw[3 * q + 2] -= s[2];
@@ -500,14 +553,13 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
         __syncthreads();
     }
     for (int l = tl.nlev - 1; l >= 0; --l) {
-        for (int32_t t = tl.lvl_pos[l] + threadIdx.x; t < tl.lvl_pos[l + 1]; t += blockDim.x) {
-            int32_t i = t - tl.P0;
+        const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
+        for (int32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             T z[3];
-            sym_mv(Dinv + 6 * (int64_t)t, sw + 3 * i, z);
-            for (int32_t p = pr_ptr[t]; p < pr_ptr[t + 1]; ++p) {
-                int32_t q = tl.tb[p - tl.Q0];
+            sym_mv(sD + 6 * i, sw + 3 * i, z);
+            for (int32_t p = spr[i]; p < spr[i + 1]; ++p) {
                 T u[3];
-                full_mtv(L + 9 * (int64_t)p, sw + 3 * q, u);
+                full_mtv(sL + 9 * p, sw + 3 * stb[p], u);
                 z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
             }
             sw[3 * i] = z[0];
@@ -529,16 +581,19 @@ static Tail tail_of(const sgp_factor *F)
     Tail t;
     t.nlev = F->levels - F->tail_level;
     t.n = (int32_t)(F->n - F->tail_P0);
+    t.np = (int32_t)(F->npairs - F->tail_Q0);
+    t.nr = F->rl_ptr[F->levels] - F->tail_R0;
     t.P0 = F->tail_P0;
+    t.Q0 = F->tail_Q0;
     t.R0 = F->tail_R0;
     t.C0 = F->tail_C0;
-    t.Q0 = F->tail_Q0;
     const int32_t *tlp = bp<const int32_t>(F->tail_idx);
     t.lvl_pos = tlp;
     t.lvl_rv = tlp + (t.nlev + 1);
     t.tq = bp<const int32_t>(F->tail_q);
-    t.tc = bp<const int32_t>(F->tail_c);
     t.tb = bp<const int32_t>(F->tail_b);
+    t.tpc = bp<const int32_t>(F->tail_c);
+    t.tct = bp<const int32_t>(F->tail_c) + t.np;
     return t;
 }
 
@@ -557,28 +612,28 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
     const int lt = F->tail_level;
     for (int l = 0; l < lt; ++l) {
         int32_t r0 = F->rl_ptr[l], cnt = F->rl_ptr[l + 1] - r0;
-        if (cnt > 0) LAUNCH(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ctv, Lf, r0, cnt, w, done);
+        if (cnt > 0) LAUNCH_PDL(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ctv, Lf, r0, cnt, w, done);
     }
     if (lt < F->levels) {
         const Tail tl = tail_of(F);
-        const size_t smem = sizeof(T) * 3 * (size_t)std::max(tl.n, 1);
-        LAUNCH(ctx, k_tree_tail<T>, 1, 1024, smem, tl, ord, rc, prp, Lf, L, Dinv, w, done);
+        const size_t smem = tail_smem_bytes<T>(tl.n, tl.np, tl.nr);
+        LAUNCH_PDL(ctx, k_tree_tail<T>, 1, 1024, smem, tl, ord, rc, prp, L, Dinv, w, done);
     }
     for (int l = lt - 1; l >= 0; --l) {
         int32_t p0 = F->lvl_ptr[l], cnt = F->lvl_ptr[l + 1] - p0;
-        if (cnt > 0) LAUNCH(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
+        if (cnt > 0) LAUNCH_PDL(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
     }
     return SGP_OK;
 }
 template sgp_status tree_apply_inplace<double>(sgp_ctx *, const sgp_factor *, double *, const int *);
 template sgp_status tree_apply_inplace<float>(sgp_ctx *, const sgp_factor *, float *, const int *);
 
-// Shared memory of the tail kernel must be opted in above 48 KB, once.
+// Shared memory of the tail kernel must be opted in above 48 KB, once per device.
 static sgp_status tail_smem_optin(sgp_ctx *ctx)
 {
     static int done_dev[64] = {0};
     if (ctx->device >= 0 && ctx->device < 64 && done_dev[ctx->device]) return SGP_OK;
-    const int bytes = (int)(sizeof(double) * 3 * TREE_TAIL_MAX);
+    const int bytes = TREE_TAIL_SMEM;
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (ctx->device >= 0 && ctx->device < 64) done_dev[ctx->device] = 1;
@@ -605,6 +660,14 @@ __global__ void k_tail_index(const int32_t *__restrict__ src, const int32_t *__r
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < count) dst[k] = pos[src[first + k]] - P0;
+}
+
+// Local pair of each tail contributor entry.
+__global__ void k_tail_pairs(const int32_t *__restrict__ ct, int32_t first, int32_t count, int32_t Q0,
+                             int32_t *dst)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) dst[k] = ct[first + k] - Q0;
 }
 }  // namespace
 
@@ -709,18 +772,12 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     for (int phase = 0; na > 0; ++phase) {
         if (phase > max_phases)
             return sgp_fail(ctx, SGP_ERR_TIMEOUT, "tree_factor: contraction did not finish");
-        const bool rake = (phase % 2) == 0;
-        if (rake) {
-            LAUNCH(ctx, k_select_rake, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level);
-            F->rounds++;
-        } else {
-            uint32_t salt = 0x9E3779B9u * (uint32_t)(phase / 2 + 1);
-            LAUNCH(ctx, k_select_compress, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A,
-                   na, level, salt);
-        }
+        const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
+        LAUNCH(ctx, k_select, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt);
+        F->rounds++;
         int32_t ne = 0;
         SGP_TRY(compact(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, &ne));
-        if (ne == 0) continue;
+        if (ne == 0) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
         // pairs (receivers) of the eliminated vertices
         LAUNCH(ctx, k_level_nrec, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, npos, ne,
                (const int32_t *)nrec, flag);
@@ -748,8 +805,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
             ncontrib += lc;
         }
         // structural update
-        if (rake) LAUNCH(ctx, k_apply_rake, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)ord, npos, ne);
-        else LAUNCH(ctx, k_apply_compress, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)ord, npos, ne, (int32_t)nt);
+        LAUNCH(ctx, k_apply, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)ord, npos, ne, (int32_t)nt);
         npos += ne;
         npair += lp;
         nrecv += nr;
@@ -806,9 +862,13 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
                (const int32_t *)pr_c, bp<const double>(F->L), ncontrib, (int32_t *)nullptr,
                bp<float>(F->Lf32));
     }
-    // the tail: the first level from which at most TREE_TAIL_MAX vertices remain
+    // the tail: the first level from which everything left fits in the
+    // tail kernel's shared memory
     int lt = 0;
-    while (lt < F->levels && n - F->lvl_ptr[lt] > TREE_TAIL_MAX) ++lt;
+    while (lt < F->levels &&
+           tail_smem_bytes<double>((int32_t)(n - F->lvl_ptr[lt]), npair - F->pl_ptr[lt],
+                                   nrecv - F->rl_ptr[lt]) > (size_t)TREE_TAIL_SMEM)
+        ++lt;
     F->tail_level = lt;
     if (lt < F->levels) {
         SGP_TRY(tail_smem_optin(ctx));
@@ -825,16 +885,20 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
         SGP_TRY(buf_ensure(ctx, F->tail_idx, sizeof(int32_t) * idx.size()));
         SGP_CUDA(ctx, cudaMemcpyAsync(F->tail_idx.p, idx.data(), sizeof(int32_t) * idx.size(),
                                       cudaMemcpyHostToDevice, ctx->stream));
+        // every pair of the tail is one contributor entry of the tail
         const int32_t nq = nrecv - F->tail_R0, nc = ncontrib - F->tail_C0, nb = npair - F->tail_Q0;
+        if (nc != nb) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent tail (%d/%d)", nc, nb);
         SGP_TRY(buf_ensure(ctx, F->tail_q, sizeof(int32_t) * std::max(nq, 1)));
-        SGP_TRY(buf_ensure(ctx, F->tail_c, sizeof(int32_t) * std::max(nc, 1)));
+        SGP_TRY(buf_ensure(ctx, F->tail_c, sizeof(int32_t) * 2 * std::max(nb, 1)));
         SGP_TRY(buf_ensure(ctx, F->tail_b, sizeof(int32_t) * std::max(nb, 1)));
         LAUNCH(ctx, k_tail_index, grid_for(nq, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv,
                (const int32_t *)pos, F->tail_R0, nq, F->tail_P0, bp<int32_t>(F->tail_q));
-        LAUNCH(ctx, k_tail_index, grid_for(nc, SGP_BLOCK), SGP_BLOCK, 0, bp<const int32_t>(F->ctv),
-               (const int32_t *)pos, F->tail_C0, nc, F->tail_P0, bp<int32_t>(F->tail_c));
         LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_q,
                (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_b));
+        LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_c,
+               (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_c));
+        LAUNCH(ctx, k_tail_pairs, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ct, F->tail_C0,
+               nb, F->tail_Q0, bp<int32_t>(F->tail_c) + nb);
         SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
     }
     int herr = 0;

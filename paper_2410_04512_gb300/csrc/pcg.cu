@@ -136,7 +136,9 @@ __global__ void __launch_bounds__(RB) k_spmv_pq(Blk<T> B, const int32_t *__restr
             } else if (g == 0) {
                 q[3 * i] = y0; q[3 * i + 1] = y1; q[3 * i + 2] = y2;
             }
-            if (g == 0) acc += (double)v0 * (double)y0 + (double)v1 * (double)y1 + (double)v2 * (double)y2;
+            // the row's three products are summed in T, the running sum in
+            // FP64 (one conversion per row keeps FP32 rows off the FP64 pipe)
+            if (g == 0) acc += (double)fma(v0, y0, fma(v1, y1, v2 * y2));
         }
     }
     double s = block_sum<RB>(acc, sh);
@@ -294,17 +296,91 @@ __global__ void k_update(int64_t n, X *x, const T *__restrict__ p, T *r, const T
     }
 }
 
-// rho' = r^T w after the tree solve; beta = rho'/rho.
+// 16-byte packs of vector entries (4 floats or 2 doubles): the streaming
+// kernels below treat the n x 3 vectors as flat arrays of 3n entries.
 template <typename T>
-__global__ void k_rz(int64_t n, const T *__restrict__ r, const T *__restrict__ w, double *partials,
-                     Scal *sc)
+struct alignas(16) Pack {
+    static constexpr int K = 16 / sizeof(T);
+    T v[K];
+};
+
+// x += alpha p, r -= alpha q, w = r, |r|^2 (tree and identity
+// preconditioners, which need no per-cell block), 16-byte accesses.
+template <typename T, int PREC>
+__global__ void __launch_bounds__(RB) k_update_v(int64_t n, T *x, const T *__restrict__ p, T *r,
+                                                 const T *__restrict__ q, T *w, double *partials, Scal *sc)
 {
     __shared__ double sh[RB / 32];
     if (sc->done) return;
+    constexpr int K = Pack<T>::K;
+    const T a = (T)sc->alpha;
+    const int64_t n3 = 3 * n, np = n3 / K;
+    const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    double rr = 0.0;
+    for (int64_t i = g0; i < np; i += gs) {
+        Pack<T> pv = reinterpret_cast<const Pack<T> *>(p)[i];
+        Pack<T> qv = reinterpret_cast<const Pack<T> *>(q)[i];
+        Pack<T> rv = reinterpret_cast<const Pack<T> *>(r)[i];
+        Pack<T> xv = reinterpret_cast<const Pack<T> *>(x)[i];
+        T s = 0;
+#pragma unroll
+        for (int e = 0; e < K; ++e) {
+            xv.v[e] = fma(a, pv.v[e], xv.v[e]);
+            rv.v[e] = fma(-a, qv.v[e], rv.v[e]);
+            s = fma(rv.v[e], rv.v[e], s);
+        }
+        rr += (double)s;  // pack sums in T, running sum in FP64
+        reinterpret_cast<Pack<T> *>(x)[i] = xv;
+        reinterpret_cast<Pack<T> *>(r)[i] = rv;
+        reinterpret_cast<Pack<T> *>(w)[i] = rv;
+    }
+    for (int64_t k = np * K + g0; k < n3; k += gs) {
+        x[k] = fma(a, p[k], x[k]);
+        T rk = fma(-a, q[k], r[k]);
+        r[k] = rk;
+        w[k] = rk;
+        rr += (double)rk * (double)rk;
+    }
+    double s1 = block_sum<RB>(rr, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s1;
+    if (last_block(&sc->cnt)) {
+        double A = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            sc->rr = A;
+            sc->it += 1;
+            if (A <= sc->stop2) sc->done = 1;
+            else if (sc->it >= sc->maxit) {
+                sc->done = 1;
+                sc->status = SGP_ERR_NO_CONVERGENCE;
+            } else if (PREC != 0) {  // identity: z = r, so r^T z = |r|^2
+                sc->beta = A / sc->rho;
+                sc->rho = A;
+                sc->rz = A;
+            }
+        }
+    }
+}
+
+// rho' = r^T w after the tree solve; beta = rho'/rho.
+template <typename T>
+__global__ void __launch_bounds__(RB) k_rz(int64_t n, const T *__restrict__ r, const T *__restrict__ w,
+                                           double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    constexpr int K = Pack<T>::K;
+    const int64_t n3 = 3 * n, np = n3 / K;
+    const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
     double acc = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * n;
-         k += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)r[k] * (double)w[k];
+    for (int64_t i = g0; i < np; i += gs) {
+        Pack<T> a = reinterpret_cast<const Pack<T> *>(r)[i];
+        Pack<T> b = reinterpret_cast<const Pack<T> *>(w)[i];
+        T s = 0;
+#pragma unroll
+        for (int e = 0; e < K; ++e) s = fma(a.v[e], b.v[e], s);
+        acc += (double)s;  // pack sums in T, running sum in FP64
+    }
+    for (int64_t k = np * K + g0; k < n3; k += gs) acc += (double)r[k] * (double)w[k];
     double s = block_sum<RB>(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
     if (last_block(&sc->cnt)) {
@@ -324,13 +400,21 @@ __global__ void k_rz(int64_t n, const T *__restrict__ r, const T *__restrict__ w
 
 // p = w + beta p
 template <typename T>
-__global__ void k_pupd(int64_t n, const T *__restrict__ w, T *p, const Scal *sc)
+__global__ void __launch_bounds__(RB) k_pupd(int64_t n, const T *__restrict__ w, T *p, const Scal *sc)
 {
     if (sc->done) return;
+    constexpr int K = Pack<T>::K;
     const T beta = (T)sc->beta;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * n;
-         k += (int64_t)gridDim.x * blockDim.x)
-        p[k] = w[k] + beta * p[k];
+    const int64_t n3 = 3 * n, np = n3 / K;
+    const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = g0; i < np; i += gs) {
+        Pack<T> a = reinterpret_cast<const Pack<T> *>(w)[i];
+        Pack<T> b = reinterpret_cast<const Pack<T> *>(p)[i];
+#pragma unroll
+        for (int e = 0; e < K; ++e) b.v[e] = fma(beta, b.v[e], a.v[e]);
+        reinterpret_cast<Pack<T> *>(p)[i] = b;
+    }
+    for (int64_t k = np * K + g0; k < n3; k += gs) p[k] = fma(beta, p[k], w[k]);
 }
 
 // FP64 residual r = F - Gamma x with |r|^2 and |F|^2 (exit check, outer loop)
@@ -397,12 +481,15 @@ __global__ void k_accumulate(int64_t n3, const float *__restrict__ d, double sca
 // ---------------------------------------------------------------------------
 namespace {
 
-// Lanes per block row of the product: 4 unless SGP_SPMV_LPR says 1, 2 or 8.
+// Lanes per block row of the product (SGP_SPMV_LPR overrides): FP64 is
+// bound by the FP64 issue rate, where idle lanes of a warp instruction are
+// wasted, so one lane per row; FP32 is bound by memory, where more lanes per
+// row give longer contiguous loads.
 template <typename T>
 sgp_status launch_spmv_pq(sgp_ctx *ctx, Blk<T> B, const int32_t *row_ptr, T g0, int64_t n, const T *p,
                           T *q, double *partials, Scal *sc)
 {
-    const int lpr = ctx->spmv_lpr > 0 ? ctx->spmv_lpr : 4;
+    const int lpr = ctx->spmv_lpr > 0 ? ctx->spmv_lpr : (sizeof(T) == 8 ? 1 : 2);
     const int64_t want = (n * lpr + RB - 1) / RB;
     auto go = [&](auto kern) -> sgp_status {
         unsigned G;
@@ -480,6 +567,12 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
         SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
     }
     LAUNCH(ctx, k_rz_init<T>, G, RB, 0, n, (const T *)r, (const T *)w, p, partials, sc);
+    // streaming kernels: one full wave of resident blocks
+    static_assert(sizeof(X) == sizeof(T), "iterate and vectors share one precision");
+    T *xt = reinterpret_cast<T *>(x);
+    unsigned Gv = 1;
+    SGP_TRY(resident_grid(ctx, (const void *)k_update_v<T, 0>, RB,
+                          (3 * n / Pack<T>::K + RB - 1) / RB, &Gv));
     // One PCG iteration per call; kernels return at once after convergence.
     auto iterate = [&](int count) -> sgp_status {
         cudaEvent_t ev;
@@ -489,25 +582,23 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
             SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
             SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
             if (precond == SGP_PRECOND_TREE)
-                LAUNCH(ctx, (k_update<T, X, 0>), G, RB, 0, n, x, (const T *)p, r, (const T *)q, w, jac,
-                       partials, sc);
+                LAUNCH(ctx, (k_update_v<T, 0>), Gv, RB, 0, n, xt, (const T *)p, r, (const T *)q, w, partials, sc);
             else if (precond == SGP_PRECOND_BLOCK_JACOBI)
                 LAUNCH(ctx, (k_update<T, X, 1>), G, RB, 0, n, x, (const T *)p, r, (const T *)q, w, jac,
                        partials, sc);
             else
-                LAUNCH(ctx, (k_update<T, X, 2>), G, RB, 0, n, x, (const T *)p, r, (const T *)q, w, jac,
-                       partials, sc);
+                LAUNCH(ctx, (k_update_v<T, 2>), Gv, RB, 0, n, xt, (const T *)p, r, (const T *)q, w, partials, sc);
             SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
             if (precond == SGP_PRECOND_TREE) {
                 SGP_TRY(kt_begin(ctx, SGP_KT_TREE_SOLVE, &ev));
                 SGP_TRY(tree_apply_inplace<T>(ctx, Fac, w, &sc->done));
                 SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
                 SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
-                LAUNCH(ctx, k_rz<T>, G, RB, 0, n, (const T *)r, (const T *)w, partials, sc);
+                LAUNCH(ctx, k_rz<T>, Gv, RB, 0, n, (const T *)r, (const T *)w, partials, sc);
             } else {
                 SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
             }
-            LAUNCH(ctx, k_pupd<T>, G, RB, 0, n, (const T *)w, p, (const Scal *)sc);
+            LAUNCH(ctx, k_pupd<T>, Gv, RB, 0, n, (const T *)w, p, (const Scal *)sc);
             SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
         }
         return SGP_OK;
@@ -643,8 +734,11 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
             const double nr = std::sqrt(rr);
             LAUNCH(ctx, k_scale_to32, grid_for(3 * n, SGP_BLOCK), SGP_BLOCK, 0, 3 * n, (const double *)r,
                    1.0 / nr, r32, d32);
-            // inner solve from d = 0 on the scaled residual (|r32| ~ 1)
-            SGP_TRY(pcg_run<float, float>(ctx, M, Fac, opts->precond, (const float *)r32, d32, 0, itol,
+            // inner solve from d = 0 on the scaled residual (|r32| ~ 1); the
+            // last step only has to bring |r| to half the outer target
+            const double need = 0.5 * opts->tol * std::sqrt(ff) / nr;
+            const double itol_k = std::max(itol, std::min(need, 0.5));
+            SGP_TRY(pcg_run<float, float>(ctx, M, Fac, opts->precond, (const float *)r32, d32, 0, itol_k,
                                           opts->maxit - total, s32, p32, q32, w32, partials, sc, &hs));
             total += hs.it;
             ++outer;

@@ -228,9 +228,36 @@ struct sgp_factor {
 // device helpers
 // ---------------------------------------------------------------------------
 #define SGP_BLOCK 256
-// Largest number of vertices the single-block tail of the tree solve holds
-// in shared memory (3 x 8 B x 8192 = 192 KB for FP64).
-#define TREE_TAIL_MAX 8192
+// Shared memory budget of the single-block tail of the tree solve (all the
+// tail's vectors, pivots, L blocks and index lists, sized for FP64).
+#define TREE_TAIL_SMEM (200 * 1024)
+
+// Launch with programmatic stream serialisation (the kernel may start while
+// the previous one finishes; it must griddepcontrol.wait before consuming).
+template <typename... KArgs, typename... Args>
+static inline sgp_status sgp_launch_pdl(sgp_ctx *ctx, const char *name, void (*k)(KArgs...), dim3 grid,
+                                        dim3 block, size_t smem, Args... args)
+{
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return SGP_OK;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+    ctx->launches++;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return sgp_fail(ctx, SGP_ERR_CUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
+    return SGP_OK;
+}
+#define LAUNCH_PDL(ctx, kern, grid, block, smem, ...) \
+    SGP_TRY(sgp_launch_pdl((ctx), #kern, kern, dim3(grid), dim3(block), (smem), __VA_ARGS__))
 
 // sym6 y = S x
 template <typename T, typename U>
