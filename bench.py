@@ -9,8 +9,12 @@ buffers, with the host<->device copies inside the timed region.
 
 Default workload: a spheroid of 1,000,000 cells (centres uniform in a ball
 at packing fraction 0.6, radii U[0.45, 0.55]), per-pair gamma_par and
-gamma_perp log-uniform in [0.1, 10], gamma0 = 1e-3, F ~ N(0, 1), FP64,
-spanning-forest preconditioner.
+gamma_perp log-uniform in [0.1, 10], gamma0 = 1e-3, F ~ N(0, 1), solved to
+relative residual 1e-8 with the spanning-forest preconditioner.  The timed
+form (``value``) is the mixed-precision one (FP32 inner PCG inside FP64
+iterative refinement); the same line reports plain FP64 PCG and FP64
+block-Jacobi PCG on the same workload (``forms``), timed after the main
+region.
 
 ``--impl reference`` times the CPU oracle instead (host cores, a bounded
 sample of the same workload).  Under torchrun each rank solves its own
@@ -125,6 +129,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def tree_bytes(n: int, npairs: int, nrecv: int, fp: int) -> int:
+    """Algorithmic bytes of one tree solve (forward + backward, all levels).
+    Forward: per L block its contributor id, the block and the contributor's
+    w; per receiver entry its id, its contributor range and w read+write.
+    Backward: per vertex its id, pair range, D^-1 and w read+write; per L
+    block the receiver id, the block and the receiver's z."""
+    wb, lb, db = 3 * fp, 9 * fp, 6 * fp
+    fwd = npairs * (4 + lb + wb) + nrecv * (8 + 2 * wb)
+    bwd = n * (8 + db + 2 * wb) + npairs * (4 + lb + wb)
+    return fwd + bwd
+
+
+def spmv_bytes(n: int, m: int, fp: int) -> int:
+    """Algorithmic bytes of one product q = Gamma p with p^T q: per directed
+    slot the symmetric block (6 words) and the column (packed into an 8-word
+    record in FP32); per row the row pointer, p_i and q_i."""
+    slot = 6 * fp + 4 if fp == 8 else 32
+    return 2 * m * slot + n * (4 + 3 * fp + 3 * fp)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -139,6 +163,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     peaks, peaks_src = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
 
     wl = WORKLOADS[args.workload]
     cells = wl["make"](2000 + rank)          # each rank: its own independent replica
@@ -149,68 +174,79 @@ def run_gpu(args):
     radii = torch.from_numpy(cells.radii).to(dev)
     F = torch.from_numpy(F_host).to(dev)
     tpd, tqd = torch.from_numpy(tp).to(dev), torch.from_numpy(tq).to(dev)
-    v = torch.zeros_like(F)
-    precision = sgp.PREC_MIXED if args.precision == "mixed" else sgp.PREC_F64
-    precond = {"tree": sgp.PRECOND_TREE, "jacobi": sgp.PRECOND_BLOCK_JACOBI,
-               "none": sgp.PRECOND_NONE}[args.precond]
     stream = torch.cuda.current_stream(dev)
     ctx = sgp.Context(local, stream)
-    H = {"g": None, "M": None, "T": None, "Fh": None}
-    last = {}
+    PREC = {"f64": sgp.PREC_F64, "mixed": sgp.PREC_MIXED}
+    PRECOND = {"tree": sgp.PRECOND_TREE, "jacobi": sgp.PRECOND_BLOCK_JACOBI, "none": sgp.PRECOND_NONE}
 
-    def step(pos_d, radii_d, F_d, out_v):
-        H["g"] = ctx.collision_graph(pos_d, radii_d, H["g"])
-        ij = H["g"].edges()
-        gp, gq = workloads.pair_gamma_torch(cells.seed, ij, tpd, tqd)
-        H["M"] = ctx.friction_assemble(H["g"], pos_d, gp.contiguous(), gq.contiguous(), cells.gamma0,
-                                       precision, H["M"])
-        if precond == sgp.PRECOND_TREE:
-            H["T"] = ctx.max_spanning_tree(H["M"], H["T"])
-            H["Fh"] = ctx.tree_factor(H["M"], H["T"], H["Fh"])
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        _, info = ctx.pcg_solve(H["M"], H["Fh"], F_d, out_v, tol=args.tol, precond=precond,
-                                precision=precision)
-        ev1.record(stream)
-        last["info"], last["solve_ev"] = info, (ev0, ev1)
-        return info
+    class Form:
+        """One solver form with its own reusable handles."""
 
-    for _ in range(args.warmup):
-        step(pos, radii, F, v)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+        def __init__(self, precision: str, precond: str):
+            self.precision, self.precond = PREC[precision], PRECOND[precond]
+            self.H = {"g": None, "M": None, "T": None, "Fh": None}
+            self.last = None
 
-    # ---- timed region: device-resident inputs -----------------------------
-    ctx.set_kernel_timing(True)
-    for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR):
-        ctx.kernel_time(k, reset=True)
-    ctx.launch_count(reset=True)
-    solve_ms, iters = [], []
+        def step(self, pos_d, radii_d, F_d, out_v):
+            H = self.H
+            H["g"] = ctx.collision_graph(pos_d, radii_d, H["g"])
+            ij = H["g"].edges()
+            gp, gq = workloads.pair_gamma_torch(cells.seed, ij, tpd, tqd)
+            H["M"] = ctx.friction_assemble(H["g"], pos_d, gp.contiguous(), gq.contiguous(), cells.gamma0,
+                                           self.precision, H["M"])
+            if self.precond == sgp.PRECOND_TREE:
+                H["T"] = ctx.max_spanning_tree(H["M"], H["T"])
+                H["Fh"] = ctx.tree_factor(H["M"], H["T"], H["Fh"])
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, info = ctx.pcg_solve(H["M"], H["Fh"], F_d, out_v, tol=args.tol, precond=self.precond,
+                                    precision=self.precision)
+            ev1.record(stream)
+            self.last = (info, ev0, ev1)
+            return info
+
+        def timed(self, steps: int, warmup: int, kernel_timing: bool):
+            v = torch.zeros_like(F)
+            for _ in range(warmup):
+                self.step(pos, radii, F, v)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            ctx.set_kernel_timing(kernel_timing)
+            for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR):
+                ctx.kernel_time(k, reset=True)
+            ctx.launch_count(reset=True)
+            solve_ms, iters = [], []
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(steps):
+                info = self.step(pos, radii, F, v)
+                _, a, b = self.last
+                b.synchronize()
+                solve_ms.append(a.elapsed_time(b))
+                iters.append(info.iterations)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            elapsed = t0.elapsed_time(t1) / 1e3
+            kt = {k: ctx.kernel_time(k) for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR)}
+            launches = ctx.launch_count()
+            ctx.set_kernel_timing(False)
+            if world > 1:
+                t = torch.tensor([elapsed], device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                elapsed = float(t.item())
+            return dict(elapsed=elapsed, solve_ms=float(np.median(solve_ms)), iters=float(np.mean(iters)),
+                        info=self.last[0], kt=kt, launches=launches, v=v)
+
+    # ---- timed region: the chosen form, device-resident inputs ------------
+    chosen = Form(args.precision, args.precond)
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(args.steps):
-            info = step(pos, radii, F, v)
-            iters.append(info.iterations)
-            a, b = last["solve_ev"]
-            b.synchronize()
-            solve_ms.append(a.elapsed_time(b))
-        t1.record(stream)
-        torch.cuda.synchronize()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    launches = ctx.launch_count()
-    kt = {k: ctx.kernel_time(k) for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR)}
-    ctx.set_kernel_timing(False)
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        res = chosen.timed(args.steps, args.warmup, kernel_timing=True)
+    elapsed = res["elapsed"]
     value = world * args.steps / elapsed
-    info = last["info"]
+    info = res["info"]
 
     # ---- end to end through the public API from pinned host buffers -------
     pos_h = torch.from_numpy(cells.pos).pin_memory()
@@ -229,7 +265,7 @@ def run_gpu(args):
         pos_e.copy_(pos_h, non_blocking=True)
         rad_e.copy_(rad_h, non_blocking=True)
         F_e.copy_(F_h, non_blocking=True)
-        step(pos_e, rad_e, F_e, v_e)
+        chosen.step(pos_e, rad_e, F_e, v_e)
         v_h.copy_(v_e, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -239,52 +275,71 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = world * e2e_steps / e2e_s
-    h2d = pos.numel() * 8 + radii.numel() * 8 + F.numel() * 8
-    d2h = F.numel() * 8
 
-    # ---- roofline of the dominant kernel ----------------------------------
-    m = H["M"].m
-    dbar = 2.0 * m / n
-    it_mean = float(np.mean(iters))
-    spmv_ms, spmv_n = kt[sgp.KT_SPMV]
-    tree_ms, tree_n = kt[sgp.KT_TREE_SOLVE]
-    vec_ms, vec_n = kt[sgp.KT_PCG_VECTOR]
-    fp = 8 if precision == sgp.PREC_F64 else 4
-    # SpMV q = Gamma p (+ p^T q): per directed slot a symmetric block (6 words)
-    # and a column index; per row the row pointer, p_i and q_i.
-    spmv_bytes = 2 * m * (6 * fp + 4) + n * (4 + 3 * fp + 3 * fp)
-    spmv_avg_s = (spmv_ms / max(spmv_n, 1)) / 1e3
-    spmv_gbs = spmv_bytes / spmv_avg_s / 1e9 if spmv_avg_s > 0 else 0.0
-    spmv_flops = 2 * m * (3 + 18) + n * 6       # v_i - v_j, S d (9 FMA), gamma0 v_i
-    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    roof = {"kernel": "k_spmv_pq<double>" if fp == 8 else "k_spmv_pq<float>",
-            "bound": "hbm", "achieved": round(spmv_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(spmv_gbs / hbm_peak, 4), "traffic": None,
-            "peak_source": f"{peaks_src} (MEASURED_PEAKS.json hbm_gbs)" if peaks_src == "measured" else "fallback",
-            "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": round(spmv_avg_s * 1e6, 2),
-            "launches": spmv_n,
-            "fp64_alu_frac": round(spmv_flops / spmv_avg_s / (FP64_NOMINAL_TFLOPS * 1e12), 4) if fp == 8 else None}
-    share = {"spmv_ms": round(spmv_ms, 2), "tree_solve_ms": round(tree_ms, 2), "pcg_vector_ms": round(vec_ms, 2),
-             "timed_ms": round(elapsed * 1e3, 2)}
+    # ---- rooflines of the two per-iteration kernels -----------------------
+    M = chosen.H["M"]
+    m = M.m
+    fp = 4 if chosen.precision == sgp.PREC_MIXED else 8
+    spmv_ms, spmv_n = res["kt"][sgp.KT_SPMV]
+    tree_ms, tree_n = res["kt"][sgp.KT_TREE_SOLVE]
+
+    def roof(name, bytes_per, total_ms, launches, unit_note):
+        avg_s = (total_ms / max(launches, 1)) / 1e3
+        gbs = bytes_per / avg_s / 1e9 if avg_s > 0 else 0.0
+        return {"kernel": name, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peaks_src == "measured"
+                                else "fallback"),
+                "algorithmic_bytes_per_launch": int(bytes_per), "avg_launch_us": round(avg_s * 1e6, 2),
+                "launches": launches, "unit_of_work": unit_note}
+
+    roofs = [roof("k_spmv_pq<%s>" % ("float" if fp == 4 else "double"), spmv_bytes(n, m, fp), spmv_ms, spmv_n,
+                  "one product Gamma p + p^T q over all rows")]
+    if chosen.precond == sgp.PRECOND_TREE:
+        _, levels, npairs, nrecv = chosen.H["Fh"].stats()
+        roofs.append(roof("tree solve (k_tree_fwd/k_tree_tail/k_tree_bwd<%s>, %d levels)"
+                          % ("float" if fp == 4 else "double", levels),
+                          tree_bytes(n, npairs, nrecv, fp), tree_ms, tree_n,
+                          "one application of P^-1 (all levels)"))
+    dominant = max(range(len(roofs)), key=lambda i: [spmv_ms, tree_ms][i])
+
+    # ---- the other forms on the same workload (outside the timed region) --
+    forms = {}
+    if rank == 0 and args.compare:
+        for label, prec, pc, steps in (("plain_fp64_mst", "f64", "tree", 2), ("fp64_block_jacobi", "f64", "jacobi", 1)):
+            if (prec, pc) == (args.precision, args.precond):
+                continue
+            r = Form(prec, pc).timed(steps, 1, kernel_timing=False)
+            forms[label] = {"solves_per_s": round(steps / r["elapsed"], 4),
+                            "solve_only_per_s": round(1e3 / r["solve_ms"], 4),
+                            "iterations": int(round(r["iters"])),
+                            "true_rel_residual": r["info"].true_rel_residual}
+        if "plain_fp64_mst" in forms:
+            forms["chosen_vs_plain_fp64"] = round(value / forms["plain_fp64_mst"]["solves_per_s"], 3)
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == sgp.PREC_F64 else "f32+f64",
+        "dtype": "f64" if fp == 8 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "n_cells": n, "edges": int(m), "mean_degree": round(dbar, 3),
-                   "precond": args.precond, "precision": args.precision, "tol": args.tol,
+        "config": {"workload": wl["desc"], "n_cells": n, "edges": int(m), "mean_degree": round(2.0 * m / n, 3),
+                   "form": "%s precision, %s preconditioner" % (args.precision, args.precond),
+                   "tol": args.tol,
                    "step": "collision graph + friction blocks + spanning forest + tree factor + PCG solve",
-                   "l2": "working set > L2 (friction blocks alone %.0f MB)" % (2 * m * 6 * fp / 1e6),
+                   "l2": "working set > L2 (friction blocks alone %.0f MB)" % (2 * m * (48 if fp == 8 else 32) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "iterations": int(round(it_mean)), "true_rel_residual": info.true_rel_residual,
-        "solve_only": {"value": round(1e3 / float(np.median(solve_ms)), 4), "unit": "solves/s",
-                       "ms_median": round(float(np.median(solve_ms)), 3)},
-        "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-        "gpu_launches": int(launches),
-        "roofline": roof, "time_share": share,
+        "iterations": int(round(res["iters"])), "true_rel_residual": info.true_rel_residual,
+        "outer_iterations": info.outer_iterations,
+        "solve_only": {"value": round(1e3 / res["solve_ms"], 4), "unit": "solves/s",
+                       "ms_median": round(res["solve_ms"], 3)},
+        "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d_bytes(pos, radii, F),
+                "d2h_bytes_per_step": F.numel() * 8, "steps": e2e_steps},
+        "gpu_launches": int(res["launches"]),
+        "roofline": roofs[dominant], "roofline_other": [r for i, r in enumerate(roofs) if i != dominant],
+        "time_share_ms": {"spmv": round(spmv_ms, 2), "tree_solve": round(tree_ms, 2),
+                          "timed": round(elapsed * 1e3, 2)},
+        "forms": forms,
         "clocks": clk.summary(),
     }
     if rank == 0 and args.cpu_baseline:
@@ -294,6 +349,10 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def h2d_bytes(*ts) -> int:
+    return int(sum(t.numel() * t.element_size() for t in ts))
 
 
 # ---------------------------------------------------------------------------
@@ -366,10 +425,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgp", choices=["sgp", "reference"])
     ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["f64", "mixed"])
     ap.add_argument("--precond", default="tree", choices=["tree", "jacobi", "none"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--cpu-baseline", dest="cpu_baseline", type=int, default=1)
+    ap.add_argument("--compare", type=int, default=1, help="also time plain FP64 and block-Jacobi")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-sample-cells", type=int, default=20000)
     args = ap.parse_args()

@@ -180,8 +180,12 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_tre
  * substitution, Appendix B.1).  b_dev, x_dev: n x 3 float64; may alias. */
 sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *factor, const double *b_dev,
                           double *x_dev);
-/* Contraction rounds and elimination levels (two per round) of the factor. */
-sgp_status sgp_factor_info(const sgp_factor *factor, int32_t *rounds, int32_t *levels);
+/* Shape of the factor: contraction levels (rounds == levels: each level
+ * eliminates leaves and degree-2 vertices together), the number of L blocks
+ * (one per eliminated vertex and current neighbour) and of receiver entries
+ * (vertex, level) of the forward substitution.  Any pointer may be NULL. */
+sgp_status sgp_factor_info(const sgp_factor *factor, int32_t *rounds, int32_t *levels,
+                           int64_t *l_blocks, int64_t *receiver_entries);
 void sgp_factor_destroy(sgp_factor *factor);
 
 /* ---- Section 1.1: preconditioned conjugate gradients ------------------------

@@ -79,7 +79,8 @@ def load_library(path: str = LIB_PATH):
         "sgp_tree_destroy": ([P], None),
         "sgp_tree_factor": ([P, P, P, PP], I32),
         "sgp_tree_apply": ([P, P, P, P], I32),
-        "sgp_factor_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], I32),
+        "sgp_factor_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I64),
+                             ctypes.POINTER(I64)], I32),
         "sgp_factor_destroy": ([P], None),
         "sgp_pcg_solve": ([P, P, P, P, P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)], I32),
         "sgp_set_kernel_timing": ([P, I32], I32),
@@ -185,9 +186,16 @@ class Factor(_Handle):
     _destroy = "sgp_factor_destroy"
 
     def info(self):
+        """(rounds, levels) of the contraction schedule."""
+        return self.stats()[:2]
+
+    def stats(self):
+        """(rounds, levels, L blocks, receiver entries)."""
         r, l = ctypes.c_int32(), ctypes.c_int32()
-        self.ctx._ok(_lib.sgp_factor_info(self.ptr, ctypes.byref(r), ctypes.byref(l)))
-        return r.value, l.value
+        nb, nr = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx._ok(_lib.sgp_factor_info(self.ptr, ctypes.byref(r), ctypes.byref(l), ctypes.byref(nb),
+                                          ctypes.byref(nr)))
+        return r.value, l.value, nb.value, nr.value
 
 
 @dataclass

@@ -210,8 +210,9 @@ sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev)
     if (!ctx->timing) return SGP_OK;
     if (ctx->capture_sink) {
         // inside a capture: an event-record node owned by the graph entry;
-        // only the product is timed there, to keep the graph lean
-        if (kclass != SGP_KT_SPMV) return SGP_OK;
+        // the product and the tree solve are timed there (not the cheap
+        // vector kernels), to keep the graph lean
+        if (kclass == SGP_KT_PCG_VECTOR) return SGP_OK;
         SGP_CUDA(ctx, cudaEventCreate(ev));
         SGP_CUDA(ctx, cudaEventRecordWithFlags(*ev, ctx->stream, cudaEventRecordExternal));
         return SGP_OK;

@@ -917,11 +917,14 @@ sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *F, const double *b, do
     return tree_apply_inplace<double>(ctx, F, x, nullptr);
 }
 
-sgp_status sgp_factor_info(const sgp_factor *F, int32_t *rounds, int32_t *levels)
+sgp_status sgp_factor_info(const sgp_factor *F, int32_t *rounds, int32_t *levels, int64_t *l_blocks,
+                           int64_t *receiver_entries)
 {
     if (!F) return SGP_ERR_INVALID_ARG;
     if (rounds) *rounds = F->rounds;
     if (levels) *levels = F->levels;
+    if (l_blocks) *l_blocks = F->npairs;
+    if (receiver_entries) *receiver_entries = F->rl_ptr.empty() ? 0 : F->rl_ptr.back();
     return SGP_OK;
 }
 
