@@ -103,6 +103,16 @@ sgp_status sgp_copy(sgp_ctx *ctx, void *dst_dev, const void *src_dev, int64_t by
  * non-positive radius.  Synchronises (to size the edge list). */
 sgp_status sgp_collision_graph(sgp_ctx *ctx, int64_t n, const double *pos_dev,
                                const double *radii_dev, sgp_graph **graph);
+/* The same for a batch of independent configurations stored one after the
+ * other: instance s owns cells [offsets[s], offsets[s+1]) (offsets: host
+ * array of n_instances + 1 values, offsets[0] = 0, non-decreasing).  Cells
+ * of different instances are never in contact, whatever their positions:
+ * each instance gets its own cell grid.  The result is one canonical edge
+ * list over global cell indices; assembly, spanning forest and tree factor
+ * then work on the whole batch at once (a block-diagonal system).
+ * Synchronises. */
+sgp_status sgp_collision_graph_batched(sgp_ctx *ctx, int64_t n_instances, const int64_t *offsets,
+                                       const double *pos_dev, const double *radii_dev, sgp_graph **graph);
 /* n, m and the device edge list (m x 2 int32, owned by the graph). */
 sgp_status sgp_graph_info(const sgp_graph *graph, int64_t *n, int64_t *m,
                           const int32_t **ij_dev);
@@ -202,6 +212,20 @@ void sgp_factor_destroy(sgp_factor *factor);
 sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_factor *factor,
                          const double *F_dev, double *v_dev, const sgp_solve_opts *opts,
                          sgp_solve_info *info);
+
+/* Batched PCG: every instance s of a block-diagonal matrix (assembled from a
+ * batched collision graph with the same offsets) is solved for its own
+ * Gamma_ss v_s = F_s with its own scalars (alpha, beta, rho) and its own
+ * stopping test |r_s| <= tol |F_s|; all instances share each kernel launch
+ * and the tree factor of the whole batch.  Converged instances drop out of
+ * the products and vector updates.  Iterations are replayed as CUDA graphs.
+ * opts as for sgp_pcg_solve (maxit per instance).  infos (host, n_instances
+ * entries, may be NULL) receives each instance's statistics.  Returns the
+ * first failing status (NOT_SPD before NO_CONVERGENCE); INVALID_ARG if an
+ * edge joins two instances.  Synchronises. */
+sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_factor *factor,
+                                 int64_t n_instances, const int64_t *offsets, const double *F_dev,
+                                 double *v_dev, const sgp_solve_opts *opts, sgp_solve_info *infos);
 
 /* ---- kernel timing ----------------------------------------------------------
  * When enabled, the library brackets every launch of the named kernel class

@@ -67,6 +67,8 @@ def load_library(path: str = LIB_PATH):
         "sgp_version": ([], ctypes.c_char_p),
         "sgp_copy": ([P, P, P, I64], I32),
         "sgp_collision_graph": ([P, I64, P, P, PP], I32),
+        "sgp_collision_graph_batched": ([P, I64, P, P, P, PP], I32),
+        "sgp_pcg_solve_batched": ([P, P, P, I64, P, P, P, ctypes.POINTER(SolveOpts), P], I32),
         "sgp_graph_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64), PP], I32),
         "sgp_graph_destroy": ([P], None),
         "sgp_friction_assemble": ([P, P, P, P, P, D, I32, PP], I32),
@@ -290,6 +292,41 @@ class Context:
         if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
             self._ok(rc)
         return v, info
+
+    # -- batches of independent configurations ------------------------------
+    def collision_graph_batched(self, offsets, pos: torch.Tensor, radii: torch.Tensor,
+                                graph: Graph | None = None) -> Graph:
+        import numpy as np
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        n = int(off[-1])
+        _check_vec(pos, n, name="pos")
+        _check_vec(radii, n, cols=0, name="radii")
+        g = graph if graph is not None else Graph(self)
+        self._ok(_lib.sgp_collision_graph_batched(self.ptr, len(off) - 1, off.ctypes.data_as(ctypes.c_void_p),
+                                                  _ptr(pos), _ptr(radii), ctypes.byref(g.ptr)))
+        return g
+
+    def pcg_solve_batched(self, M: Matrix, Fh: Factor | None, offsets, F: torch.Tensor,
+                          v: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 100000,
+                          precond: int = PRECOND_TREE, precision: int = PREC_F64, x0_given: bool = False,
+                          max_outer: int = 0, inner_tol: float = 0.0, raise_on_error: bool = True):
+        """Solve every instance of a batch; returns (v, [Info per instance])."""
+        import numpy as np
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        k = len(off) - 1
+        _check_vec(F, M.n, name="F")
+        v = torch.zeros_like(F) if v is None else v
+        _check_vec(v, M.n, name="v")
+        o = SolveOpts(tol, maxit, precond, precision, int(x0_given), max_outer, inner_tol)
+        infos = (SolveInfo * k)()
+        rc = _lib.sgp_pcg_solve_batched(self.ptr, M.ptr, Fh.ptr if Fh is not None else None, k,
+                                        off.ctypes.data_as(ctypes.c_void_p), _ptr(F), _ptr(v), ctypes.byref(o),
+                                        ctypes.cast(infos, ctypes.c_void_p))
+        out = [Info(i.iterations, i.outer_iterations, i.status, i.rel_residual, i.true_rel_residual)
+               for i in infos]
+        if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
+            self._ok(rc)
+        return v, out
 
     # -- instrumentation ---------------------------------------------------
     def set_kernel_timing(self, enable: bool):

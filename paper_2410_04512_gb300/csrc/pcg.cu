@@ -11,7 +11,7 @@
 // partials in a fixed order and updates them, so no host round trip is
 // needed per iteration and results are bitwise reproducible.  The host
 // launches iterations in chunks and polls the `done` word between chunks.
-#include "sgp_internal.cuh"
+#include "solver_common.cuh"
 
 template <typename T>
 sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
@@ -27,31 +27,6 @@ struct Scal {
     int done, status;
     unsigned cnt;
     int pad;
-};
-
-// -------------------------------------------------------------- block loads
-template <typename T> struct Blk;
-template <> struct Blk<double> {
-    const int32_t *col;
-    const double *blk;
-    __device__ __forceinline__ void load(int32_t s, double *S, int32_t &j) const
-    {
-        const double2 *b2 = reinterpret_cast<const double2 *>(blk + 6 * (int64_t)s);
-        double2 a = b2[0], b = b2[1], c = b2[2];
-        S[0] = a.x; S[1] = a.y; S[2] = b.x; S[3] = b.y; S[4] = c.x; S[5] = c.y;
-        j = col[s];
-    }
-};
-template <> struct Blk<float> {
-    const int32_t *col;
-    const float *blk;
-    __device__ __forceinline__ void load(int32_t s, float *S, int32_t &j) const
-    {
-        const float4 *b4 = reinterpret_cast<const float4 *>(blk + 8 * (int64_t)s);
-        float4 a = b4[0], b = b4[1];
-        S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w; S[4] = b.x; S[5] = b.y;
-        j = __float_as_int(b.z);
-    }
 };
 
 // y_i of the Appendix B.2 product for row i
@@ -296,14 +271,6 @@ __global__ void k_update(int64_t n, X *x, const T *__restrict__ p, T *r, const T
     }
 }
 
-// 16-byte packs of vector entries (4 floats or 2 doubles): the streaming
-// kernels below treat the n x 3 vectors as flat arrays of 3n entries.
-template <typename T>
-struct alignas(16) Pack {
-    static constexpr int K = 16 / sizeof(T);
-    T v[K];
-};
-
 // x += alpha p, r -= alpha q, w = r, |r|^2 (tree and identity
 // preconditioners, which need no per-cell block), 16-byte accesses.
 template <typename T, int PREC>
@@ -512,18 +479,6 @@ static unsigned red_grid(int64_t n)
     return (unsigned)std::max<int64_t>(g, 1);
 }
 
-template <typename T>
-Blk<T> make_blk(const sgp_matrix *M);
-template <>
-Blk<double> make_blk<double>(const sgp_matrix *M)
-{
-    return Blk<double>{bp<const int32_t>(M->col), bp<const double>(M->blk)};
-}
-template <>
-Blk<float> make_blk<float>(const sgp_matrix *M)
-{
-    return Blk<float>{bp<const int32_t>(M->col), bp<const float>(M->blk32)};
-}
 
 // One PCG run in precision T on Gamma(T) x = F(T).  X is the type of the
 // iterate x.  Returns the device scalar block's final state in *hs.

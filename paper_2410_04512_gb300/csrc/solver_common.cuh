@@ -1,0 +1,76 @@
+// solver_common.cuh -- device helpers shared by the single and the batched
+// PCG drivers: loads of one directed slot's block, and 16-byte packs of
+// vector entries.
+#pragma once
+
+#include "sgp_internal.cuh"
+
+namespace {
+
+// One directed slot of the block-sparse rows: the symmetric 3x3 block and
+// the column.  FP64: 6 doubles (three 16-byte loads) plus the column array;
+// FP32: an 8-float record (6 floats, the column's bits, pad; two loads).
+template <typename T> struct Blk;
+template <> struct Blk<double> {
+    const int32_t *col;
+    const double *blk;
+    __device__ __forceinline__ void load(int32_t s, double *S, int32_t &j) const
+    {
+        const double2 *b2 = reinterpret_cast<const double2 *>(blk + 6 * (int64_t)s);
+        double2 a = b2[0], b = b2[1], c = b2[2];
+        S[0] = a.x; S[1] = a.y; S[2] = b.x; S[3] = b.y; S[4] = c.x; S[5] = c.y;
+        j = col[s];
+    }
+};
+template <> struct Blk<float> {
+    const int32_t *col;
+    const float *blk;
+    __device__ __forceinline__ void load(int32_t s, float *S, int32_t &j) const
+    {
+        const float4 *b4 = reinterpret_cast<const float4 *>(blk + 8 * (int64_t)s);
+        float4 a = b4[0], b = b4[1];
+        S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w; S[4] = b.x; S[5] = b.y;
+        j = __float_as_int(b.z);
+    }
+};
+
+template <typename T>
+Blk<T> make_blk(const sgp_matrix *M);
+template <>
+inline Blk<double> make_blk<double>(const sgp_matrix *M)
+{
+    return Blk<double>{bp<const int32_t>(M->col), bp<const double>(M->blk)};
+}
+template <>
+inline Blk<float> make_blk<float>(const sgp_matrix *M)
+{
+    return Blk<float>{bp<const int32_t>(M->col), bp<const float>(M->blk32)};
+}
+
+// Row i of the Appendix B.2 product accumulated with fused multiply-adds:
+// y += sum over the row's slots s0, s0+step, ... of Upsilon (v_i - v_j).
+template <typename T>
+__device__ __forceinline__ void row_accumulate(const Blk<T> &B, int32_t s0, int32_t s1, int step,
+                                               const T *__restrict__ p, T v0, T v1, T v2, T &y0, T &y1,
+                                               T &y2)
+{
+    for (int32_t s = s0; s < s1; s += step) {
+        T S[6];
+        int32_t j;
+        B.load(s, S, j);
+        const T d0 = v0 - p[3 * (int64_t)j], d1 = v1 - p[3 * (int64_t)j + 1], d2 = v2 - p[3 * (int64_t)j + 2];
+        y0 = fma(S[0], d0, y0); y0 = fma(S[1], d1, y0); y0 = fma(S[2], d2, y0);
+        y1 = fma(S[1], d0, y1); y1 = fma(S[3], d1, y1); y1 = fma(S[4], d2, y1);
+        y2 = fma(S[2], d0, y2); y2 = fma(S[4], d1, y2); y2 = fma(S[5], d2, y2);
+    }
+}
+
+// 16-byte packs of vector entries (4 floats or 2 doubles): streaming
+// kernels treat the n x 3 vectors as flat arrays of 3n entries.
+template <typename T>
+struct alignas(16) Pack {
+    static constexpr int K = 16 / sizeof(T);
+    T v[K];
+};
+
+}  // namespace
