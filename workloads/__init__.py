@@ -229,3 +229,30 @@ def sphere_offsets(sizes: np.ndarray) -> np.ndarray:
     off = np.zeros(len(sizes) + 1, dtype=np.int64)
     np.cumsum(sizes, out=off[1:])
     return off
+
+
+# ---------------------------------------------------------------------------
+# Initial weights of the warm-start network (drawn here so that the GPU and
+# the oracle start from the same values)
+# ---------------------------------------------------------------------------
+MPNN_H, MPNN_K, MPNN_DIN = 64, 3, 8
+
+
+def mpnn_init(seed: int = 5000) -> np.ndarray:
+    """FP32 master parameters, flat, in the order W_in (64x8), b_in, then for
+    each of 3 layers W (64x128) and c (64), then W_out (3x64), b_out (3).
+    Glorot-uniform matrices, zero biases, and b_out = (0, 1, 0) so that the
+    untrained network returns the spanning-forest solve P^-1 F."""
+    g = _rng(seed, 5)
+    H, K, D = MPNN_H, MPNN_K, MPNN_DIN
+    parts = []
+
+    def glorot(o, i):
+        a = math.sqrt(6.0 / (o + i))
+        return g.uniform(-a, a, size=(o, i))
+
+    parts += [glorot(H, D).ravel(), np.zeros(H)]
+    for _ in range(3):
+        parts += [glorot(H, 2 * H).ravel(), np.zeros(H)]
+    parts += [0.01 * glorot(K, H).ravel(), np.array([0.0, 1.0, 0.0])]
+    return np.concatenate(parts).astype(np.float32)
