@@ -15,7 +15,12 @@ Network (width H = 64, 3 message-passing layers, BF16 weights):
   v0_i = sum_k c_ik b_i^(k)
 Every input is rotation invariant and every output vector a scalar
 combination of equivariant fields, so rotating F (and the geometry) rotates
-v0.  Loss: L = sum_i |v0_i - v*_i|^2 / sum_i |v*_i|^2.
+v0.  Two training losses against the converged solution v*:
+  "l2":     L = |v0 - v*|^2 / |v*|^2
+  "energy": L = (v0 - v*)^T Gamma (v0 - v*) / v*^T Gamma v*, the error norm
+            that conjugate gradients minimises over its Krylov space.
+Inference may rescale the prediction by the minimal-residual step
+alpha = (Gamma v0)^T F / |Gamma v0|^2, after which |F - Gamma v0| <= |F|.
 Weights enter in BF16 (round-to-nearest-even of the FP32 master values);
 arithmetic here is FP64.
 """
@@ -113,17 +118,62 @@ def forward(params_flat: np.ndarray, basis: np.ndarray, ptr, nbr, cache: bool = 
     return v0
 
 
-def loss(v0: np.ndarray, target: np.ndarray) -> float:
-    return float(np.sum((v0 - target) ** 2) / np.sum(target ** 2))
+def loss(v0: np.ndarray, target: np.ndarray, matvec=None) -> float:
+    """The "l2" loss, or the "energy" loss when ``matvec`` (v -> Gamma v)
+    is given."""
+    e = v0 - target
+    if matvec is None:
+        return float(np.sum(e * e) / np.sum(target * target))
+    return float(np.sum(e * matvec(e)) / np.sum(target * matvec(target)))
 
 
-def backward(params_flat, basis, ptr, nbr, target, round_bf16: bool = True):
-    """(loss, gradient w.r.t. the (BF16-rounded) parameters, flat)."""
+def mr_scale(v0: np.ndarray, F: np.ndarray, matvec) -> np.ndarray:
+    """alpha v0 with the minimal-residual step alpha = (G v0)^T F / |G v0|^2
+    (v0 unchanged when G v0 = 0)."""
+    g = matvec(v0)
+    den = float(np.sum(g * g))
+    return v0 * (float(np.sum(g * F)) / den) if den > 0 else v0
+
+
+def relu_ambiguous(params_flat, basis, ptr, nbr, rel: float = 2e-5, round_bf16: bool = True):
+    """ReLU decisions that rounding may take either way: (layer, cell, unit)
+    triples (layer 0 is the input layer, 1..3 the message-passing layers)
+    whose pre-activation z lies within ``rel`` times its bound
+    |W| |input| + |bias| of zero.  An evaluation in lower precision may put
+    such a z on the other side of zero; its gradient then differs from this
+    one by flipping those entries of the ReLU mask."""
     v0, C = forward(params_flat, basis, ptr, nbr, cache=True, round_bf16=round_bf16)
     p = C["p"]
-    nrm = np.sum(target ** 2)
-    L = float(np.sum((v0 - target) ** 2) / nrm)
-    dv = 2.0 * (v0 - target) / nrm
+    out = []
+    ins = [C["x"]] + [np.concatenate([C["hs"][l], C["aggs"][l]], axis=1) for l in range(3)]
+    Ws = [(p["W_in"], p["b_in"])] + [(p[f"W{l}"], p[f"c{l}"]) for l in range(3)]
+    for layer, (u, (W, b)) in enumerate(zip(ins, Ws)):
+        bound = np.abs(u) @ np.abs(W).T + np.abs(b)
+        cells, units = np.nonzero(np.abs(C["zs"][layer]) <= rel * bound)
+        out += [(layer, int(i), int(k)) for i, k in zip(cells, units)]
+    return out
+
+
+def backward(params_flat, basis, ptr, nbr, target, round_bf16: bool = True, matvec=None, flips=()):
+    """(loss, gradient w.r.t. the (BF16-rounded) parameters, flat) of the
+    "l2" loss, or of the "energy" loss when ``matvec`` is given.  ``flips``
+    lists (layer, cell, unit) entries of the ReLU masks to invert (see
+    ``relu_ambiguous``)."""
+    v0, C = forward(params_flat, basis, ptr, nbr, cache=True, round_bf16=round_bf16)
+    masks = [z > 0 for z in C["zs"]]
+    for layer, i, k in flips:
+        masks[layer][i, k] = not masks[layer][i, k]
+    p = C["p"]
+    e = v0 - target
+    if matvec is None:
+        nrm = np.sum(target ** 2)
+        L = float(np.sum(e * e) / nrm)
+        dv = 2.0 * e / nrm
+    else:
+        Ge = matvec(e)
+        nrm = np.sum(target * matvec(target))
+        L = float(np.sum(e * Ge) / nrm)
+        dv = 2.0 * Ge / nrm
     dc = np.einsum("nd,knd->nk", dv, basis)
     g = {}
     g["W_out"] = dc.T @ C["hs"][3]
@@ -133,7 +183,7 @@ def backward(params_flat, basis, ptr, nbr, target, round_bf16: bool = True):
     deg = np.diff(ptr)
     rows = np.repeat(np.arange(n), deg)
     for l in (2, 1, 0):
-        dz = dh * (C["zs"][l + 1] > 0)
+        dz = dh * masks[l + 1]
         u = np.concatenate([C["hs"][l], C["aggs"][l]], axis=1)
         g[f"W{l}"] = dz.T @ u
         g[f"c{l}"] = dz.sum(axis=0)
@@ -144,7 +194,19 @@ def backward(params_flat, basis, ptr, nbr, target, round_bf16: bool = True):
         dh_nb = np.zeros_like(dh_self)
         np.add.at(dh_nb, nbr, w[rows])
         dh = dh_self + dh_nb
-    dz0 = dh * (C["zs"][0] > 0)
+    dz0 = dh * masks[0]
     g["W_in"] = dz0.T @ C["x"]
     g["b_in"] = dz0.sum(axis=0)
     return L, pack(g)
+
+
+def adam_step(params, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1: bias-corrected
+    first and second moment estimates).  t is the 1-based step count.
+    Returns (params, m, v) as new arrays."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return params - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -256,3 +256,61 @@ def mpnn_init(seed: int = 5000) -> np.ndarray:
         parts += [glorot(H, 2 * H).ravel(), np.zeros(H)]
     parts += [0.01 * glorot(K, H).ravel(), np.array([0.0, 1.0, 0.0])]
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Time stepping of the learned-warm-start workload: overlap springs plus
+# active noise, positions advanced by x <- x + v dt
+# ---------------------------------------------------------------------------
+def spring_forces_np(pos: np.ndarray, radii: np.ndarray, ij: np.ndarray, k: float = 1.0) -> np.ndarray:
+    """Repulsive overlap springs: each contact (i, j) pushes j away from i
+    with k * (R_i + R_j - |r_j - r_i|) along u = (r_j - r_i) / |r_j - r_i|
+    and i away from j by the opposite force."""
+    ij = np.asarray(ij, dtype=np.int64)
+    d = pos[ij[:, 1]] - pos[ij[:, 0]]
+    dist = np.sqrt(np.sum(d * d, axis=1))
+    ov = np.maximum(radii[ij[:, 0]] + radii[ij[:, 1]] - dist, 0.0)
+    f = (k * ov / dist)[:, None] * d
+    F = np.zeros_like(pos)
+    np.add.at(F, ij[:, 0], -f)
+    np.add.at(F, ij[:, 1], f)
+    return F
+
+
+def spring_forces_torch(pos, radii, ij, k: float = 1.0):
+    """Torch twin of ``spring_forces_np`` with a fixed summation order per
+    cell (contacts sorted by cell, summed along a padded table), so the same
+    inputs give the same bits on every run."""
+    import torch
+    n = pos.shape[0]
+    ij = ij.to(torch.int64)
+    if ij.shape[0] == 0:
+        return torch.zeros_like(pos)
+    a, b = ij[:, 0], ij[:, 1]
+    d = pos[b] - pos[a]
+    dist = torch.sqrt(torch.sum(d * d, dim=1))
+    ov = torch.clamp(radii[a] + radii[b] - dist, min=0.0)
+    f = (k * ov / dist)[:, None] * d
+    rows = torch.cat([a, b])
+    vals = torch.cat([-f, f])
+    order = torch.argsort(rows, stable=True)
+    rows, vals = rows[order], vals[order]
+    deg = torch.bincount(rows, minlength=n)
+    start = torch.cumsum(deg, 0) - deg
+    slot = torch.arange(rows.numel(), device=pos.device) - start[rows]
+    tab = torch.zeros((n, int(deg.max().item()), 3), dtype=pos.dtype, device=pos.device)
+    tab[rows, slot] = vals
+    return tab.sum(dim=1)
+
+
+def active_noise(seed: int, step: int, n: int, sigma: float = 0.1) -> np.ndarray:
+    """Per-cell active force N(0, sigma^2) per component, drawn afresh at
+    every time step."""
+    rng = np.random.Generator(np.random.PCG64([seed, 7717, step]))
+    return np.ascontiguousarray(sigma * rng.standard_normal((n, 3)))
+
+
+def spheroid_200k(seed: int = 5000) -> Cells:
+    """The learned-warm-start workload's spheroid: 200,000 cells in a ball at
+    packing fraction 0.6 (radius 34.78), gamma in [0.1, 10], gamma0 = 1e-3."""
+    return ball(n=200_000, seed=seed, gamma0=1e-3)
