@@ -445,6 +445,127 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warm(args):
+    """The learned-warm-start workload: a 200,000-cell spheroid advanced by
+    x <- x + v dt (dt = 0.01) for ``--warm-steps`` steps under overlap springs
+    (k = 1) plus fresh active noise N(0, 0.1^2); graph, friction blocks,
+    spanning forest and factor are rebuilt every step.  The network is
+    trained (energy-norm loss, Adam) on the solver's solutions of the first
+    ``--warm-train`` steps and predicts v0 afterwards; each predicted step is
+    solved to the same tolerance from the learned v0, from zero and from the
+    previous step's v."""
+    import torch
+
+    import paper_2410_04512_gb300 as sgp
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgp.Context(0, stream)
+    peaks, peaks_src = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    c = workloads.spheroid_200k()
+    n = c.n
+    pos = torch.from_numpy(c.pos).to(dev)
+    radii = torch.from_numpy(c.radii).to(dev)
+    tp, tq = (torch.from_numpy(t).to(dev) for t in c.tables())
+    prec = sgp.PREC_MIXED if args.precision == "mixed" else sgp.PREC_F64
+    net = ctx.mpnn_create(workloads.mpnn_init(5000))
+    H = {"g": None, "M": None, "T": None, "Fh": None}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def build(step):
+        H["g"] = ctx.collision_graph(pos, radii, H["g"])
+        ij = H["g"].edges()
+        gp, gq = workloads.pair_gamma_torch(c.seed, ij, tp, tq)
+        H["M"] = ctx.friction_assemble(H["g"], pos, gp.contiguous(), gq.contiguous(), c.gamma0, prec, H["M"])
+        H["T"] = ctx.max_spanning_tree(H["M"], H["T"])
+        H["Fh"] = ctx.tree_factor(H["M"], H["T"], H["Fh"])
+        noise = torch.from_numpy(workloads.active_noise(c.seed, step, n)).to(dev)
+        return (workloads.spring_forces_torch(pos, radii, ij) + noise).contiguous()
+
+    def timed(fn):
+        a, b = ev(), ev()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    def solve(F, x0):
+        v = torch.zeros_like(F) if x0 is None else x0.clone()
+        _, inf = ctx.pcg_solve(H["M"], H["Fh"], F, v, tol=args.tol, precision=prec, x0_given=x0 is not None)
+        return v, inf
+
+    vprev = None
+    train_ms, rows = [], []
+    ctx.launch_count(reset=True)
+    with ClockSampler(0) as clk:
+        for step in range(1, args.warm_steps + 1):
+            F, build_ms = timed(lambda: build(step))
+            (vstar, inf0), zero_ms = timed(lambda: solve(F, None))
+            if step <= args.warm_train:
+                def train():
+                    L = 0.0
+                    for _ in range(args.warm_epochs):
+                        ctx.mpnn_forward(net, H["M"], H["Fh"], F, vprev)
+                        L = ctx.mpnn_backward(net, vstar, sgp.MPNN_LOSS_ENERGY)
+                        ctx.mpnn_step(net, args.warm_lr)
+                    return L
+                L, ms = timed(train)
+                train_ms.append(ms)
+                v_next = vstar
+            else:
+                (v0, used), inf_ms = timed(lambda: ctx.warm_start(net, H["M"], H["Fh"], F, vprev, mr_scale=True))
+                (vw, infw), warm_ms = timed(lambda: solve(F, v0))
+                (vp, infp), prev_ms = timed(lambda: solve(F, vprev))
+                e = (v0 - vstar).contiguous()
+                E = float(torch.sum(e * ctx.spmv(H["M"], e)) / torch.sum(vstar * F))
+                rows.append(dict(build=build_ms, zero=zero_ms, infer=inf_ms, warm=warm_ms, prev=prev_ms,
+                                 it0=inf0.iterations, itw=infw.iterations, itp=infp.iterations, used=used, E=E,
+                                 res=max(inf0.true_rel_residual, infw.true_rel_residual)))
+                v_next = vw
+            vprev = v_next
+            pos = (pos + 0.01 * v_next).contiguous()
+    launches = ctx.launch_count()
+    R = {k: np.array([r[k] for r in rows], dtype=np.float64) for k in rows[0]}
+    per_learned = R["build"] + R["infer"] + R["warm"]
+    per_zero = R["build"] + R["zero"]
+    per_prev = R["build"] + R["prev"]
+    value = len(rows) / (per_learned.sum() / 1e3)
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": 1,
+        "steps": len(rows), "warmup": args.warm_train, "ms_per_step": round(float(per_learned.mean()), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == sgp.PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "learned warm start: %d-cell spheroid (ball at packing 0.6), %d time steps "
+                               "x <- x + v dt, dt 0.01, overlap springs k=1 + active noise N(0,0.1^2), gamma "
+                               "log-uniform [0.1,10], gamma0 1e-3; trained on steps 1-%d (%d Adam steps per "
+                               "step, lr %g, energy-norm loss), predicting steps %d-%d"
+                               % (n, args.warm_steps, args.warm_train, args.warm_epochs, args.warm_lr,
+                                  args.warm_train + 1, args.warm_steps),
+                   "form": "%s precision, tree preconditioner, v0 from the network (minimal-residual "
+                           "scaled, residual-checked)" % args.precision,
+                   "tol": args.tol,
+                   "step": "collision graph + friction blocks + spanning forest + tree factor + network "
+                           "inference + PCG from v0"},
+        "learned": {"solves_per_s": round(value, 4), "iterations_mean": float(R["itw"].mean()),
+                    "inference_ms_mean": round(float(R["infer"].mean()), 3),
+                    "accepted": int(R["used"].sum()), "energy_error_median": float(np.median(R["E"]))},
+        "zero_guess": {"solves_per_s": round(len(rows) / (per_zero.sum() / 1e3), 4),
+                       "iterations_mean": float(R["it0"].mean())},
+        "previous_v": {"solves_per_s": round(len(rows) / (per_prev.sum() / 1e3), 4),
+                       "iterations_mean": float(R["itp"].mean())},
+        "solve_only_ms_mean": {"learned": round(float((R["infer"] + R["warm"]).mean()), 3),
+                               "zero": round(float(R["zero"].mean()), 3), "prev": round(float(R["prev"].mean()), 3)},
+        "build_ms_mean": round(float(R["build"].mean()), 3),
+        "training": {"steps": args.warm_train, "ms_per_step_mean": round(float(np.mean(train_ms)), 3)},
+        "true_rel_residual_max": float(R["res"].max()),
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "peak_hbm_gbs": hbm_peak, "peak_source": peaks_src,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle: cpu_baseline leg and the reference arm
 # ---------------------------------------------------------------------------
@@ -514,7 +635,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgp", choices=["sgp", "reference"])
-    ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS) + ["batch512"])
+    ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS) + ["batch512", "warm200k"])
     ap.add_argument("--batch", type=int, default=512, help="instances of the batch512 workload")
     ap.add_argument("--precision", default="mixed", choices=["f64", "mixed"])
     ap.add_argument("--precond", default="tree", choices=["tree", "jacobi", "none"])
@@ -523,6 +644,10 @@ def main():
     ap.add_argument("--compare", type=int, default=1, help="also time plain FP64 and block-Jacobi")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-sample-cells", type=int, default=20000)
+    ap.add_argument("--warm-steps", dest="warm_steps", type=int, default=200)
+    ap.add_argument("--warm-train", dest="warm_train", type=int, default=50)
+    ap.add_argument("--warm-epochs", dest="warm_epochs", type=int, default=8)
+    ap.add_argument("--warm-lr", dest="warm_lr", type=float, default=2e-3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "sgp":
         args.warmup = 3
@@ -530,6 +655,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch512":
         run_batch(args)
+    elif args.workload == "warm200k":
+        run_warm(args)
     else:
         run_gpu(args)
 

@@ -227,6 +227,66 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *matrix, const s
                                  int64_t n_instances, const int64_t *offsets, const double *F_dev,
                                  double *v_dev, const sgp_solve_opts *opts, sgp_solve_info *infos);
 
+/* ---- learned warm start (no counterpart in the paper) -----------------------
+ * A message-passing network over the collision graph predicts the initial
+ * guess v0 of the PCG of Section 1.1; the solver's own iteration count
+ * judges the prediction.  Width 64, three message-passing layers, BF16
+ * weights (round-to-nearest-even copies of FP32 master weights), FP32
+ * activations and accumulation:
+ *   basis  b0 = D^-1 F (block Jacobi), b1 = P^-1 F (spanning-forest factor),
+ *          b2 = v_prev (zero when NULL)
+ *   x_i    = |b0|, |b1|, |b2| / s; b0.b1, b0.b2, b1.b2 / s^2 (s = mean |b1|),
+ *            deg_i / 6, 1
+ *   h0 = relu(W_in x + b_in); h_{l+1} = relu(W_l [h_l ; mean_{j~i} h_l,j] + c_l)
+ *   c = W_out h3 + b_out; v0_i = sum_k c_ik b_i^(k)
+ * Parameters (FP32, flat, SGP_MPNN_PARAMS values) in the order W_in (64x8),
+ * b_in (64), then W_l (64x128), c_l (64) for l = 0, 1, 2, then W_out (3x64),
+ * b_out (3); matrices row-major.  Training minimises, with Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8), either loss against the converged solution v*:
+ *   SGP_MPNN_LOSS_L2:     |v0 - v*|^2 / |v*|^2
+ *   SGP_MPNN_LOSS_ENERGY: (v0 - v*)^T Gamma (v0 - v*) / v*^T Gamma v*, the
+ *                         error norm conjugate gradients minimises. */
+typedef struct sgp_mpnn sgp_mpnn;
+#define SGP_MPNN_PARAMS 25539
+#define SGP_MPNN_LOSS_L2 0
+#define SGP_MPNN_LOSS_ENERGY 1
+#define SGP_WARM_MR_SCALE 1
+/* Create a network from `count` (== SGP_MPNN_PARAMS) host FP32 parameters
+ * (copied; the caller keeps ownership).  INVALID_ARG on a wrong count. */
+sgp_status sgp_mpnn_create(sgp_ctx *ctx, const float *params_host, int64_t count, sgp_mpnn **net);
+void sgp_mpnn_destroy(sgp_mpnn *net);
+/* Copy the FP32 master parameters and/or the last gradient (each
+ * SGP_MPNN_PARAMS floats, host) out; either pointer may be NULL.
+ * Synchronises. */
+sgp_status sgp_mpnn_params(sgp_ctx *ctx, const sgp_mpnn *net, float *params_host, float *grads_host);
+/* Inference: v0_dev (n x 3 float64) from F_dev (n x 3), the matrix (for the
+ * neighbours and the block-Jacobi inverse), the factor of the same matrix
+ * and v_prev_dev (n x 3, or NULL).  Activations are kept in `net` for a
+ * following sgp_mpnn_backward; `matrix` must outlive that call.
+ * Asynchronous apart from building the block-Jacobi inverse once. */
+sgp_status sgp_mpnn_forward(sgp_ctx *ctx, sgp_mpnn *net, const sgp_matrix *matrix,
+                            const sgp_factor *factor, const double *F_dev, const double *v_prev_dev,
+                            double *v0_dev);
+/* Gradient of loss `loss_kind` (SGP_MPNN_LOSS_*) of the last forward pass
+ * against the target v_target_dev (n x 3 float64, the converged solution),
+ * kept in `net`; loss (host, may be NULL) receives the loss value
+ * (synchronises then).  The energy loss uses the matrix of the forward pass.
+ * The weight gradients are reduced in a fixed order: the same inputs give
+ * the same bits.  INVALID_ARG for an unknown loss or before any forward. */
+sgp_status sgp_mpnn_backward(sgp_ctx *ctx, sgp_mpnn *net, const double *v_target_dev, int32_t loss_kind,
+                             double *loss);
+/* One Adam step with learning rate lr > 0 on the last gradient; refreshes
+ * the BF16 weights.  Asynchronous. */
+sgp_status sgp_mpnn_step(sgp_ctx *ctx, sgp_mpnn *net, float lr);
+/* sgp_mpnn_forward, then (flag SGP_WARM_MR_SCALE) the minimal-residual
+ * rescaling v0 <- alpha v0, alpha = (Gamma v0)^T F / |Gamma v0|^2, then the
+ * acceptance test: v0 is kept when |F - Gamma v0| <= |F| (FP64), else set to
+ * 0 (the zero guess has the smaller residual).  used (host, may be NULL)
+ * receives 1 if v0 was kept.  INVALID_ARG for unknown flags.  Synchronises. */
+sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *net, const sgp_matrix *matrix,
+                          const sgp_factor *factor, const double *F_dev, const double *v_prev_dev,
+                          double *v0_dev, int32_t flags, int32_t *used);
+
 /* ---- kernel timing ----------------------------------------------------------
  * When enabled, the library brackets every launch of the named kernel class
  * with CUDA events on the context stream and accumulates the elapsed time,

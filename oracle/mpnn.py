@@ -149,7 +149,8 @@ def relu_ambiguous(params_flat, basis, ptr, nbr, rel: float = 2e-5, round_bf16: 
     Ws = [(p["W_in"], p["b_in"])] + [(p[f"W{l}"], p[f"c{l}"]) for l in range(3)]
     for layer, (u, (W, b)) in enumerate(zip(ins, Ws)):
         bound = np.abs(u) @ np.abs(W).T + np.abs(b)
-        cells, units = np.nonzero(np.abs(C["zs"][layer]) <= rel * bound)
+        # an all-zero input row and bias give z = 0 exactly in any precision
+        cells, units = np.nonzero((np.abs(C["zs"][layer]) <= rel * bound) & (bound > 0))
         out += [(layer, int(i), int(k)) for i, k in zip(cells, units)]
     return out
 

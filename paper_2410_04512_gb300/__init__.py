@@ -23,6 +23,9 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_NOT_SPD, ERR_NO_CONV
 PREC_F64, PREC_MIXED = 0, 1
 PRECOND_TREE, PRECOND_BLOCK_JACOBI, PRECOND_NONE = 0, 1, 2
 KT_SPMV, KT_TREE_SOLVE, KT_PCG_VECTOR = 0, 1, 2
+MPNN_PARAMS = 25539
+MPNN_LOSS_L2, MPNN_LOSS_ENERGY = 0, 1
+WARM_MR_SCALE = 1
 
 _STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "DEGENERATE", 5: "NOT_SPD",
                  6: "NO_CONVERGENCE", 7: "TIMEOUT"}
@@ -88,6 +91,13 @@ def load_library(path: str = LIB_PATH):
         "sgp_set_kernel_timing": ([P, I32], I32),
         "sgp_kernel_time": ([P, I32, ctypes.POINTER(D), ctypes.POINTER(I64), I32], I32),
         "sgp_launch_count": ([P, ctypes.POINTER(I64), I32], I32),
+        "sgp_mpnn_create": ([P, P, I64, PP], I32),
+        "sgp_mpnn_destroy": ([P], None),
+        "sgp_mpnn_params": ([P, P, P, P], I32),
+        "sgp_mpnn_forward": ([P, P, P, P, P, P, P], I32),
+        "sgp_mpnn_backward": ([P, P, P, I32, ctypes.POINTER(D)], I32),
+        "sgp_mpnn_step": ([P, P, ctypes.c_float], I32),
+        "sgp_warm_start": ([P, P, P, P, P, P, P, I32, ctypes.POINTER(I32)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -198,6 +208,21 @@ class Factor(_Handle):
         self.ctx._ok(_lib.sgp_factor_info(self.ptr, ctypes.byref(r), ctypes.byref(l), ctypes.byref(nb),
                                           ctypes.byref(nr)))
         return r.value, l.value, nb.value, nr.value
+
+
+class Mpnn(_Handle):
+    """The warm-start network (FP32 master weights and BF16 copies on the
+    device, Adam state, activations of the last forward pass)."""
+    _destroy = "sgp_mpnn_destroy"
+
+    def params(self):
+        """(master parameters, last gradient) as float32 numpy arrays."""
+        import numpy as np
+        p = np.empty(MPNN_PARAMS, dtype=np.float32)
+        g = np.empty(MPNN_PARAMS, dtype=np.float32)
+        self.ctx._ok(_lib.sgp_mpnn_params(self.ctx.ptr, self.ptr, p.ctypes.data_as(ctypes.c_void_p),
+                                          g.ctypes.data_as(ctypes.c_void_p)))
+        return p, g
 
 
 @dataclass
@@ -327,6 +352,50 @@ class Context:
         if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
             self._ok(rc)
         return v, out
+
+    # -- learned warm start ---------------------------------------------------
+    def mpnn_create(self, params) -> Mpnn:
+        import numpy as np
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        net = Mpnn(self)
+        self._ok(_lib.sgp_mpnn_create(self.ptr, p.ctypes.data_as(ctypes.c_void_p), p.size,
+                                      ctypes.byref(net.ptr)))
+        return net
+
+    def mpnn_forward(self, net: Mpnn, M: Matrix, Fh: Factor, F: torch.Tensor, v_prev: torch.Tensor | None = None,
+                     v0: torch.Tensor | None = None) -> torch.Tensor:
+        _check_vec(F, M.n, name="F")
+        if v_prev is not None:
+            _check_vec(v_prev, M.n, name="v_prev")
+        v0 = torch.empty_like(F) if v0 is None else v0
+        _check_vec(v0, M.n, name="v0")
+        net._M = M  # the activations refer to the matrix's neighbour lists
+        self._ok(_lib.sgp_mpnn_forward(self.ptr, net.ptr, M.ptr, Fh.ptr, _ptr(F), _ptr(v_prev), _ptr(v0)))
+        return v0
+
+    def mpnn_backward(self, net: Mpnn, v_target: torch.Tensor, loss: int = MPNN_LOSS_L2) -> float:
+        _check_vec(v_target, net._M.n, name="v_target")
+        L = ctypes.c_double()
+        self._ok(_lib.sgp_mpnn_backward(self.ptr, net.ptr, _ptr(v_target), loss, ctypes.byref(L)))
+        return L.value
+
+    def mpnn_step(self, net: Mpnn, lr: float):
+        self._ok(_lib.sgp_mpnn_step(self.ptr, net.ptr, float(lr)))
+
+    def warm_start(self, net: Mpnn, M: Matrix, Fh: Factor, F: torch.Tensor, v_prev: torch.Tensor | None = None,
+                   v0: torch.Tensor | None = None, mr_scale: bool = False):
+        """(v0, used): the network's guess, or zeros when it does not beat
+        the zero guess on the residual."""
+        _check_vec(F, M.n, name="F")
+        if v_prev is not None:
+            _check_vec(v_prev, M.n, name="v_prev")
+        v0 = torch.empty_like(F) if v0 is None else v0
+        _check_vec(v0, M.n, name="v0")
+        used = ctypes.c_int32()
+        net._M = M
+        self._ok(_lib.sgp_warm_start(self.ptr, net.ptr, M.ptr, Fh.ptr, _ptr(F), _ptr(v_prev), _ptr(v0),
+                                     WARM_MR_SCALE if mr_scale else 0, ctypes.byref(used)))
+        return v0, bool(used.value)
 
     # -- instrumentation ---------------------------------------------------
     def set_kernel_timing(self, enable: bool):

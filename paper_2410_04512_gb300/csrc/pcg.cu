@@ -589,6 +589,38 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
 
 }  // namespace
 
+// FP64 product y = Gamma v without the timing hooks (used by the warm-start
+// network's loss and scaling).
+sgp_status spmv64(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *y)
+{
+    LAUNCH(ctx, k_spmv<double>, grid_for(M->n, 128), 128, 0, make_blk<double>(M), bp<const int32_t>(M->row_ptr),
+           M->gamma0, M->n, v, y);
+    return SGP_OK;
+}
+
+// Warm-start acceptance: keep v0 only if |F - Gamma v0| <= |F| (otherwise
+// the zero guess has the smaller residual and v0 is cleared).
+sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *F, double *v0, int *used)
+{
+    const int64_t n = M->n;
+    *used = 0;
+    if (n == 0) return SGP_OK;
+    SGP_TRY(scratch_ensure(ctx, sizeof(double) * 2 * MAXP + 512));
+    double *partials = reinterpret_cast<double *>(ctx->d_scratch);
+    double *o2 = partials + 2 * MAXP;
+    SGP_CUDA(ctx, cudaMemsetAsync(o2, 0, 32, ctx->stream));
+    LAUNCH(ctx, k_resid64, red_grid(n), RB, 0, make_blk<double>(M), bp<const int32_t>(M->row_ptr), M->gamma0,
+           n, F, (const double *)v0, (double *)nullptr, partials, o2);
+    double h[2] = {0, 0};
+    SGP_TRY(read_back(ctx, h, o2, sizeof(h)));
+    if (h[0] <= h[1] && std::isfinite(h[0])) {
+        *used = 1;
+        return SGP_OK;
+    }
+    SGP_CUDA(ctx, cudaMemsetAsync(v0, 0, sizeof(double) * 3 * n, ctx->stream));
+    return SGP_OK;
+}
+
 extern "C" {
 
 sgp_status sgp_spmv(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *y)

@@ -78,10 +78,11 @@ def test_permutation_equivariance():
     np.testing.assert_allclose(v2, v[perm], rtol=1e-10, atol=1e-12)
 
 
-def test_untrained_network_returns_the_tree_solve():
+def test_output_head_selects_the_tree_solve():
     c, s, basis, ptr, nbr = small_problem()
     params = workloads.mpnn_init(5).astype(np.float64)
     params[-3 - 3 * 64:-3] = 0.0                   # W_out = 0
+    params[-3:] = (0.0, 1.0, 0.0)                  # b_out picks b1 = P^-1 F
     v = mpnn.forward(params, basis, ptr, nbr)
     np.testing.assert_array_equal(v, basis[1])
 
@@ -152,8 +153,10 @@ def test_relu_ambiguity_and_mask_flips():
     c, s, basis, ptr, nbr = small_problem()
     params = workloads.mpnn_init(9).astype(np.float64)
     target = np.random.default_rng(5).standard_normal((c.n, 3))
-    # a huge band marks every unit of every layer ...
-    assert len(mpnn.relu_ambiguous(params, basis, ptr, nbr, rel=2.0)) == 4 * c.n * mpnn.H
+    # a huge band marks every unit whose bound is nonzero ...
+    _, C0 = mpnn.forward(params, basis, ptr, nbr, cache=True)
+    nz = sum(int(np.sum(np.abs(C0["hs"][l]).sum(axis=1) + np.abs(C0["aggs"][l]).sum(axis=1) > 0)) for l in range(3))
+    assert len(mpnn.relu_ambiguous(params, basis, ptr, nbr, rel=2.0)) == (c.n + nz) * mpnn.H
     # ... a zero band none
     assert mpnn.relu_ambiguous(params, basis, ptr, nbr, rel=0.0) == []
     # flipping an inactive unit of the last layer adds exactly that unit's

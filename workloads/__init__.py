@@ -241,8 +241,9 @@ MPNN_H, MPNN_K, MPNN_DIN = 64, 3, 8
 def mpnn_init(seed: int = 5000) -> np.ndarray:
     """FP32 master parameters, flat, in the order W_in (64x8), b_in, then for
     each of 3 layers W (64x128) and c (64), then W_out (3x64), b_out (3).
-    Glorot-uniform matrices, zero biases, and b_out = (0, 1, 0) so that the
-    untrained network returns the spanning-forest solve P^-1 F."""
+    Glorot-uniform matrices, zero biases, W_out scaled by 0.01: the
+    untrained network returns a guess close to zero, so training starts
+    from the solver's own default."""
     g = _rng(seed, 5)
     H, K, D = MPNN_H, MPNN_K, MPNN_DIN
     parts = []
@@ -254,7 +255,7 @@ def mpnn_init(seed: int = 5000) -> np.ndarray:
     parts += [glorot(H, D).ravel(), np.zeros(H)]
     for _ in range(3):
         parts += [glorot(H, 2 * H).ravel(), np.zeros(H)]
-    parts += [0.01 * glorot(K, H).ravel(), np.array([0.0, 1.0, 0.0])]
+    parts += [0.01 * glorot(K, H).ravel(), np.zeros(K)]
     return np.concatenate(parts).astype(np.float32)
 
 
