@@ -242,6 +242,13 @@ def run_gpu(args):
 
     # ---- timed region: the chosen form, device-resident inputs ------------
     chosen = Form(args.precision, args.precond)
+    tuning = None
+    if args.autotune:
+        # launch shapes picked by the library's autotuner on this workload
+        # (outside the timed region; the factor is rebuilt every step anyway)
+        chosen.step(pos, radii, F, torch.zeros_like(F))
+        tuning = ctx.autotune(chosen.H["M"], chosen.H["T"], chosen.H["Fh"], F, precond=chosen.precond,
+                              precision=chosen.precision, iterations=args.autotune)
     with ClockSampler(local) as clk:
         res = chosen.timed(args.steps, args.warmup, kernel_timing=True)
     elapsed = res["elapsed"]
@@ -306,6 +313,7 @@ def run_gpu(args):
     # ---- the other forms on the same workload (outside the timed region) --
     forms = {}
     if rank == 0 and args.compare:
+        ctx.set_tuning()      # the other forms run with the built-in launch shapes
         for label, prec, pc, steps in (("plain_fp64_mst", "f64", "tree", 2), ("fp64_block_jacobi", "f64", "jacobi", 1)):
             if (prec, pc) == (args.precision, args.precond):
                 continue
@@ -340,6 +348,7 @@ def run_gpu(args):
         "time_share_ms": {"spmv": round(spmv_ms, 2), "tree_solve": round(tree_ms, 2),
                           "timed": round(elapsed * 1e3, 2)},
         "forms": forms,
+        "tuning": tuning if tuning is not None else ctx.get_tuning(),
         "clocks": clk.summary(),
     }
     if rank == 0 and args.cpu_baseline:
@@ -389,6 +398,11 @@ def run_batch(args):
         return ctx.pcg_solve_batched(H["M"], H["Fh"], off, F, v, tol=args.tol, precision=prec)[1]
 
     v = torch.zeros_like(F)
+    tuning = None
+    if args.autotune:
+        step(v)
+        tuning = ctx.autotune(H["M"], H["T"], H["Fh"], F, offsets=off, precision=prec,
+                              iterations=max(5, args.autotune // 3))
     for _ in range(args.warmup):
         step(v)
     torch.cuda.synchronize()
@@ -406,7 +420,9 @@ def run_batch(args):
     its = np.array([i.iterations for i in infos])
     res = np.array([i.true_rel_residual for i in infos])
 
-    # the plain solver looped over the same instances (FP64, one at a time)
+    # the plain solver looped over the same instances (FP64, one at a time,
+    # built-in launch shapes)
+    ctx.set_tuning()
     lat = []
     Hs = {"g": None, "M": None, "T": None, "Fh": None}
     for s in range(len(cells)):
@@ -440,7 +456,7 @@ def run_batch(args):
                        "looped_plain_fp64_p50": round(float(np.percentile(lat, 50)), 3),
                        "looped_plain_fp64_p99": round(float(np.percentile(lat, 99)), 3)},
         "looped_plain_fp64": {"value": round(len(cells) / (lat.sum() / 1e3), 3), "unit": "instance solves/s"},
-        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "gpu_launches": int(launches), "tuning": tuning, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -644,6 +660,8 @@ def main():
     ap.add_argument("--compare", type=int, default=1, help="also time plain FP64 and block-Jacobi")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-sample-cells", type=int, default=20000)
+    ap.add_argument("--autotune", type=int, default=30,
+                    help="PCG iterations per autotuner candidate before timing (0: built-in defaults)")
     ap.add_argument("--warm-steps", dest="warm_steps", type=int, default=200)
     ap.add_argument("--warm-train", dest="warm_train", type=int, default=50)
     ap.add_argument("--warm-epochs", dest="warm_epochs", type=int, default=8)

@@ -287,6 +287,44 @@ sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *net, const sgp_matrix *matrix,
                           const sgp_factor *factor, const double *F_dev, const double *v_prev_dev,
                           double *v0_dev, int32_t flags, int32_t *used);
 
+/* ---- tuning (no counterpart in the paper) -----------------------------------
+ * Launch-shape knobs of the solver, kept per context. */
+typedef struct {
+    int32_t spmv_lpr;    /* lanes per block row of the PCG product: 1, 2, 4 or 8;
+                            0 = default (1 for FP64, 2 for FP32) */
+    int32_t tail_cap;    /* the tree solve runs its last contraction levels in one
+                            thread block once at most tail_cap vertices are left
+                            (-1: as many as fit in shared memory; 0: no tail;
+                            default 1024); read when a factor is built */
+    int32_t batch_chunk; /* rows per work item of the batched solver: 0 (default
+                            2048) or 256..65536 */
+    int32_t comp_size;   /* block of the tree factor's local phase: the forest is
+                            cut into blocks of comp_size consecutive vertices of a
+                            depth-first order, and the contraction levels that
+                            stay inside blocks run block by block in shared
+                            memory; 0 (none) or a power of two in 64..8192
+                            (default 0); read when a factor is built */
+    double ms_per_iteration; /* sgp_autotune: time of one PCG iteration with the
+                                chosen values; 0 from sgp_get_tuning */
+} sgp_tuning;
+sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *tuning);
+/* INVALID_ARG for a value outside the ranges above (nothing is changed). */
+sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *tuning);
+/* Time `iterations` PCG iterations (opts' precision and preconditioner, the
+ * tolerance ignored) of the caller's system for each candidate and keep the
+ * fastest, one knob after the other: comp_size in {0, 256, 512, 1024, 2048,
+ * 4096} and tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} (tree
+ * preconditioner only; *factor is rebuilt from `tree` for each candidate
+ * and left built with the chosen values), then spmv_lpr in
+ * {1, 2, 4, 8}, then, when n_instances > 0 (a batch with host `offsets`, as
+ * for sgp_pcg_solve_batched), batch_chunk in {512, ..., 8192} with the
+ * batched solver timed throughout.  The choice is stored in the context and
+ * copied to `out` (may be NULL).  F_dev is only read.  On failure the
+ * previous tuning is restored.  Synchronises. */
+sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_tree *tree, sgp_factor **factor,
+                        int64_t n_instances, const int64_t *offsets, const double *F_dev,
+                        const sgp_solve_opts *opts, int32_t iterations, sgp_tuning *out);
+
 /* ---- kernel timing ----------------------------------------------------------
  * When enabled, the library brackets every launch of the named kernel class
  * with CUDA events on the context stream and accumulates the elapsed time,

@@ -43,6 +43,14 @@ class SolveOpts(ctypes.Structure):
                 ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("spmv_lpr", ctypes.c_int32), ("tail_cap", ctypes.c_int32), ("batch_chunk", ctypes.c_int32),
+                ("comp_size", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("outer_iterations", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
@@ -91,6 +99,9 @@ def load_library(path: str = LIB_PATH):
         "sgp_set_kernel_timing": ([P, I32], I32),
         "sgp_kernel_time": ([P, I32, ctypes.POINTER(D), ctypes.POINTER(I64), I32], I32),
         "sgp_launch_count": ([P, ctypes.POINTER(I64), I32], I32),
+        "sgp_get_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "sgp_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "sgp_autotune": ([P, P, P, PP, I64, P, P, ctypes.POINTER(SolveOpts), I32, ctypes.POINTER(Tuning)], I32),
         "sgp_mpnn_create": ([P, P, I64, PP], I32),
         "sgp_mpnn_destroy": ([P], None),
         "sgp_mpnn_params": ([P, P, P, P], I32),
@@ -396,6 +407,35 @@ class Context:
         self._ok(_lib.sgp_warm_start(self.ptr, net.ptr, M.ptr, Fh.ptr, _ptr(F), _ptr(v_prev), _ptr(v0),
                                      WARM_MR_SCALE if mr_scale else 0, ctypes.byref(used)))
         return v0, bool(used.value)
+
+    # -- tuning ------------------------------------------------------------------
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._ok(_lib.sgp_get_tuning(self.ptr, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, comp_size: int = 0):
+        """Set the launch-shape knobs (the defaults are the library's)."""
+        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, 0.0)
+        self._ok(_lib.sgp_set_tuning(self.ptr, ctypes.byref(t)))
+
+    def autotune(self, M: Matrix, T: Tree | None, Fh: Factor | None, F: torch.Tensor, offsets=None,
+                 precond: int = PRECOND_TREE, precision: int = PREC_F64, iterations: int = 30) -> dict:
+        """Pick the launch-shape knobs by timing `iterations` PCG iterations
+        per candidate (rebuilds Fh in place for each tail size)."""
+        import numpy as np
+        _check_vec(F, M.n, name="F")
+        o = SolveOpts(1e-8, iterations, precond, precision, 0, 0, 0.0)
+        t = Tuning()
+        if offsets is not None:
+            off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+            k, offp = len(off) - 1, off.ctypes.data_as(ctypes.c_void_p)
+        else:
+            k, offp = 0, None
+        self._ok(_lib.sgp_autotune(self.ptr, M.ptr, T.ptr if T is not None else None,
+                                   ctypes.byref(Fh.ptr) if Fh is not None else None, k, offp, _ptr(F),
+                                   ctypes.byref(o), iterations, ctypes.byref(t)))
+        return t.as_dict()
 
     # -- instrumentation ---------------------------------------------------
     def set_kernel_timing(self, enable: bool):

@@ -396,6 +396,10 @@ sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
     ctx->use_graphs = (ng && ng[0] == '1') ? 0 : 1;
     const char *lpr = getenv("SGP_SPMV_LPR");
     if (lpr) ctx->spmv_lpr = atoi(lpr);
+    const char *np = getenv("SGP_NO_PDL");
+    ctx->use_pdl = (np && np[0] == '1') ? 0 : 1;
+    const char *tc = getenv("SGP_TAIL_CAP");
+    if (tc) ctx->tail_cap = atoi(tc);
     if (scratch_ensure(ctx, 1 << 20) != SGP_OK || cudaMalloc(&ctx->d_flags, 4096) != cudaSuccess ||
         cudaMemset(ctx->d_flags, 0, 4096) != cudaSuccess) {
         cudaGetLastError();

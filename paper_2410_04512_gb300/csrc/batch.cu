@@ -8,7 +8,7 @@
 // scalars (Section 1.1): each instance has its own rho, alpha, beta and
 // stopping test |r_s| <= tol |F_s|.
 //
-// Work items are (instance, chunk of <= CH rows).  Each reduction kernel
+// Work items are (instance, chunk of <= CH rows; CH is a tuning knob).  Each reduction kernel
 // writes one partial per chunk; the last chunk of an instance to arrive (a
 // per-instance arrival counter) sums that instance's partials in chunk order
 // and updates the instance's scalars -- deterministic, no float atomics.
@@ -22,7 +22,7 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
 namespace {
 
 constexpr int BB = 256;    // threads per block (one block per chunk)
-constexpr int CH = 2048;   // rows per chunk
+constexpr int CH_DEFAULT = 2048;   // rows per chunk unless tuned
 
 struct BScal {
     double rho, alpha, beta, FF, stop2, rr, pq, rz;
@@ -475,6 +475,7 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *M, const sgp_fa
     }
     SGP_CUDA(ctx, cudaSetDevice(ctx->device));
     // chunk table: instances cut into chunks of at most CH rows
+    const int CH = ctx->batch_chunk > 0 ? ctx->batch_chunk : CH_DEFAULT;
     std::vector<int32_t> chunk_inst, chunk_row, inst_chunk(n_inst + 1), inst_row(n_inst + 1);
     for (int64_t s = 0; s < n_inst; ++s) {
         inst_chunk[s] = (int32_t)chunk_inst.size();

@@ -114,6 +114,157 @@ __global__ void k_acc_init(const int32_t *__restrict__ adj_ptr, int64_t n,
     alive[v] = (int32_t)v;
 }
 
+// ----------------------------------------- depth-first preorder of the forest
+// Euler tour: directed slot s of u (u -> v = nbr[s]) is followed by the slot
+// after twin(s) in v's sorted list, cyclically.  Each tree's tour starts at
+// its root's first slot (the root is the tree's label from the spanning
+// forest); the slot whose successor would wrap around to it ends the tour.
+__global__ void k_et_init(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ nbr,
+                          const int32_t *__restrict__ twin, const int32_t *__restrict__ comp, int64_t n,
+                          int32_t *succ, int32_t *dist)
+{
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s) {
+        const int32_t v = nbr[s], t = twin[s];
+        const bool wrap = t + 1 >= adj_ptr[v + 1];
+        if (wrap && comp[v] == v) {
+            succ[s] = -1;
+            dist[s] = 0;
+        } else {
+            succ[s] = wrap ? adj_ptr[v] : t + 1;
+            dist[s] = 1;
+        }
+    }
+}
+
+// one round of pointer jumping: dist becomes the number of slots to the end
+__global__ void k_et_jump(int64_t m2, const int32_t *__restrict__ succ, const int32_t *__restrict__ dist,
+                          int32_t *succ2, int32_t *dist2)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= m2) return;
+    const int32_t nx = succ[s];
+    if (nx < 0) {
+        succ2[s] = -1;
+        dist2[s] = dist[s];
+    } else {
+        succ2[s] = succ[nx];
+        dist2[s] = dist[s] + dist[nx];
+    }
+}
+
+__global__ void k_root_flag(const int32_t *__restrict__ comp, int64_t n, int32_t *flag)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = comp[v] == (int32_t)v;
+}
+
+// tree index (rank of the root among roots) and tree sizes
+__global__ void k_tree_index(const int32_t *__restrict__ comp, const int32_t *__restrict__ rank, int64_t n,
+                             int32_t *tid, int32_t *size)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t t = rank[comp[v]];
+    tid[v] = t;
+    atomicAdd(size + t, 1);
+}
+
+// A slot is a down edge (parent -> child) if the tour takes it before its
+// twin.  Down flags are laid out in tour order, trees one after another
+// (tree t's tour starts at 2 (voff[t] - t), voff the exclusive sum of sizes).
+__device__ __forceinline__ int32_t tour_index(int32_t s, int32_t t, const int32_t *voff, const int32_t *size,
+                                              const int32_t *dist)
+{
+    return 2 * (voff[t] - t) + (2 * (size[t] - 1) - 1 - dist[s]);
+}
+
+__global__ void k_et_down(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ twin,
+                          const int32_t *__restrict__ dist, const int32_t *__restrict__ tid,
+                          const int32_t *__restrict__ voff, const int32_t *__restrict__ size, int64_t n,
+                          int64_t ns, int32_t *down, int *err)
+{
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t t = tid[u];
+    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s) {
+        const int32_t k = tour_index(s, t, voff, size, dist);
+        if (k < 0 || k >= ns) {      // not a tour: record, skip the write
+            atomicOr(err, 8);
+            continue;
+        }
+        down[k] = dist[s] > dist[twin[s]];
+    }
+}
+
+// preorder number: the root of tree t gets voff[t]; the head of a down edge
+// gets 1 + (down edges before it in the tour) + t
+__global__ void k_preorder(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ nbr,
+                           const int32_t *__restrict__ twin, const int32_t *__restrict__ dist,
+                           const int32_t *__restrict__ tid, const int32_t *__restrict__ voff,
+                           const int32_t *__restrict__ size, const int32_t *__restrict__ dscan,
+                           const int32_t *__restrict__ comp, int64_t n, int64_t ns, int32_t *pre, int *err)
+{
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t t = tid[u];
+    if (comp[u] == (int32_t)u) pre[u] = voff[t];
+    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s)
+        if (dist[s] > dist[twin[s]]) {
+            const int32_t k = tour_index(s, t, voff, size, dist);
+            if (k < 0 || k >= ns) {
+                atomicOr(err, 8);
+                continue;
+            }
+            pre[nbr[s]] = 1 + dscan[k] + t;
+        }
+}
+
+// inverse permutation, and the vertices with a tree neighbour in another block
+__global__ void k_blocks(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ nbr,
+                         const int32_t *__restrict__ pre, int64_t n, int32_t shift, int32_t *inv_pre,
+                         int32_t *pinned, int *err)
+{
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t pu = pre[u];
+    if (pu < 0 || pu >= n) {
+        atomicOr(err, 8);
+        pinned[u] = 1;
+        return;
+    }
+    inv_pre[pu] = (int32_t)u;
+    int32_t pin = 0;
+    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s)
+        if ((pre[nbr[s]] >> shift) != (pu >> shift)) pin = 1;
+    pinned[u] = pin;
+}
+
+// in-block index of each listed vertex
+__global__ void k_loc_map(const int32_t *__restrict__ src, const int32_t *__restrict__ pre, int32_t count,
+                          int32_t mask, int32_t *dst)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) dst[k] = pre[src[k]] & mask;
+}
+
+// out[c] = first k in [lo, hi) whose vertex lies in block >= c (the list is
+// in preorder within a level), c = 0..nb
+__global__ void k_block_ranges(const int32_t *__restrict__ list, const int32_t *__restrict__ pre, int32_t lo,
+                               int32_t hi, int32_t nb, int32_t shift, int32_t *out)
+{
+    int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nb) return;
+    int32_t a = lo, b = hi;
+    while (a < b) {
+        const int32_t m = (a + b) >> 1;
+        if ((pre[list[m]] >> shift) < c) a = m + 1;
+        else b = m;
+    }
+    out[c] = a;
+}
+
 // -------------------------------------------------------- structure: select
 __device__ __forceinline__ uint32_t mix32(uint32_t x)
 {
@@ -142,11 +293,16 @@ struct Sim {
 // degree-2 neighbours by the level's hash.  No two chosen vertices are
 // adjacent, and each has at most two neighbours, so eliminating them all at
 // once equals eliminating them one by one: the forest stays a forest.
-__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt)
+// Pinned vertices (local phase: a tree neighbour in another block) are never
+// chosen, and the rules that defer to a neighbour ignore pinned neighbours.
+__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt,
+                         const int32_t *__restrict__ pin)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= na) return;
     const int32_t v = A[k];
+    if (pin && pin[v]) return;
+    auto free_ = [&](int32_t u) { return !(pin && pin[u]); };
     const int32_t d = S.deg[v];
     if (d == 0) {
         S.lev[v] = level;
@@ -162,7 +318,7 @@ __global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32
         }
     const int32_t a = S.nbr[e1];
     if (d == 1) {
-        if (S.deg[a] == 1 && a > v) return;
+        if (S.deg[a] == 1 && a > v && free_(a)) return;
         S.lev[v] = level;
         S.nrec[v] = 1;
         S.rq[v] = make_int2(a, -1);
@@ -172,9 +328,9 @@ __global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32
     }
     const int32_t b = S.nbr[e2];
     const int32_t da = S.deg[a], db = S.deg[b];
-    if (da == 1 || db == 1) return;
-    if (da == 2 && key_less(a, v, salt)) return;
-    if (db == 2 && key_less(b, v, salt)) return;
+    if ((da == 1 && free_(a)) || (db == 1 && free_(b))) return;
+    if (da == 2 && free_(a) && key_less(a, v, salt)) return;
+    if (db == 2 && free_(b) && key_less(b, v, salt)) return;
     const bool sw = a > b;
     S.lev[v] = level;
     S.nrec[v] = 2;
@@ -412,23 +568,41 @@ __global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__rest
     if (k >= cnt || (done && *done)) return;
     const int32_t q = rv[r0 + k];
     const int32_t j0 = rc_ptr[r0 + k], j1 = rc_ptr[r0 + k + 1];
-    // the first contributor's block and vertex do not depend on the
-    // previous level: load them before waiting
-    T L0[9];
+    // Contributor ids and L blocks do not depend on the previous level: load
+    // the first FWD_PRE of them before waiting, so that after the wait all
+    // their w loads go out together (one memory round trip per level).
+    constexpr int FWD_PRE = 4;
+    T Lr[FWD_PRE][9];
+    int32_t cr[FWD_PRE];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) L0[a] = Lf[9 * (int64_t)j0 + a];
-    const int32_t c0 = ctv[j0];
-    pdl_wait();
-    T s[3];
-    {
-        T x[3] = {w[3 * (int64_t)c0], w[3 * (int64_t)c0 + 1], w[3 * (int64_t)c0 + 2]};
-        full_mv(L0, x, s);
+    for (int e = 0; e < FWD_PRE; ++e) {
+        const int32_t j = j0 + e;
+        cr[e] = j < j1 ? ctv[j] : -1;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) Lr[e][a] = j < j1 ? Lf[9 * (int64_t)j + a] : T(0);
     }
-    for (int32_t j = j0 + 1; j < j1; ++j) {
-        int32_t c = ctv[j];
-        T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
+    pdl_wait();
+    T x[FWD_PRE][3];
+#pragma unroll
+    for (int e = 0; e < FWD_PRE; ++e) {
+        const int64_t c = cr[e] >= 0 ? cr[e] : q;
+        x[e][0] = w[3 * c];
+        x[e][1] = w[3 * c + 1];
+        x[e][2] = w[3 * c + 2];
+    }
+    T s[3] = {0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < FWD_PRE; ++e) {
+        if (cr[e] < 0) break;
         T y[3];
-        full_mv(Lf + 9 * (int64_t)j, x, y);
+        full_mv(Lr[e], x[e], y);
+        s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+    }
+    for (int32_t j = j0 + FWD_PRE; j < j1; ++j) {
+        int32_t c = ctv[j];
+        T xx[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
+        T y[3];
+        full_mv(Lf + 9 * (int64_t)j, xx, y);
         s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
     }
     w[3 * (int64_t)q] -= s[0];
@@ -449,24 +623,147 @@ __global__ void k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__res
     const int32_t t = p0 + k;
     const int32_t c = ord[t];
     const int32_t pa = pr_ptr[t], pb = pr_ptr[t + 1];
+    // An eliminated vertex has at most two receivers (a leaf one, a
+    // compressed vertex two): load their ids, L blocks and D^-1 before
+    // waiting; after the wait the three vector loads go out together.
     T Di[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) Di[a] = Dinv[6 * (int64_t)t + a];
-    const int32_t q0 = pa < pb ? pr_q[pa] : 0;
+    int32_t qr[2];
+    T Lr[2][9];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int32_t p = pa + e;
+        qr[e] = p < pb ? pr_q[p] : -1;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) Lr[e][a] = p < pb ? L[9 * (int64_t)p + a] : T(0);
+    }
     pdl_wait();
     T x[3] = {w[3 * (int64_t)c], w[3 * (int64_t)c + 1], w[3 * (int64_t)c + 2]};
+    T y[2][3];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int64_t q = qr[e] >= 0 ? qr[e] : c;
+        y[e][0] = w[3 * q];
+        y[e][1] = w[3 * q + 1];
+        y[e][2] = w[3 * q + 2];
+    }
     T z[3];
     sym_mv(Di, x, z);
-    for (int32_t p = pa; p < pb; ++p) {
-        int32_t q = p == pa ? q0 : pr_q[p];
-        T y[3] = {w[3 * (int64_t)q], w[3 * (int64_t)q + 1], w[3 * (int64_t)q + 2]};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        if (qr[e] < 0) break;
         T u[3];
-        full_mtv(L + 9 * (int64_t)p, y, u);
+        full_mtv(Lr[e], y[e], u);
+        z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+    }
+    for (int32_t p = pa + 2; p < pb; ++p) {   // not reached for a forest
+        int32_t q = pr_q[p];
+        T yy[3] = {w[3 * (int64_t)q], w[3 * (int64_t)q + 1], w[3 * (int64_t)q + 2]};
+        T u[3];
+        full_mtv(L + 9 * (int64_t)p, yy, u);
         z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
     }
     w[3 * (int64_t)c] = z[0];
     w[3 * (int64_t)c + 1] = z[1];
     w[3 * (int64_t)c + 2] = z[2];
+}
+
+// Local levels: one thread block per block of comp_size consecutive
+// preorder numbers.  Every vertex eliminated in a local level has all its
+// tree neighbours (and so all its receivers) in its own block, so the block
+// runs all local levels on its slice of the vector in shared memory, with
+// block barriers between levels, and touches global memory only to gather
+// the slice at the start and scatter it at the end.
+struct Local {
+    int32_t nlev, nb, shift, n;
+    const int32_t *inv_pre, *roff, *poff, *rc_ptr, *pr_ptr, *loc_r, *loc_c, *loc_o, *loc_q;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_local_fwd(Local a, const T *__restrict__ Lf, T *w, const int *done)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    pdl_trigger();
+    if (done && *done) return;
+    const int32_t c = blockIdx.x, base = c << a.shift;
+    const int32_t cnt = min(1 << a.shift, a.n - base);
+    pdl_wait();
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        sw[3 * i] = w[3 * v];
+        sw[3 * i + 1] = w[3 * v + 1];
+        sw[3 * i + 2] = w[3 * v + 2];
+    }
+    __syncthreads();
+    for (int l = 0; l < a.nlev; ++l) {
+        const int32_t *ro = a.roff + (size_t)l * (a.nb + 1);
+        const int32_t k1 = ro[c + 1];
+        for (int32_t k = ro[c] + threadIdx.x; k < k1; k += blockDim.x) {
+            T s[3] = {0, 0, 0};
+            for (int32_t j = a.rc_ptr[k]; j < a.rc_ptr[k + 1]; ++j) {
+                T y[3];
+                full_mv(Lf + 9 * (int64_t)j, sw + 3 * a.loc_c[j], y);
+                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+            }
+            const int32_t q = a.loc_r[k];
+            sw[3 * q] -= s[0];
+            sw[3 * q + 1] -= s[1];
+            sw[3 * q + 2] -= s[2];
+        }
+        __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        w[3 * v] = sw[3 * i];
+        w[3 * v + 1] = sw[3 * i + 1];
+        w[3 * v + 2] = sw[3 * i + 2];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_local_bwd(Local a, const T *__restrict__ L, const T *__restrict__ Dinv,
+                                                   T *w, const int *done)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sw = reinterpret_cast<T *>(smem_raw);
+    pdl_trigger();
+    if (done && *done) return;
+    const int32_t c = blockIdx.x, base = c << a.shift;
+    const int32_t cnt = min(1 << a.shift, a.n - base);
+    pdl_wait();
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        sw[3 * i] = w[3 * v];
+        sw[3 * i + 1] = w[3 * v + 1];
+        sw[3 * i + 2] = w[3 * v + 2];
+    }
+    __syncthreads();
+    for (int l = a.nlev - 1; l >= 0; --l) {
+        const int32_t *po = a.poff + (size_t)l * (a.nb + 1);
+        const int32_t t1 = po[c + 1];
+        for (int32_t t = po[c] + threadIdx.x; t < t1; t += blockDim.x) {
+            const int32_t i = a.loc_o[t];
+            T z[3];
+            sym_mv(Dinv + 6 * (int64_t)t, sw + 3 * i, z);
+            for (int32_t p = a.pr_ptr[t]; p < a.pr_ptr[t + 1]; ++p) {
+                T u[3];
+                full_mtv(L + 9 * (int64_t)p, sw + 3 * a.loc_q[p], u);
+                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+            }
+            sw[3 * i] = z[0];
+            sw[3 * i + 1] = z[1];
+            sw[3 * i + 2] = z[2];
+        }
+        __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        w[3 * v] = sw[3 * i];
+        w[3 * v + 1] = sw[3 * i + 1];
+        w[3 * v + 2] = sw[3 * i + 2];
+    }
 }
 
 // The last levels (the vertices at elimination positions >= P0) in one
@@ -489,26 +786,26 @@ __host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size
 template <typename T>
 __host__ __device__ inline size_t tail_smem_bytes(int32_t n, int32_t np, int32_t nr)
 {
-    return tail_align(sizeof(T) * 9 * (size_t)n) + tail_align(sizeof(T) * 9 * (size_t)np) +
-           tail_align(4 * (size_t)(n + 1)) + 3 * tail_align(4 * (size_t)np) + tail_align(4 * (size_t)(nr + 1)) +
-           tail_align(4 * (size_t)nr);
+    return tail_align(sizeof(T) * 3 * (size_t)n) + tail_align(4 * (size_t)(n + 1)) + 3 * tail_align(4 * (size_t)np) +
+           tail_align(4 * (size_t)(nr + 1)) + tail_align(4 * (size_t)nr);
 }
 
+// Only the vectors and the local index lists live in shared memory; L and
+// D^-1 (each read once per direction) stream from global memory in level
+// order, so the tail holds several thousand vertices.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__restrict__ ord,
                                                     const int32_t *__restrict__ rc_ptr,
                                                     const int32_t *__restrict__ pr_ptr,
-                                                    const T *__restrict__ L, const T *__restrict__ Dinv,
-                                                    T *w, const int *done)
+                                                    const T *__restrict__ L, const T *__restrict__ Lf,
+                                                    const T *__restrict__ Dinv, T *w, const int *done)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_trigger();
     if (done && *done) return;
     unsigned char *cur = smem_raw;
     auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
-    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 9 * tl.n));  // w (3) then D^-1 (6) per vertex
-    T *sD = sw + 3 * tl.n;
-    T *sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * tl.np));
+    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * tl.n));
     int32_t *spr = reinterpret_cast<int32_t *>(take(4 * (tl.n + 1)));
     int32_t *stb = reinterpret_cast<int32_t *>(take(4 * tl.np));
     int32_t *spc = reinterpret_cast<int32_t *>(take(4 * tl.np));
@@ -516,9 +813,8 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
     int32_t *src = reinterpret_cast<int32_t *>(take(4 * (tl.nr + 1)));
     int32_t *stq = reinterpret_cast<int32_t *>(take(4 * tl.nr));
     (void)take(0);
-    // stage the factor (independent of the previous kernel)
-    for (int32_t i = threadIdx.x; i < 6 * tl.n; i += blockDim.x) sD[i] = Dinv[6 * (int64_t)tl.P0 + i];
-    for (int32_t i = threadIdx.x; i < 9 * tl.np; i += blockDim.x) sL[i] = L[9 * (int64_t)tl.Q0 + i];
+    const T *Lt = L + 9 * (int64_t)tl.Q0, *Lft = Lf + 9 * (int64_t)tl.C0, *Dt = Dinv + 6 * (int64_t)tl.P0;
+    // stage the index lists (independent of the previous kernel)
     for (int32_t i = threadIdx.x; i <= tl.n; i += blockDim.x) spr[i] = pr_ptr[tl.P0 + i] - tl.Q0;
     for (int32_t i = threadIdx.x; i < tl.np; i += blockDim.x) {
         stb[i] = tl.tb[i];
@@ -540,9 +836,8 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
         for (int32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             T s[3] = {0, 0, 0};
             for (int32_t j = src[k]; j < src[k + 1]; ++j) {
-                const int32_t p = sct[j];
                 T y[3];
-                full_mv(sL + 9 * p, sw + 3 * spc[p], y);
+                full_mv(Lft + 9 * (int64_t)j, sw + 3 * spc[sct[j]], y);
                 s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
             }
             const int32_t q = stq[k];
@@ -556,10 +851,10 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
         const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
         for (int32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             T z[3];
-            sym_mv(sD + 6 * i, sw + 3 * i, z);
+            sym_mv(Dt + 6 * (int64_t)i, sw + 3 * i, z);
             for (int32_t p = spr[i]; p < spr[i + 1]; ++p) {
                 T u[3];
-                full_mtv(sL + 9 * p, sw + 3 * stb[p], u);
+                full_mtv(Lt + 9 * (int64_t)p, sw + 3 * stb[p], u);
                 z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
             }
             sw[3 * i] = z[0];
@@ -609,20 +904,34 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
                   *ctv = bp<const int32_t>(F->ctv), *ord = bp<const int32_t>(F->ord),
                   *prp = bp<const int32_t>(F->pr_ptr), *prq = bp<const int32_t>(F->pr_q);
     const int B = 128;
-    const int lt = F->tail_level;
-    for (int l = 0; l < lt; ++l) {
+    // the tail was sized for the factor's own precision; an FP64 apply of a
+    // MIXED factor whose tail does not fit runs every level as its own kernel
+    int lt = F->tail_level;
+    if (lt < F->levels) {
+        const Tail tl = tail_of(F);
+        if (tail_smem_bytes<T>(tl.n, tl.np, tl.nr) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
+    }
+    const int L1 = F->local_levels;
+    Local la{L1, F->ncomp, 0, (int32_t)F->n, bp<const int32_t>(F->inv_pre), bp<const int32_t>(F->roff),
+             bp<const int32_t>(F->poff), rc, prp, bp<const int32_t>(F->loc_r), bp<const int32_t>(F->loc_c),
+             bp<const int32_t>(F->loc_o), bp<const int32_t>(F->loc_q)};
+    while ((1 << la.shift) < F->comp_size) ++la.shift;
+    const size_t lsm = sizeof(T) * 3 * (size_t)F->comp_size;
+    if (L1 > 0) LAUNCH_PDL(ctx, k_local_fwd<T>, F->ncomp, 256, lsm, la, Lf, w, done);
+    for (int l = L1; l < lt; ++l) {
         int32_t r0 = F->rl_ptr[l], cnt = F->rl_ptr[l + 1] - r0;
         if (cnt > 0) LAUNCH_PDL(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ctv, Lf, r0, cnt, w, done);
     }
     if (lt < F->levels) {
         const Tail tl = tail_of(F);
         const size_t smem = tail_smem_bytes<T>(tl.n, tl.np, tl.nr);
-        LAUNCH_PDL(ctx, k_tree_tail<T>, 1, 1024, smem, tl, ord, rc, prp, L, Dinv, w, done);
+        LAUNCH_PDL(ctx, k_tree_tail<T>, 1, 1024, smem, tl, ord, rc, prp, L, Lf, Dinv, w, done);
     }
-    for (int l = lt - 1; l >= 0; --l) {
+    for (int l = lt - 1; l >= L1; --l) {
         int32_t p0 = F->lvl_ptr[l], cnt = F->lvl_ptr[l + 1] - p0;
         if (cnt > 0) LAUNCH_PDL(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
     }
+    if (L1 > 0) LAUNCH_PDL(ctx, k_local_bwd<T>, F->ncomp, 256, lsm, la, L, Dinv, w, done);
     return SGP_OK;
 }
 template sgp_status tree_apply_inplace<double>(sgp_ctx *, const sgp_factor *, double *, const int *);
@@ -636,6 +945,10 @@ static sgp_status tail_smem_optin(sgp_ctx *ctx)
     const int bytes = TREE_TAIL_SMEM;
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (ctx->device >= 0 && ctx->device < 64) done_dev[ctx->device] = 1;
     return SGP_OK;
 }
@@ -766,17 +1079,94 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
            M->gamma0, bp<double>(F->acc), deg, lev, A);
     SGP_CUDA(ctx, cudaMemsetAsync(rflag, 0, sizeof(int32_t) * n1, ctx->stream));
 
+    // local phase: depth-first preorder, blocks of comp_size consecutive
+    // preorder numbers, pinned vertices; the alive list starts in preorder so
+    // that every per-level list comes out grouped by block
+    const int32_t B = ctx->comp_size;
+    const bool local = B > 0;
+    int32_t shift = 0;
+    int32_t *pinned = nullptr;
+    F->comp_size = local ? B : 0;
+    F->local_levels = 0;
+    F->ncomp = 0;
+    if (local) {
+        while ((1 << shift) < B) ++shift;
+        F->ncomp = (int32_t)((n + B - 1) >> shift);
+        SGP_TRY(buf_ensure(ctx, F->pre, sizeof(int32_t) * n1));
+        SGP_TRY(buf_ensure(ctx, F->inv_pre, sizeof(int32_t) * n1));
+        SGP_TRY(buf_ensure(ctx, F->pinned, sizeof(int32_t) * n1));
+        SGP_TRY(buf_ensure(ctx, F->et_tid, sizeof(int32_t) * n1));
+        SGP_TRY(buf_ensure(ctx, F->et_size, sizeof(int32_t) * (n1 + 1)));
+        const size_t m2 = 2 * (size_t)nt + 1;
+        SGP_TRY(buf_ensure(ctx, F->et_succ, sizeof(int32_t) * m2));
+        SGP_TRY(buf_ensure(ctx, F->et_dist, sizeof(int32_t) * m2));
+        SGP_TRY(buf_ensure(ctx, F->et_succ2, sizeof(int32_t) * m2));
+        SGP_TRY(buf_ensure(ctx, F->et_dist2, sizeof(int32_t) * m2));
+        SGP_TRY(buf_ensure(ctx, F->et_flag, sizeof(int32_t) * (m2 + 1)));
+        int32_t *pre = bp<int32_t>(F->pre), *tid = bp<int32_t>(F->et_tid), *tsize = bp<int32_t>(F->et_size);
+        int32_t *succ = bp<int32_t>(F->et_succ), *dist = bp<int32_t>(F->et_dist);
+        int32_t *succ2 = bp<int32_t>(F->et_succ2), *dist2 = bp<int32_t>(F->et_dist2);
+        int32_t *dflag = bp<int32_t>(F->et_flag);
+        const int32_t *comp = bp<const int32_t>(T->comp);
+        pinned = bp<int32_t>(F->pinned);
+        // trees: rank of each root among roots, sizes, exclusive size sums
+        LAUNCH(ctx, k_root_flag, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n, flag);
+        SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, n));
+        int32_t ntree = 0;
+        SGP_TRY(read_back(ctx, &ntree, tmp + n, sizeof(int32_t)));
+        SGP_CUDA(ctx, cudaMemsetAsync(tsize, 0, sizeof(int32_t) * (n1 + 1), ctx->stream));
+        LAUNCH(ctx, k_tree_index, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, (const int32_t *)tmp, n, tid, tsize);
+        int32_t *voff = bp<int32_t>(F->pos);   // scratch until the contraction starts
+        SGP_TRY(scan_exclusive_i32(ctx, tsize, voff, ntree));
+        int *perr = ctx->d_flags + 16;
+        SGP_TRY(tail_smem_optin(ctx));
+        SGP_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
+        SGP_CUDA(ctx, cudaMemsetAsync(pre, 0xff, sizeof(int32_t) * n, ctx->stream));
+        const int64_t ns = 2 * nt;
+        if (nt > 0) {
+            LAUNCH(ctx, k_et_init, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
+                   (const int32_t *)nbr, (const int32_t *)twin, comp, n, succ, dist);
+            for (int64_t span = 1; span < ns; span *= 2) {
+                LAUNCH(ctx, k_et_jump, grid_for(ns, SGP_BLOCK), SGP_BLOCK, 0, ns, (const int32_t *)succ,
+                       (const int32_t *)dist, succ2, dist2);
+                std::swap(succ, succ2);
+                std::swap(dist, dist2);
+            }
+            LAUNCH(ctx, k_et_down, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
+                   (const int32_t *)twin, (const int32_t *)dist, (const int32_t *)tid, (const int32_t *)voff,
+                   (const int32_t *)tsize, n, ns, dflag, perr);
+            SGP_TRY(scan_exclusive_i32(ctx, dflag, dflag, ns));
+        }
+        LAUNCH(ctx, k_preorder, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
+               (const int32_t *)nbr, (const int32_t *)twin, (const int32_t *)dist, (const int32_t *)tid,
+               (const int32_t *)voff, (const int32_t *)tsize, (const int32_t *)dflag, comp, n, ns, pre, perr);
+        LAUNCH(ctx, k_blocks, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
+               (const int32_t *)nbr, (const int32_t *)pre, n, shift, bp<int32_t>(F->inv_pre), pinned, perr);
+        int herr8 = 0;
+        SGP_TRY(read_back(ctx, &herr8, perr, sizeof(int)));
+        if (herr8) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: the depth-first order is not a permutation");
+        SGP_CUDA(ctx, cudaMemcpyAsync(A, F->inv_pre.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    }
+
     Sim S{adj_ptr, nbr, twin, eref, deg, lev, nrec, bp<int2>(F->rq), bp<int2>(F->re), bp<int2>(F->ren)};
     int32_t na = (int32_t)n, npos = 0, npair = 0, nrecv = 0, ncontrib = 0, level = 0;
     const int max_phases = 4 * 64 + 8 * 32;
+    bool phase1 = local;
     for (int phase = 0; na > 0; ++phase) {
         if (phase > max_phases)
             return sgp_fail(ctx, SGP_ERR_TIMEOUT, "tree_factor: contraction did not finish");
         const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
-        LAUNCH(ctx, k_select, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt);
+        LAUNCH(ctx, k_select, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt,
+               (const int32_t *)(phase1 ? pinned : nullptr));
         F->rounds++;
         int32_t ne = 0;
         SGP_TRY(compact(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, &ne));
+        if (ne == 0 && phase1) {        // local phase exhausted: the rest contracts globally
+            phase1 = false;
+            F->local_levels = level;
+            continue;
+        }
         if (ne == 0) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
         // pairs (receivers) of the eliminated vertices
         LAUNCH(ctx, k_level_nrec, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, npos, ne,
@@ -820,6 +1210,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
         na = nalive;
     }
     if (npos != n) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: %d of %lld eliminated", npos, (long long)n);
+    if (phase1) F->local_levels = level;
     F->levels = level;
     F->npairs = npair;
     // closing entries of the pointer arrays
@@ -864,10 +1255,41 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     }
     // the tail: the first level from which everything left fits in the
     // tail kernel's shared memory
-    int lt = 0;
-    while (lt < F->levels &&
-           tail_smem_bytes<double>((int32_t)(n - F->lvl_ptr[lt]), npair - F->pl_ptr[lt],
-                                   nrecv - F->rl_ptr[lt]) > (size_t)TREE_TAIL_SMEM)
+    // in-block indices and per-block ranges of the local levels
+    const int L1 = F->local_levels;
+    if (L1 > 0) {
+        const int32_t nb = F->ncomp, mask = B - 1;
+        const int32_t nr1 = F->rl_ptr[L1], nc1 = F->cl_ptr[L1], no1 = F->lvl_ptr[L1], nq1 = F->pl_ptr[L1];
+        SGP_TRY(buf_ensure(ctx, F->loc_r, sizeof(int32_t) * std::max(nr1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->loc_c, sizeof(int32_t) * std::max(nc1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->loc_o, sizeof(int32_t) * std::max(no1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->loc_q, sizeof(int32_t) * std::max(nq1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->roff, sizeof(int32_t) * (size_t)L1 * (nb + 1)));
+        SGP_TRY(buf_ensure(ctx, F->poff, sizeof(int32_t) * (size_t)L1 * (nb + 1)));
+        const int32_t *pre = bp<const int32_t>(F->pre);
+        LAUNCH(ctx, k_loc_map, grid_for(nr1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv, pre, nr1, mask,
+               bp<int32_t>(F->loc_r));
+        LAUNCH(ctx, k_loc_map, grid_for(nc1, SGP_BLOCK), SGP_BLOCK, 0, bp<const int32_t>(F->ctv), pre, nc1, mask,
+               bp<int32_t>(F->loc_c));
+        LAUNCH(ctx, k_loc_map, grid_for(no1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, pre, no1, mask,
+               bp<int32_t>(F->loc_o));
+        LAUNCH(ctx, k_loc_map, grid_for(nq1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_q, pre, nq1, mask,
+               bp<int32_t>(F->loc_q));
+        for (int l = 0; l < L1; ++l) {
+            LAUNCH(ctx, k_block_ranges, grid_for(nb + 1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv, pre,
+                   F->rl_ptr[l], F->rl_ptr[l + 1], nb, shift, bp<int32_t>(F->roff) + (size_t)l * (nb + 1));
+            LAUNCH(ctx, k_block_ranges, grid_for(nb + 1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, pre,
+                   F->lvl_ptr[l], F->lvl_ptr[l + 1], nb, shift, bp<int32_t>(F->poff) + (size_t)l * (nb + 1));
+        }
+    }
+    int lt = L1;
+    auto tail_bytes = [&](int l) {
+        const int32_t tn = (int32_t)(n - F->lvl_ptr[l]), tp = npair - F->pl_ptr[l], tr = nrecv - F->rl_ptr[l];
+        return F->precision == SGP_PREC_MIXED ? tail_smem_bytes<float>(tn, tp, tr)
+                                              : tail_smem_bytes<double>(tn, tp, tr);
+    };
+    while (lt < F->levels && (tail_bytes(lt) > (size_t)TREE_TAIL_SMEM ||
+                              (ctx->tail_cap >= 0 && n - F->lvl_ptr[lt] > ctx->tail_cap)))
         ++lt;
     F->tail_level = lt;
     if (lt < F->levels) {
@@ -937,7 +1359,9 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->eref, &F->deg, &F->lev, &F->nrec, &F->rq, &F->re, &F->ren, &F->pos,
                     &F->flag, &F->alive_a, &F->alive_b, &F->acc, &F->fill, &F->sbuf, &F->tmp,
                     &F->rflag, &F->cnt, &F->ctv, &F->Lf, &F->Lf32, &F->tail_idx, &F->tail_q,
-                    &F->tail_c, &F->tail_b};
+                    &F->tail_c, &F->tail_b, &F->pre, &F->inv_pre, &F->loc_r, &F->loc_c, &F->loc_o,
+                    &F->loc_q, &F->roff, &F->poff, &F->et_succ, &F->et_dist, &F->et_succ2,
+                    &F->et_dist2, &F->et_tid, &F->et_size, &F->et_flag, &F->pinned};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete F;

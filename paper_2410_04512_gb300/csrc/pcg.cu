@@ -573,7 +573,8 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
                             M->gen, Fac ? Fac->gen : 0ull, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)r,
                             (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q, (uint64_t)(uintptr_t)w,
                             (uint64_t)(uintptr_t)partials, (uint64_t)(uintptr_t)sc,
-                            (uint64_t)(uintptr_t)jac, (uint64_t)ctx->timing, (uint64_t)chunk};
+                            (uint64_t)(uintptr_t)jac, (uint64_t)ctx->timing, (uint64_t)chunk,
+                            (uint64_t)ctx->spmv_lpr};
     GraphEntry *ge = nullptr;
     SGP_TRY(graph_lookup(ctx, key, sizeof(key) / sizeof(key[0]), &ge));
     if (!ge->exec) SGP_TRY(graph_capture(ctx, ge, [&]() { return iterate(chunk); }));

@@ -61,6 +61,10 @@ struct sgp_ctx {
     size_t d_scan_bytes = 0;
     // tuning knobs (0 = built-in default)
     int spmv_lpr = 0;
+    int tail_cap = 1024;    // largest tail of the tree solve in vertices (-1: what fits)
+    int comp_size = 0;      // block of the local phase of the tree factor (0: none)
+    int use_pdl = 1;        // programmatic dependent launch of the level kernels
+    int batch_chunk = 0;    // rows per work item of the batched solver
     int num_sms = 0;
     std::vector<std::pair<const void *, int>> occupancy;  // kernel -> resident blocks/SM
     // CUDA graphs of solver chunks (captured on a private stream)
@@ -219,6 +223,15 @@ struct sgp_factor {
     DBuf tail_idx;  // level positions and receiver offsets of the tail levels
     DBuf tail_q, tail_c, tail_b;  // local indices (position - tail_P0)
     DBuf work;      // n x 3 float64 apply workspace
+    // local phase: the forest is cut into blocks of comp_size consecutive
+    // vertices of a depth-first preorder; levels < local_levels eliminate
+    // only vertices whose tree neighbours are all in their own block, and the
+    // solve runs those levels block by block in shared memory
+    int32_t local_levels = 0, comp_size = 0, ncomp = 0;
+    DBuf pre, inv_pre;          // n int32: preorder number of each vertex and its inverse
+    DBuf loc_r, loc_c, loc_o, loc_q;  // local (in-block) index of rv, ctv, ord, pr_q entries
+    DBuf roff, poff;            // local_levels x (ncomp + 1) receiver / position ranges per block
+    DBuf et_succ, et_dist, et_succ2, et_dist2, et_tid, et_size, et_flag, pinned;  // Euler tour scratch
     // structure-simulation scratch
     DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,
         acc, fill, sbuf, tmp, rflag, cnt;
@@ -246,7 +259,7 @@ static inline sgp_status sgp_launch_pdl(sgp_ctx *ctx, const char *name, void (*k
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = ctx->use_pdl;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);

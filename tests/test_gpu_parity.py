@@ -136,14 +136,14 @@ def test_spanning_forest_with_all_weights_tied(ctx):
 EPS = np.finfo(np.float64).eps
 
 
-def _tree_check(ctx, c, seed=0):
+def _tree_check(ctx, c, seed=0, precision=sgp.PREC_F64):
     """Forward error of the GPU tree solve against the oracle's, and the
     tolerance the arithmetic allows: both are backward stable solves of
     P x = b in different elimination orders, so they may differ by about
     eps * kappa(P); kappa(P) <= (gamma0 + 2 max_i sum_j |Upsilon_ij|) / gamma0
     (Gershgorin; lambda_min(P) >= gamma0 by Lemma 2.4).  The backward error
     |P x - b| / (|P| |x|) must be at rounding level regardless of kappa."""
-    s = GpuSystem(ctx, c)
+    s = GpuSystem(ctx, c, precision=precision)
     o = oracle_system(c)
     f = oracle.prim_msf(c.n, o.ij, o.w)
     fac = oracle.tree_ldlt(f, o.blocks, c.gamma0)
@@ -169,6 +169,34 @@ def test_tree_solve_matches_oracle(ctx, k):
     assert err <= tol, (err, tol)
     rounds, levels = s.Fac.info()
     assert rounds <= 4 * np.log2(s.n) + 8
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_tree_solve_fp64_apply_of_mixed_factor(ctx, k):
+    """A MIXED factor sizes its shared-memory tail for FP32 vectors; an FP64
+    apply of it (the public call) must still be the FP64 solve."""
+    err, tol, _ = _tree_check(ctx, cases()[k], k, precision=sgp.PREC_MIXED)
+    assert err <= tol, (err, tol)
+
+
+def test_tree_solve_mid_size_ball(ctx):
+    """60,000 cells: many level kernels before the tail, in both precisions."""
+    c = workloads.ball(n=60000, seed=2001, gamma0=1e-3)
+    for prec in (sgp.PREC_F64, sgp.PREC_MIXED):
+        s = GpuSystem(ctx, c, precision=prec)
+        b = np.random.default_rng(3).standard_normal((c.n, 3))
+        x = ctx.tree_apply(s.Fac, dev_tensor(b)).cpu().numpy()
+        te = s.T.edge_ids().cpu().numpy()
+        ij = s.ij.cpu().numpy()[te]
+        blocks = s.M.edge_blocks()[0].cpu().numpy()[te]
+        Px = oracle.matvec(c.n, ij, blocks, c.gamma0, x)
+        norms = np.abs(blocks).sum(axis=2).max(axis=1)
+        rowsum = np.zeros(c.n)
+        np.add.at(rowsum, ij[:, 0], norms)
+        np.add.at(rowsum, ij[:, 1], norms)
+        pnorm = c.gamma0 + 2 * rowsum.max()
+        back = np.linalg.norm(Px - b) / (pnorm * np.linalg.norm(x))
+        assert back <= 1e-14, (prec, back)
 
 
 def test_tree_solve_long_chain(ctx):

@@ -1,0 +1,91 @@
+"""The autotuner and the tuning knobs: every candidate is a valid launch
+shape, so the solution must not depend on the choice (beyond rounding), and
+the chosen values come from the documented candidate sets."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2410_04512_gb300 as sgp
+import workloads
+from gpu_common import GpuSystem, dev_tensor, oracle_system, rel_err, small_cube
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def ctx(cuda_device):
+    return sgp.Context(0)
+
+
+def test_set_tuning_validates(ctx):
+    for bad in (dict(spmv_lpr=3), dict(tail_cap=-2), dict(batch_chunk=100), dict(batch_chunk=70000),
+                dict(comp_size=1000), dict(comp_size=32), dict(comp_size=16384)):
+        with pytest.raises(sgp.SgpError):
+            ctx.set_tuning(**bad)
+    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256)
+    assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "comp_size": 256,
+                                "ms_per_iteration": 0.0}
+
+
+@pytest.mark.parametrize("cap,cs", [(0, 0), (64, 1024), (256, 64), (-1, 256), (1024, 8192), (0, 4096)])
+@pytest.mark.parametrize("prec", [sgp.PREC_F64, sgp.PREC_MIXED])
+def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, prec):
+    c = workloads.ball(n=20000, seed=2002, gamma0=1e-3)
+    ctx.set_tuning(tail_cap=cap, comp_size=cs)
+    s = GpuSystem(ctx, c, precision=prec)
+    F = c.forces()
+    v, info = ctx.pcg_solve(s.M, s.Fac, dev_tensor(F), tol=1e-10, precision=prec)
+    assert info.status == 0 and info.true_rel_residual <= 1e-10
+    ctx.set_tuning(tail_cap=-1)
+    ref = GpuSystem(ctx, c, precision=sgp.PREC_F64)
+    vr, _ = ctx.pcg_solve(ref.M, ref.Fac, dev_tensor(F), tol=1e-12)
+    assert rel_err(v.cpu().numpy(), vr.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("lpr", [1, 2, 4, 8])
+def test_lanes_per_row_do_not_change_the_solution(ctx, lpr):
+    c = small_cube(3000, seed=1003)
+    s = GpuSystem(ctx, c)
+    o = oracle_system(c)
+    F = c.forces()
+    ctx.set_tuning(spmv_lpr=lpr)
+    v, info = ctx.pcg_solve(s.M, s.Fac, dev_tensor(F), tol=1e-12)
+    ref, _ = oracle.solve_system(o, F, tol=1e-13)
+    assert rel_err(v.cpu().numpy(), ref.x) <= 1e-9
+
+
+def test_autotune_single_system(ctx):
+    c = workloads.ball(n=30000, seed=2003, gamma0=1e-3)
+    s = GpuSystem(ctx, c, precision=sgp.PREC_MIXED)
+    F = dev_tensor(c.forces())
+    t = ctx.autotune(s.M, s.T, s.Fac, F, precision=sgp.PREC_MIXED, iterations=20)
+    assert t["tail_cap"] in (0, 256, 512, 1024, 2048, 4096, -1)
+    assert t["comp_size"] in (0, 256, 512, 1024, 2048, 4096)
+    assert t["spmv_lpr"] in (1, 2, 4, 8)
+    assert t["ms_per_iteration"] > 0
+    assert ctx.get_tuning()["tail_cap"] == t["tail_cap"]
+    # the factor handle was left built with the chosen tail and still solves
+    v, info = ctx.pcg_solve(s.M, s.Fac, F, tol=1e-8, precision=sgp.PREC_MIXED)
+    assert info.status == 0 and info.true_rel_residual <= 1e-8
+
+
+def test_autotune_batch(ctx):
+    sizes = np.array([1500, 800, 3000, 200, 2500, 1200])
+    off = workloads.sphere_offsets(sizes)
+    cells = [workloads.batch_instance(int(n), s) for s, n in enumerate(sizes)]
+    pos = dev_tensor(np.concatenate([c.pos for c in cells]))
+    radii = dev_tensor(np.concatenate([c.radii for c in cells]))
+    g = ctx.collision_graph_batched(off, pos, radii)
+    tab = dev_tensor(workloads.gamma_table(0.1, 10.0))
+    gp, gq = workloads.pair_gamma_torch(4000, g.edges(), tab, tab)
+    M = ctx.friction_assemble(g, pos, gp.contiguous(), gq.contiguous(), 1e-2, sgp.PREC_F64)
+    T = ctx.max_spanning_tree(M)
+    Fh = ctx.tree_factor(M, T)
+    F = dev_tensor(np.random.default_rng(0).standard_normal((int(off[-1]), 3)))
+    v0, _ = ctx.pcg_solve_batched(M, Fh, off, F, tol=1e-10)
+    t = ctx.autotune(M, T, Fh, F, offsets=off, iterations=10)
+    assert t["batch_chunk"] in (512, 1024, 2048, 4096, 8192)
+    assert t["spmv_lpr"] in (1, 2, 4)
+    v1, infos = ctx.pcg_solve_batched(M, Fh, off, F, tol=1e-10)
+    assert all(i.status == 0 for i in infos)
+    assert rel_err(v1.cpu().numpy(), v0.cpu().numpy()) <= 1e-8
