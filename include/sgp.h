@@ -304,6 +304,12 @@ typedef struct {
                             stay inside blocks run block by block in shared
                             memory; 0 (none) or a power of two in 64..8192
                             (default 0); read when a factor is built */
+    int32_t coop_cap;    /* the middle contraction levels, from the first one with
+                            at most coop_cap vertices left down to the tail, run in
+                            one cooperative kernel per direction with grid-wide
+                            barriers instead of one launch per level; 0 (none,
+                            default) or 256..16777216; read when a factor is built */
+    int32_t reserved;
     double ms_per_iteration; /* sgp_autotune: time of one PCG iteration with the
                                 chosen values; 0 from sgp_get_tuning */
 } sgp_tuning;
@@ -313,7 +319,8 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *tuning);
 /* Time `iterations` PCG iterations (opts' precision and preconditioner, the
  * tolerance ignored) of the caller's system for each candidate and keep the
  * fastest, one knob after the other: comp_size in {0, 256, 512, 1024, 2048,
- * 4096} and tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} (tree
+ * 4096}, tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} and coop_cap in
+ * {0, 8192, 32768, 131072} (tree
  * preconditioner only; *factor is rebuilt from `tree` for each candidate
  * and left built with the chosen values), then spmv_lpr in
  * {1, 2, 4, 8}, then, when n_instances > 0 (a batch with host `offsets`, as

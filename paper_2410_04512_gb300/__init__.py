@@ -45,10 +45,11 @@ class SolveOpts(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("spmv_lpr", ctypes.c_int32), ("tail_cap", ctypes.c_int32), ("batch_chunk", ctypes.c_int32),
-                ("comp_size", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
+                ("comp_size", ctypes.c_int32), ("coop_cap", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_per_iteration", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class SolveInfo(ctypes.Structure):
@@ -414,9 +415,10 @@ class Context:
         self._ok(_lib.sgp_get_tuning(self.ptr, ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, comp_size: int = 0):
+    def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, comp_size: int = 0,
+                   coop_cap: int = 0):
         """Set the launch-shape knobs (the defaults are the library's)."""
-        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, 0.0)
+        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, coop_cap, 0, 0.0)
         self._ok(_lib.sgp_set_tuning(self.ptr, ctypes.byref(t)))
 
     def autotune(self, M: Matrix, T: Tree | None, Fh: Factor | None, F: torch.Tensor, offsets=None,

@@ -25,6 +25,8 @@
 // replays them forward (receivers gather L_qc z_c) and backward (each
 // eliminated vertex gathers from its receivers).  All sums run in a fixed
 // order, so results are bitwise reproducible.
+#include <cooperative_groups.h>
+
 #include "sgp_internal.cuh"
 
 namespace {
@@ -242,7 +244,7 @@ __global__ void k_blocks(const int32_t *__restrict__ adj_ptr, const int32_t *__r
 }
 
 // in-block index of each listed vertex
-__global__ void k_loc_map(const int32_t *__restrict__ src, const int32_t *__restrict__ pre, int32_t count,
+__global__ void k_loc_map(const int32_t *src, const int32_t *__restrict__ pre, int32_t count,
                           int32_t mask, int32_t *dst)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,6 +265,124 @@ __global__ void k_block_ranges(const int32_t *__restrict__ list, const int32_t *
         else b = m;
     }
     out[c] = a;
+}
+
+// ------------------------------------------- block-major layout of local levels
+// Per block c, for kind k (0 forward entries, 1 contributors, 2 positions,
+// 3 pairs): prefix counts over the local levels (nlev + 1 values) and totals.
+__global__ void k_bm_tables(int32_t nlev, int32_t nb, const int32_t *__restrict__ roff,
+                            const int32_t *__restrict__ poff, const int32_t *__restrict__ rc_ptr,
+                            const int32_t *__restrict__ pr_ptr, int32_t *tab, int32_t *tot, int32_t *mx)
+{
+    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    int32_t *t = tab + (size_t)c * 4 * (nlev + 1);
+    int32_t acc[4] = {0, 0, 0, 0};
+    for (int32_t l = 0; l < nlev; ++l) {
+        const int32_t *ro = roff + (size_t)l * (nb + 1), *po = poff + (size_t)l * (nb + 1);
+        const int32_t r0 = ro[c], r1 = ro[c + 1], p0 = po[c], p1 = po[c + 1];
+        const int32_t d[4] = {r1 - r0, rc_ptr[r1] - rc_ptr[r0], p1 - p0, pr_ptr[p1] - pr_ptr[p0]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            t[k * (nlev + 1) + l] = acc[k];
+            acc[k] += d[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        t[k * (nlev + 1) + nlev] = acc[k];
+        tot[(size_t)k * nb + c] = acc[k];
+        atomicMax(mx + k, acc[k]);
+    }
+}
+
+// position in the block-major array of kind k of an entry at offset `off`
+// within block c's segment of level l
+__device__ __forceinline__ int32_t bm_at(const int32_t *tab, const int32_t *base, int32_t nlev, int32_t nb,
+                                         int32_t c, int32_t l, int k, int32_t off)
+{
+    return base[(size_t)k * (nb + 1) + c] + tab[((size_t)c * 4 + k) * (nlev + 1) + l] + off;
+}
+
+__global__ void k_bm_recv(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t k0, int32_t cnt,
+                          const int32_t *__restrict__ rv, const int32_t *__restrict__ pre,
+                          const int32_t *__restrict__ roff, const int32_t *__restrict__ rc_ptr,
+                          const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
+                          const int32_t *__restrict__ loc_r, int32_t *bm_q, int32_t *bm_beg)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int32_t k = k0 + i;
+    const int32_t c = pre[rv[k]] >> shift;
+    const int32_t seg = roff[(size_t)l * (nb + 1) + c];
+    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 0, k - seg);
+    bm_q[e] = loc_r[k];
+    bm_beg[e] = tab[((size_t)c * 4 + 1) * (nlev + 1) + l] + (rc_ptr[k] - rc_ptr[seg]);
+}
+
+__global__ void k_bm_contrib(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t j0, int32_t cnt,
+                             const int32_t *__restrict__ ctv, const int32_t *__restrict__ pre,
+                             const int32_t *__restrict__ roff, const int32_t *__restrict__ rc_ptr,
+                             const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
+                             const int32_t *__restrict__ loc_c, const double *__restrict__ Lf,
+                             const float *__restrict__ Lf32, int32_t *bm_cloc, double *bm_Lf, float *bm_Lf32)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int32_t j = j0 + i;
+    const int32_t c = pre[ctv[j]] >> shift;
+    const int32_t seg = rc_ptr[roff[(size_t)l * (nb + 1) + c]];
+    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 1, j - seg);
+    bm_cloc[e] = loc_c[j];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) bm_Lf[9 * (int64_t)e + a] = Lf[9 * (int64_t)j + a];
+    if (Lf32)
+#pragma unroll
+        for (int a = 0; a < 9; ++a) bm_Lf32[9 * (int64_t)e + a] = Lf32[9 * (int64_t)j + a];
+}
+
+__global__ void k_bm_pos(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t t0, int32_t cnt,
+                         const int32_t *__restrict__ ord, const int32_t *__restrict__ pre,
+                         const int32_t *__restrict__ poff, const int32_t *__restrict__ pr_ptr,
+                         const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
+                         const int32_t *__restrict__ loc_o, const double *__restrict__ Dinv,
+                         const float *__restrict__ Dinv32, int32_t *bm_oloc, int32_t *bm_pbeg, double *bm_D,
+                         float *bm_D32)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int32_t t = t0 + i;
+    const int32_t c = pre[ord[t]] >> shift;
+    const int32_t seg = poff[(size_t)l * (nb + 1) + c];
+    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 2, t - seg);
+    bm_oloc[e] = loc_o[t];
+    bm_pbeg[e] = tab[((size_t)c * 4 + 3) * (nlev + 1) + l] + (pr_ptr[t] - pr_ptr[seg]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) bm_D[6 * (int64_t)e + a] = Dinv[6 * (int64_t)t + a];
+    if (Dinv32)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) bm_D32[6 * (int64_t)e + a] = Dinv32[6 * (int64_t)t + a];
+}
+
+__global__ void k_bm_pair(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t q0, int32_t cnt,
+                          const int32_t *__restrict__ pr_c, const int32_t *__restrict__ pre,
+                          const int32_t *__restrict__ poff, const int32_t *__restrict__ pr_ptr,
+                          const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
+                          const int32_t *__restrict__ loc_q, const double *__restrict__ L,
+                          const float *__restrict__ L32, int32_t *bm_qloc, double *bm_Lb, float *bm_Lb32)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int32_t p = q0 + i;
+    const int32_t c = pre[pr_c[p]] >> shift;
+    const int32_t seg = pr_ptr[poff[(size_t)l * (nb + 1) + c]];
+    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 3, p - seg);
+    bm_qloc[e] = loc_q[p];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) bm_Lb[9 * (int64_t)e + a] = L[9 * (int64_t)p + a];
+    if (L32)
+#pragma unroll
+        for (int a = 0; a < 9; ++a) bm_Lb32[9 * (int64_t)e + a] = L32[9 * (int64_t)p + a];
 }
 
 // -------------------------------------------------------- structure: select
@@ -766,6 +886,248 @@ __global__ void __launch_bounds__(256) k_local_bwd(Local a, const T *__restrict_
     }
 }
 
+// Middle levels in one cooperative kernel per direction: the grid walks the
+// levels [coop_level, tail_level) with a grid-wide barrier between levels
+// instead of one launch per level (same per-entry arithmetic and order as
+// k_tree_fwd / k_tree_bwd).  Launched cooperatively, so every block is
+// resident and the barrier is CUDA's own.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(256) k_tree_coop(int32_t nlev, const int32_t *__restrict__ lidx,
+                                                   const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
+                                                   const int32_t *__restrict__ ctv, const T *__restrict__ Lf,
+                                                   const int32_t *__restrict__ ord, const int32_t *__restrict__ pr_ptr,
+                                                   const int32_t *__restrict__ pr_q, const T *__restrict__ L,
+                                                   const T *__restrict__ Dinv, T *w, const int *done)
+{
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    if (done && *done) return;   // the same value in every block: no block reaches a barrier
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    if (FWD) {
+        for (int32_t l = 0; l < nlev; ++l) {
+            const int32_t r0 = lidx[nlev + 1 + l], r1 = lidx[nlev + 2 + l];
+            for (int64_t k = r0 + tid; k < r1; k += nth) {
+                const int32_t q = rv[k];
+                T s[3] = {0, 0, 0};
+                for (int32_t j = rc_ptr[k]; j < rc_ptr[k + 1]; ++j) {
+                    const int64_t c = ctv[j];
+                    T x[3] = {w[3 * c], w[3 * c + 1], w[3 * c + 2]};
+                    T y[3];
+                    full_mv(Lf + 9 * (int64_t)j, x, y);
+                    s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+                }
+                w[3 * (int64_t)q] -= s[0];
+                w[3 * (int64_t)q + 1] -= s[1];
+                w[3 * (int64_t)q + 2] -= s[2];
+            }
+            if (l + 1 < nlev) grid.sync();
+        }
+    } else {
+        for (int32_t l = nlev - 1; l >= 0; --l) {
+            const int32_t p0 = lidx[l], p1 = lidx[l + 1];
+            for (int64_t t = p0 + tid; t < p1; t += nth) {
+                const int64_t c = ord[t];
+                T x[3] = {w[3 * c], w[3 * c + 1], w[3 * c + 2]};
+                T z[3];
+                sym_mv(Dinv + 6 * t, x, z);
+                for (int32_t p = pr_ptr[t]; p < pr_ptr[t + 1]; ++p) {
+                    const int64_t q = pr_q[p];
+                    T y[3] = {w[3 * q], w[3 * q + 1], w[3 * q + 2]};
+                    T u[3];
+                    full_mtv(L + 9 * (int64_t)p, y, u);
+                    z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+                }
+                w[3 * c] = z[0];
+                w[3 * c + 1] = z[1];
+                w[3 * c + 2] = z[2];
+            }
+            if (l > 0) grid.sync();
+        }
+    }
+}
+
+template <typename T, bool FWD>
+static sgp_status launch_coop(sgp_ctx *ctx, const sgp_factor *F, int32_t nlev, const int32_t *lidx,
+                              const int32_t *rv, const int32_t *rc, const int32_t *ctv, const T *Lf,
+                              const int32_t *ord, const int32_t *prp, const int32_t *prq, const T *L,
+                              const T *Dinv, T *w, const int *done)
+{
+    auto kern = k_tree_coop<T, FWD>;
+    int per_sm = 0;
+    SGP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+    if (ctx->num_sms <= 0) SGP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int grid = std::max(1, std::min(per_sm, 2) * ctx->num_sms);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, nlev, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done);
+    ctx->launches++;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return sgp_fail(ctx, SGP_ERR_CUDA, "launch of k_tree_coop failed: %s", cudaGetErrorString(e));
+    (void)F;
+    return SGP_OK;
+}
+
+// shared-memory carving: every piece starts on a 16-byte boundary
+__host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Staged local levels: the block's share of the block-major arrays (its
+// forward entries and contributors, or its positions and pairs, level after
+// level) is copied into shared memory with contiguous loads before the wait
+// on the previous kernel; the levels then run from shared memory.
+struct LocalS {
+    int32_t nlev, nb, shift, n;
+    const int32_t *inv_pre, *tab, *base;
+    const int32_t *q, *beg, *cloc, *oloc, *pbeg, *qloc;
+};
+
+template <typename T>
+__host__ __device__ inline size_t local_fwd_smem(int32_t B, int32_t nlev, int32_t me, int32_t mc)
+{
+    return tail_align(sizeof(T) * 3 * (size_t)B) + tail_align(sizeof(T) * 9 * (size_t)mc) +
+           tail_align(4 * (size_t)mc) + tail_align(4 * (size_t)me) + tail_align(4 * ((size_t)me + 1)) +
+           tail_align(4 * ((size_t)nlev + 1));
+}
+
+template <typename T>
+__host__ __device__ inline size_t local_bwd_smem(int32_t B, int32_t nlev, int32_t mp, int32_t mq)
+{
+    return tail_align(sizeof(T) * 3 * (size_t)B) + tail_align(sizeof(T) * 6 * (size_t)mp) +
+           tail_align(sizeof(T) * 9 * (size_t)mq) + tail_align(4 * (size_t)mp) + tail_align(4 * ((size_t)mp + 1)) +
+           tail_align(4 * (size_t)mq) + tail_align(4 * ((size_t)nlev + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_local_fwd_s(LocalS a, const T *__restrict__ Lb, T *w, const int *done,
+                                                     int32_t me, int32_t mc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    if (done && *done) return;
+    const int32_t B = 1 << a.shift, c = blockIdx.x, base = c << a.shift;
+    const int32_t cnt = min(B, a.n - base);
+    unsigned char *cur = smem_raw;
+    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
+    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * B));
+    T *sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * mc));
+    int32_t *sc = reinterpret_cast<int32_t *>(take(4 * mc));
+    int32_t *sq = reinterpret_cast<int32_t *>(take(4 * me));
+    int32_t *sb = reinterpret_cast<int32_t *>(take(4 * (me + 1)));
+    int32_t *st = reinterpret_cast<int32_t *>(take(4 * (a.nlev + 1)));
+    const int32_t *tab = a.tab + (size_t)c * 4 * (a.nlev + 1);
+    const int32_t ne = tab[a.nlev], nc = tab[(a.nlev + 1) + a.nlev];
+    const int32_t e0 = a.base[c], c0 = a.base[(a.nb + 1) + c];
+    for (int32_t i = threadIdx.x; i <= a.nlev; i += blockDim.x) st[i] = tab[i];
+    for (int32_t i = threadIdx.x; i < 9 * nc; i += blockDim.x) sL[i] = Lb[9 * (int64_t)c0 + i];
+    for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) sc[i] = a.cloc[c0 + i];
+    for (int32_t i = threadIdx.x; i < ne; i += blockDim.x) {
+        sq[i] = a.q[e0 + i];
+        sb[i] = a.beg[e0 + i];
+    }
+    if (threadIdx.x == 0) sb[ne] = nc;
+    pdl_wait();
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        sw[3 * i] = w[3 * v];
+        sw[3 * i + 1] = w[3 * v + 1];
+        sw[3 * i + 2] = w[3 * v + 2];
+    }
+    __syncthreads();
+    for (int l = 0; l < a.nlev; ++l) {
+        const int32_t k1 = st[l + 1];
+        for (int32_t k = st[l] + threadIdx.x; k < k1; k += blockDim.x) {
+            T s[3] = {0, 0, 0};
+            for (int32_t j = sb[k]; j < sb[k + 1]; ++j) {
+                T y[3];
+                full_mv(sL + 9 * j, sw + 3 * sc[j], y);
+                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+            }
+            const int32_t q = sq[k];
+            sw[3 * q] -= s[0];
+            sw[3 * q + 1] -= s[1];
+            sw[3 * q + 2] -= s[2];
+        }
+        __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        w[3 * v] = sw[3 * i];
+        w[3 * v + 1] = sw[3 * i + 1];
+        w[3 * v + 2] = sw[3 * i + 2];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_local_bwd_s(LocalS a, const T *__restrict__ Lb, const T *__restrict__ Db,
+                                                     T *w, const int *done, int32_t mp, int32_t mq)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    if (done && *done) return;
+    const int32_t B = 1 << a.shift, c = blockIdx.x, base = c << a.shift;
+    const int32_t cnt = min(B, a.n - base);
+    unsigned char *cur = smem_raw;
+    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
+    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * B));
+    T *sD = reinterpret_cast<T *>(take(sizeof(T) * 6 * mp));
+    T *sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * mq));
+    int32_t *so = reinterpret_cast<int32_t *>(take(4 * mp));
+    int32_t *sp = reinterpret_cast<int32_t *>(take(4 * (mp + 1)));
+    int32_t *sq = reinterpret_cast<int32_t *>(take(4 * mq));
+    int32_t *st = reinterpret_cast<int32_t *>(take(4 * (a.nlev + 1)));
+    const int32_t *tab = a.tab + (size_t)c * 4 * (a.nlev + 1);
+    const int32_t np = tab[3 * (a.nlev + 1) - 1], nq = tab[4 * (a.nlev + 1) - 1];
+    const int32_t t0 = a.base[2 * (a.nb + 1) + c], q0 = a.base[3 * (a.nb + 1) + c];
+    for (int32_t i = threadIdx.x; i <= a.nlev; i += blockDim.x) st[i] = tab[2 * (a.nlev + 1) + i];
+    for (int32_t i = threadIdx.x; i < 6 * np; i += blockDim.x) sD[i] = Db[6 * (int64_t)t0 + i];
+    for (int32_t i = threadIdx.x; i < 9 * nq; i += blockDim.x) sL[i] = Lb[9 * (int64_t)q0 + i];
+    for (int32_t i = threadIdx.x; i < np; i += blockDim.x) {
+        so[i] = a.oloc[t0 + i];
+        sp[i] = a.pbeg[t0 + i];
+    }
+    if (threadIdx.x == 0) sp[np] = nq;
+    for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) sq[i] = a.qloc[q0 + i];
+    pdl_wait();
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        sw[3 * i] = w[3 * v];
+        sw[3 * i + 1] = w[3 * v + 1];
+        sw[3 * i + 2] = w[3 * v + 2];
+    }
+    __syncthreads();
+    for (int l = a.nlev - 1; l >= 0; --l) {
+        const int32_t i1 = st[l + 1];
+        for (int32_t i = st[l] + threadIdx.x; i < i1; i += blockDim.x) {
+            const int32_t o = so[i];
+            T z[3];
+            sym_mv(sD + 6 * i, sw + 3 * o, z);
+            for (int32_t p = sp[i]; p < sp[i + 1]; ++p) {
+                T u[3];
+                full_mtv(sL + 9 * p, sw + 3 * sq[p], u);
+                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+            }
+            sw[3 * o] = z[0];
+            sw[3 * o + 1] = z[1];
+            sw[3 * o + 2] = z[2];
+        }
+        __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t v = a.inv_pre[base + i];
+        w[3 * v] = sw[3 * i];
+        w[3 * v + 1] = sw[3 * i + 1];
+        w[3 * v + 2] = sw[3 * i + 2];
+    }
+}
+
 // The last levels (the vertices at elimination positions >= P0) in one
 // thread block with every array they use staged in shared memory: vectors,
 // D^-1 and L blocks by local index (position - P0, pair - Q0), and the local
@@ -781,7 +1143,6 @@ struct Tail {
     const int32_t *tct;       // np: local pair of each contributor entry
 };
 
-__host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
 
 template <typename T>
 __host__ __device__ inline size_t tail_smem_bytes(int32_t n, int32_t np, int32_t nr)
@@ -790,10 +1151,17 @@ __host__ __device__ inline size_t tail_smem_bytes(int32_t n, int32_t np, int32_t
            tail_align(4 * (size_t)(nr + 1)) + tail_align(4 * (size_t)nr);
 }
 
-// Only the vectors and the local index lists live in shared memory; L and
-// D^-1 (each read once per direction) stream from global memory in level
-// order, so the tail holds several thousand vertices.
+// The vectors and the local index lists live in shared memory; when they fit
+// (STAGE), D^-1 and the L blocks are staged there as well before the wait on
+// the previous kernel, otherwise they stream from global memory in level
+// order (each is read once per direction).
 template <typename T>
+__host__ __device__ inline size_t tail_smem_staged(int32_t n, int32_t np, int32_t nr)
+{
+    return tail_smem_bytes<T>(n, np, nr) + tail_align(sizeof(T) * 6 * (size_t)n) + tail_align(sizeof(T) * 9 * (size_t)np);
+}
+
+template <typename T, bool STAGE>
 __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__restrict__ ord,
                                                     const int32_t *__restrict__ rc_ptr,
                                                     const int32_t *__restrict__ pr_ptr,
@@ -812,8 +1180,14 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
     int32_t *sct = reinterpret_cast<int32_t *>(take(4 * tl.np));
     int32_t *src = reinterpret_cast<int32_t *>(take(4 * (tl.nr + 1)));
     int32_t *stq = reinterpret_cast<int32_t *>(take(4 * tl.nr));
-    (void)take(0);
     const T *Lt = L + 9 * (int64_t)tl.Q0, *Lft = Lf + 9 * (int64_t)tl.C0, *Dt = Dinv + 6 * (int64_t)tl.P0;
+    T *sD = nullptr, *sL = nullptr;
+    if (STAGE) {
+        sD = reinterpret_cast<T *>(take(sizeof(T) * 6 * tl.n));
+        sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * tl.np));
+        for (int32_t i = threadIdx.x; i < 6 * tl.n; i += blockDim.x) sD[i] = Dt[i];
+        for (int32_t i = threadIdx.x; i < 9 * tl.np; i += blockDim.x) sL[i] = Lt[i];
+    }
     // stage the index lists (independent of the previous kernel)
     for (int32_t i = threadIdx.x; i <= tl.n; i += blockDim.x) spr[i] = pr_ptr[tl.P0 + i] - tl.Q0;
     for (int32_t i = threadIdx.x; i < tl.np; i += blockDim.x) {
@@ -836,8 +1210,9 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
         for (int32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             T s[3] = {0, 0, 0};
             for (int32_t j = src[k]; j < src[k + 1]; ++j) {
+                const int32_t p = sct[j];
                 T y[3];
-                full_mv(Lft + 9 * (int64_t)j, sw + 3 * spc[sct[j]], y);
+                full_mv(STAGE ? sL + 9 * p : Lft + 9 * (int64_t)j, sw + 3 * spc[p], y);
                 s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
             }
             const int32_t q = stq[k];
@@ -851,10 +1226,10 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
         const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
         for (int32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             T z[3];
-            sym_mv(Dt + 6 * (int64_t)i, sw + 3 * i, z);
+            sym_mv(STAGE ? sD + 6 * i : Dt + 6 * (int64_t)i, sw + 3 * i, z);
             for (int32_t p = spr[i]; p < spr[i + 1]; ++p) {
                 T u[3];
-                full_mtv(Lt + 9 * (int64_t)p, sw + 3 * stb[p], u);
+                full_mtv(STAGE ? sL + 9 * p : Lt + 9 * (int64_t)p, sw + 3 * stb[p], u);
                 z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
             }
             sw[3 * i] = z[0];
@@ -917,21 +1292,50 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
              bp<const int32_t>(F->loc_o), bp<const int32_t>(F->loc_q)};
     while ((1 << la.shift) < F->comp_size) ++la.shift;
     const size_t lsm = sizeof(T) * 3 * (size_t)F->comp_size;
-    if (L1 > 0) LAUNCH_PDL(ctx, k_local_fwd<T>, F->ncomp, 256, lsm, la, Lf, w, done);
-    for (int l = L1; l < lt; ++l) {
+    LocalS ls{L1, F->ncomp, la.shift, (int32_t)F->n, bp<const int32_t>(F->inv_pre), bp<const int32_t>(F->bm_tab),
+              bp<const int32_t>(F->bm_base), bp<const int32_t>(F->bm_q), bp<const int32_t>(F->bm_beg),
+              bp<const int32_t>(F->bm_cloc), bp<const int32_t>(F->bm_oloc), bp<const int32_t>(F->bm_pbeg),
+              bp<const int32_t>(F->bm_qloc)};
+    const int32_t *mv = F->bm_maxv;
+    const size_t fsm = local_fwd_smem<T>(F->comp_size, L1, mv[0], mv[1]);
+    const size_t bsm = local_bwd_smem<T>(F->comp_size, L1, mv[2], mv[3]);
+    const bool staged = L1 > 0 && fsm <= (size_t)TREE_TAIL_SMEM && bsm <= (size_t)TREE_TAIL_SMEM;
+    const T *bLf = reinterpret_cast<const T *>(f64 ? F->bm_Lf.p : F->bm_Lf32.p);
+    const T *bLb = reinterpret_cast<const T *>(f64 ? F->bm_Lb.p : F->bm_Lb32.p);
+    const T *bD = reinterpret_cast<const T *>(f64 ? F->bm_D.p : F->bm_D32.p);
+    if (L1 > 0) {
+        if (staged) LAUNCH_PDL(ctx, k_local_fwd_s<T>, F->ncomp, 512, fsm, ls, bLf, w, done, mv[0], mv[1]);
+        else LAUNCH_PDL(ctx, k_local_fwd<T>, F->ncomp, 256, lsm, la, Lf, w, done);
+    }
+    // the cooperative kernel covers [lc, lt) when the factor has one and the
+    // tail is in use (an FP64 apply whose tail does not fit runs plain levels)
+    const int lc = (F->coop_level < F->tail_level && lt == F->tail_level) ? F->coop_level : lt;
+    const int32_t *lidx = bp<const int32_t>(F->coop_idx);
+    for (int l = L1; l < lc; ++l) {
         int32_t r0 = F->rl_ptr[l], cnt = F->rl_ptr[l + 1] - r0;
         if (cnt > 0) LAUNCH_PDL(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ctv, Lf, r0, cnt, w, done);
     }
+    if (lc < lt)
+        SGP_TRY((launch_coop<T, true>(ctx, F, lt - lc, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done)));
     if (lt < F->levels) {
         const Tail tl = tail_of(F);
-        const size_t smem = tail_smem_bytes<T>(tl.n, tl.np, tl.nr);
-        LAUNCH_PDL(ctx, k_tree_tail<T>, 1, 1024, smem, tl, ord, rc, prp, L, Lf, Dinv, w, done);
+        const size_t staged = tail_smem_staged<T>(tl.n, tl.np, tl.nr);
+        if (staged <= (size_t)TREE_TAIL_SMEM)
+            LAUNCH_PDL(ctx, (k_tree_tail<T, true>), 1, 1024, staged, tl, ord, rc, prp, L, Lf, Dinv, w, done);
+        else
+            LAUNCH_PDL(ctx, (k_tree_tail<T, false>), 1, 1024, tail_smem_bytes<T>(tl.n, tl.np, tl.nr), tl, ord, rc,
+                       prp, L, Lf, Dinv, w, done);
     }
-    for (int l = lt - 1; l >= L1; --l) {
+    if (lc < lt)
+        SGP_TRY((launch_coop<T, false>(ctx, F, lt - lc, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done)));
+    for (int l = lc - 1; l >= L1; --l) {
         int32_t p0 = F->lvl_ptr[l], cnt = F->lvl_ptr[l + 1] - p0;
         if (cnt > 0) LAUNCH_PDL(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
     }
-    if (L1 > 0) LAUNCH_PDL(ctx, k_local_bwd<T>, F->ncomp, 256, lsm, la, L, Dinv, w, done);
+    if (L1 > 0) {
+        if (staged) LAUNCH_PDL(ctx, k_local_bwd_s<T>, F->ncomp, 512, bsm, ls, bLb, bD, w, done, mv[2], mv[3]);
+        else LAUNCH_PDL(ctx, k_local_bwd<T>, F->ncomp, 256, lsm, la, L, Dinv, w, done);
+    }
     return SGP_OK;
 }
 template sgp_status tree_apply_inplace<double>(sgp_ctx *, const sgp_factor *, double *, const int *);
@@ -943,12 +1347,18 @@ static sgp_status tail_smem_optin(sgp_ctx *ctx)
     static int done_dev[64] = {0};
     if (ctx->device >= 0 && ctx->device < 64 && done_dev[ctx->device]) return SGP_OK;
     const int bytes = TREE_TAIL_SMEM;
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (ctx->device >= 0 && ctx->device < 64) done_dev[ctx->device] = 1;
     return SGP_OK;
 }
@@ -1020,6 +1430,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     F->pl_ptr.assign(1, 0);
     F->cl_ptr.assign(1, 0);
     F->tail_level = 0;
+    F->coop_level = 0;
     const size_t n1 = (size_t)n + 1, P = 2 * (size_t)n + 2;
     SGP_TRY(buf_ensure(ctx, F->adj_ptr, sizeof(int32_t) * n1));
     SGP_TRY(buf_ensure(ctx, F->nbr, sizeof(int32_t) * (2 * nt + 1)));
@@ -1089,9 +1500,11 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     F->comp_size = local ? B : 0;
     F->local_levels = 0;
     F->ncomp = 0;
-    if (local) {
-        while ((1 << shift) < B) ++shift;
-        F->ncomp = (int32_t)((n + B - 1) >> shift);
+    {
+        if (local) {
+            while ((1 << shift) < B) ++shift;
+            F->ncomp = (int32_t)((n + B - 1) >> shift);
+        }
         SGP_TRY(buf_ensure(ctx, F->pre, sizeof(int32_t) * n1));
         SGP_TRY(buf_ensure(ctx, F->inv_pre, sizeof(int32_t) * n1));
         SGP_TRY(buf_ensure(ctx, F->pinned, sizeof(int32_t) * n1));
@@ -1141,7 +1554,8 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
                (const int32_t *)nbr, (const int32_t *)twin, (const int32_t *)dist, (const int32_t *)tid,
                (const int32_t *)voff, (const int32_t *)tsize, (const int32_t *)dflag, comp, n, ns, pre, perr);
         LAUNCH(ctx, k_blocks, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
-               (const int32_t *)nbr, (const int32_t *)pre, n, shift, bp<int32_t>(F->inv_pre), pinned, perr);
+               (const int32_t *)nbr, (const int32_t *)pre, n, local ? shift : 31, bp<int32_t>(F->inv_pre), pinned,
+               perr);
         int herr8 = 0;
         SGP_TRY(read_back(ctx, &herr8, perr, sizeof(int)));
         if (herr8) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: the depth-first order is not a permutation");
@@ -1281,6 +1695,59 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
             LAUNCH(ctx, k_block_ranges, grid_for(nb + 1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, pre,
                    F->lvl_ptr[l], F->lvl_ptr[l + 1], nb, shift, bp<int32_t>(F->poff) + (size_t)l * (nb + 1));
         }
+        // block-major copies
+        SGP_TRY(buf_ensure(ctx, F->bm_tab, sizeof(int32_t) * (size_t)nb * 4 * (L1 + 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_tot, sizeof(int32_t) * 4 * (size_t)nb));
+        SGP_TRY(buf_ensure(ctx, F->bm_base, sizeof(int32_t) * 4 * ((size_t)nb + 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_max, sizeof(int32_t) * 4));
+        SGP_CUDA(ctx, cudaMemsetAsync(F->bm_max.p, 0, sizeof(int32_t) * 4, ctx->stream));
+        int32_t *tab = bp<int32_t>(F->bm_tab), *tot = bp<int32_t>(F->bm_tot), *base = bp<int32_t>(F->bm_base);
+        LAUNCH(ctx, k_bm_tables, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)L1, nb, bp<const int32_t>(F->roff),
+               bp<const int32_t>(F->poff), (const int32_t *)rc_ptr, (const int32_t *)pr_ptr, tab, tot,
+               bp<int32_t>(F->bm_max));
+        for (int k = 0; k < 4; ++k)
+            SGP_TRY(scan_exclusive_i32(ctx, tot + (size_t)k * nb, base + (size_t)k * (nb + 1), nb));
+        SGP_TRY(read_back(ctx, F->bm_maxv, F->bm_max.p, sizeof(int32_t) * 4));
+        const bool m32 = F->precision == SGP_PREC_MIXED;
+        SGP_TRY(buf_ensure(ctx, F->bm_q, sizeof(int32_t) * std::max(nr1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_beg, sizeof(int32_t) * std::max(nr1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_cloc, sizeof(int32_t) * std::max(nc1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_Lf, sizeof(double) * 9 * std::max(nc1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_oloc, sizeof(int32_t) * std::max(no1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_pbeg, sizeof(int32_t) * std::max(no1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_D, sizeof(double) * 6 * std::max(no1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_qloc, sizeof(int32_t) * std::max(nq1, 1)));
+        SGP_TRY(buf_ensure(ctx, F->bm_Lb, sizeof(double) * 9 * std::max(nq1, 1)));
+        if (m32) {
+            SGP_TRY(buf_ensure(ctx, F->bm_Lf32, sizeof(float) * 9 * std::max(nc1, 1)));
+            SGP_TRY(buf_ensure(ctx, F->bm_D32, sizeof(float) * 6 * std::max(no1, 1)));
+            SGP_TRY(buf_ensure(ctx, F->bm_Lb32, sizeof(float) * 9 * std::max(nq1, 1)));
+        }
+        const int32_t *cpre = pre, *croff = bp<const int32_t>(F->roff), *cpoff = bp<const int32_t>(F->poff);
+        for (int l = 0; l < L1; ++l) {
+            const int32_t r0 = F->rl_ptr[l], rn = F->rl_ptr[l + 1] - r0;
+            const int32_t j0 = F->cl_ptr[l], jn = F->cl_ptr[l + 1] - j0;
+            const int32_t t0 = F->lvl_ptr[l], tn = F->lvl_ptr[l + 1] - t0;
+            const int32_t q0 = F->pl_ptr[l], qn = F->pl_ptr[l + 1] - q0;
+            LAUNCH(ctx, k_bm_recv, grid_for(rn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, r0, rn,
+                   (const int32_t *)rv, cpre, croff, (const int32_t *)rc_ptr, (const int32_t *)tab,
+                   (const int32_t *)base, bp<const int32_t>(F->loc_r), bp<int32_t>(F->bm_q), bp<int32_t>(F->bm_beg));
+            LAUNCH(ctx, k_bm_contrib, grid_for(jn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, j0,
+                   jn, bp<const int32_t>(F->ctv), cpre, croff, (const int32_t *)rc_ptr, (const int32_t *)tab,
+                   (const int32_t *)base, bp<const int32_t>(F->loc_c), bp<const double>(F->Lf),
+                   m32 ? bp<const float>(F->Lf32) : (const float *)nullptr, bp<int32_t>(F->bm_cloc),
+                   bp<double>(F->bm_Lf), m32 ? bp<float>(F->bm_Lf32) : (float *)nullptr);
+            LAUNCH(ctx, k_bm_pos, grid_for(tn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, t0, tn,
+                   (const int32_t *)ord, cpre, cpoff, (const int32_t *)pr_ptr, (const int32_t *)tab,
+                   (const int32_t *)base, bp<const int32_t>(F->loc_o), bp<const double>(F->Dinv),
+                   m32 ? bp<const float>(F->Dinv32) : (const float *)nullptr, bp<int32_t>(F->bm_oloc),
+                   bp<int32_t>(F->bm_pbeg), bp<double>(F->bm_D), m32 ? bp<float>(F->bm_D32) : (float *)nullptr);
+            LAUNCH(ctx, k_bm_pair, grid_for(qn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, q0, qn,
+                   (const int32_t *)pr_c, cpre, cpoff, (const int32_t *)pr_ptr, (const int32_t *)tab,
+                   (const int32_t *)base, bp<const int32_t>(F->loc_q), bp<const double>(F->L),
+                   m32 ? bp<const float>(F->L32) : (const float *)nullptr, bp<int32_t>(F->bm_qloc),
+                   bp<double>(F->bm_Lb), m32 ? bp<float>(F->bm_Lb32) : (float *)nullptr);
+        }
     }
     int lt = L1;
     auto tail_bytes = [&](int l) {
@@ -1292,6 +1759,30 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
                               (ctx->tail_cap >= 0 && n - F->lvl_ptr[lt] > ctx->tail_cap)))
         ++lt;
     F->tail_level = lt;
+    // the cooperative middle: from the first level with at most coop_cap
+    // vertices left up to the tail
+    {
+        int lc = lt;
+        if (ctx->coop_cap > 0)
+            for (int l = L1; l < lt; ++l)
+                if (n - F->lvl_ptr[l] <= ctx->coop_cap) {
+                    lc = l;
+                    break;
+                }
+        F->coop_level = lc;
+        if (lc < lt) {
+            const int nl = lt - lc;
+            std::vector<int32_t> idx(2 * (nl + 1));
+            for (int l = 0; l <= nl; ++l) {
+                idx[l] = F->lvl_ptr[lc + l];
+                idx[nl + 1 + l] = F->rl_ptr[lc + l];
+            }
+            SGP_TRY(buf_ensure(ctx, F->coop_idx, sizeof(int32_t) * idx.size()));
+            SGP_CUDA(ctx, cudaMemcpyAsync(F->coop_idx.p, idx.data(), sizeof(int32_t) * idx.size(),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+            SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
+        }
+    }
     if (lt < F->levels) {
         SGP_TRY(tail_smem_optin(ctx));
         const int nl = F->levels - lt;
@@ -1361,7 +1852,10 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->rflag, &F->cnt, &F->ctv, &F->Lf, &F->Lf32, &F->tail_idx, &F->tail_q,
                     &F->tail_c, &F->tail_b, &F->pre, &F->inv_pre, &F->loc_r, &F->loc_c, &F->loc_o,
                     &F->loc_q, &F->roff, &F->poff, &F->et_succ, &F->et_dist, &F->et_succ2,
-                    &F->et_dist2, &F->et_tid, &F->et_size, &F->et_flag, &F->pinned};
+                    &F->et_dist2, &F->et_tid, &F->et_size, &F->et_flag, &F->pinned, &F->bm_tab,
+                    &F->bm_tot, &F->bm_base, &F->bm_max, &F->bm_q, &F->bm_beg, &F->bm_cloc, &F->bm_oloc,
+                    &F->bm_pbeg, &F->bm_qloc, &F->bm_Lf, &F->bm_Lf32, &F->bm_Lb, &F->bm_Lb32, &F->bm_D,
+                    &F->bm_D32, &F->coop_idx};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete F;

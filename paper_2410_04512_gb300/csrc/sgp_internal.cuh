@@ -63,6 +63,7 @@ struct sgp_ctx {
     int spmv_lpr = 0;
     int tail_cap = 1024;    // largest tail of the tree solve in vertices (-1: what fits)
     int comp_size = 0;      // block of the local phase of the tree factor (0: none)
+    int coop_cap = 0;       // vertices left when one cooperative kernel takes over the levels (0: none)
     int use_pdl = 1;        // programmatic dependent launch of the level kernels
     int batch_chunk = 0;    // rows per work item of the batched solver
     int num_sms = 0;
@@ -220,6 +221,9 @@ struct sgp_factor {
     DBuf Lf, Lf32;  // L blocks in ct order (forward pass streams them)
     // tail: levels >= tail_level run in one thread block (positions >= tail_P0)
     int32_t tail_level = 0, tail_P0 = 0, tail_R0 = 0, tail_C0 = 0, tail_Q0 = 0;
+    // levels [coop_level, tail_level) run in one cooperative kernel per direction
+    int32_t coop_level = 0;
+    DBuf coop_idx;  // (nlev + 1) positions, then (nlev + 1) receiver offsets
     DBuf tail_idx;  // level positions and receiver offsets of the tail levels
     DBuf tail_q, tail_c, tail_b;  // local indices (position - tail_P0)
     DBuf work;      // n x 3 float64 apply workspace
@@ -231,6 +235,13 @@ struct sgp_factor {
     DBuf pre, inv_pre;          // n int32: preorder number of each vertex and its inverse
     DBuf loc_r, loc_c, loc_o, loc_q;  // local (in-block) index of rv, ctv, ord, pr_q entries
     DBuf roff, poff;            // local_levels x (ncomp + 1) receiver / position ranges per block
+    // block-major copies of the local levels' data (each block's forward
+    // entries, contributors, positions and pairs, level after level), so that
+    // a thread block stages its whole share with contiguous loads
+    DBuf bm_tab, bm_tot, bm_base, bm_max;   // per-block per-level prefix counts, totals, bases, maxima
+    DBuf bm_q, bm_beg, bm_cloc, bm_oloc, bm_pbeg, bm_qloc;
+    DBuf bm_Lf, bm_Lf32, bm_Lb, bm_Lb32, bm_D, bm_D32;
+    int32_t bm_maxv[4] = {0, 0, 0, 0};      // largest per-block count of each kind
     DBuf et_succ, et_dist, et_succ2, et_dist2, et_tid, et_size, et_flag, pinned;  // Euler tour scratch
     // structure-simulation scratch
     DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,

@@ -61,6 +61,7 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *t)
     t->tail_cap = ctx->tail_cap;
     t->batch_chunk = ctx->batch_chunk;
     t->comp_size = ctx->comp_size;
+    t->coop_cap = ctx->coop_cap;
     t->ms_per_iteration = 0.0;
     return SGP_OK;
 }
@@ -71,6 +72,8 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     if (!(t->spmv_lpr == 0 || t->spmv_lpr == 1 || t->spmv_lpr == 2 || t->spmv_lpr == 4 || t->spmv_lpr == 8))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_lpr must be 0, 1, 2, 4 or 8");
     if (t->tail_cap < -1) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: tail_cap must be >= -1");
+    if (t->coop_cap != 0 && (t->coop_cap < 256 || t->coop_cap > (1 << 24)))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: coop_cap must be 0 or in [256, 16777216]");
     if (t->batch_chunk != 0 && (t->batch_chunk < 256 || t->batch_chunk > 65536))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: batch_chunk must be 0 or in [256, 65536]");
     if (!(t->comp_size == 0 || (t->comp_size >= 64 && t->comp_size <= 8192 &&
@@ -79,6 +82,7 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     ctx->spmv_lpr = t->spmv_lpr;
     ctx->tail_cap = t->tail_cap;
     ctx->comp_size = t->comp_size;
+    ctx->coop_cap = t->coop_cap;
     ctx->batch_chunk = t->batch_chunk;
     return SGP_OK;
 }
@@ -145,6 +149,17 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
             if (ms < best_ms) best_ms = ms, best_cap = cap;
         }
         ctx->tail_cap = best_cap;
+        const int coops[] = {0, 8192, 32768, 131072};
+        int best_coop = ctx->coop_cap;
+        best_ms = 1e300;
+        for (int cc : coops) {
+            ctx->coop_cap = cc;
+            if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
+            double ms;
+            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
+            if (ms < best_ms) best_ms = ms, best_coop = cc;
+        }
+        ctx->coop_cap = best_coop;
         if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
     }
     // 2. lanes per block row of the product

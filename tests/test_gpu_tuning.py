@@ -19,19 +19,21 @@ def ctx(cuda_device):
 
 def test_set_tuning_validates(ctx):
     for bad in (dict(spmv_lpr=3), dict(tail_cap=-2), dict(batch_chunk=100), dict(batch_chunk=70000),
-                dict(comp_size=1000), dict(comp_size=32), dict(comp_size=16384)):
+                dict(comp_size=1000), dict(comp_size=32), dict(comp_size=16384), dict(coop_cap=100),
+                dict(coop_cap=1 << 25)):
         with pytest.raises(sgp.SgpError):
             ctx.set_tuning(**bad)
-    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256)
+    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096)
     assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "comp_size": 256,
-                                "ms_per_iteration": 0.0}
+                                "coop_cap": 4096, "ms_per_iteration": 0.0}
 
 
-@pytest.mark.parametrize("cap,cs", [(0, 0), (64, 1024), (256, 64), (-1, 256), (1024, 8192), (0, 4096)])
+@pytest.mark.parametrize("cap,cs,coop", [(0, 0, 0), (64, 1024, 0), (256, 64, 2048), (-1, 256, 0), (1024, 8192, 0),
+                                         (0, 4096, 0), (1024, 0, 8192), (0, 0, 20000), (256, 1024, 4096)])
 @pytest.mark.parametrize("prec", [sgp.PREC_F64, sgp.PREC_MIXED])
-def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, prec):
+def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, coop, prec):
     c = workloads.ball(n=20000, seed=2002, gamma0=1e-3)
-    ctx.set_tuning(tail_cap=cap, comp_size=cs)
+    ctx.set_tuning(tail_cap=cap, comp_size=cs, coop_cap=coop)
     s = GpuSystem(ctx, c, precision=prec)
     F = c.forces()
     v, info = ctx.pcg_solve(s.M, s.Fac, dev_tensor(F), tol=1e-10, precision=prec)
@@ -61,6 +63,7 @@ def test_autotune_single_system(ctx):
     t = ctx.autotune(s.M, s.T, s.Fac, F, precision=sgp.PREC_MIXED, iterations=20)
     assert t["tail_cap"] in (0, 256, 512, 1024, 2048, 4096, -1)
     assert t["comp_size"] in (0, 256, 512, 1024, 2048, 4096)
+    assert t["coop_cap"] in (0, 8192, 32768, 131072)
     assert t["spmv_lpr"] in (1, 2, 4, 8)
     assert t["ms_per_iteration"] > 0
     assert ctx.get_tuning()["tail_cap"] == t["tail_cap"]
