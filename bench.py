@@ -127,6 +127,32 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# replicas: one independent system per rank, no data-path collective
+# ---------------------------------------------------------------------------
+def replica_seed(rank: int) -> int:
+    """Seed of rank `rank`'s replica of the workload (rank 0: the default)."""
+    return 2000 + rank
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """MAX of a per-rank value over the default process group (the slowest
+    rank's time); the value itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, steps: int, max_elapsed_s: float) -> float:
+    """Whole-job solves per second: every rank solved `steps` systems, the job
+    took as long as its slowest rank."""
+    return world * steps / max_elapsed_s
+
+
+# ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
 def tree_bytes(n: int, npairs: int, nrecv: int, fp: int) -> int:
@@ -166,7 +192,7 @@ def run_gpu(args):
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
 
     wl = WORKLOADS[args.workload]
-    cells = wl["make"](2000 + rank)          # each rank: its own independent replica
+    cells = wl["make"](replica_seed(rank))   # each rank: its own independent replica
     n = cells.n
     F_host = cells.forces()
     tp, tq = cells.tables()
@@ -233,10 +259,7 @@ def run_gpu(args):
             kt = {k: ctx.kernel_time(k) for k in (sgp.KT_SPMV, sgp.KT_TREE_SOLVE, sgp.KT_PCG_VECTOR)}
             launches = ctx.launch_count()
             ctx.set_kernel_timing(False)
-            if world > 1:
-                t = torch.tensor([elapsed], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                elapsed = float(t.item())
+            elapsed = max_over_ranks(elapsed, dev)
             return dict(elapsed=elapsed, solve_ms=float(np.median(solve_ms)), iters=float(np.mean(iters)),
                         info=self.last[0], kt=kt, launches=launches, v=v)
 
@@ -252,7 +275,7 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         res = chosen.timed(args.steps, args.warmup, kernel_timing=True)
     elapsed = res["elapsed"]
-    value = world * args.steps / elapsed
+    value = replica_throughput(world, args.steps, elapsed)
     info = res["info"]
 
     # ---- end to end through the public API from pinned host buffers -------
@@ -277,11 +300,8 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_value = replica_throughput(world, e2e_steps, e2e_s)
 
     # ---- rooflines of the two per-iteration kernels -----------------------
     M = chosen.H["M"]
