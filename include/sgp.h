@@ -309,7 +309,8 @@ typedef struct {
                             one cooperative kernel per direction with grid-wide
                             barriers instead of one launch per level; 0 (none,
                             default) or 256..16777216; read when a factor is built */
-    int32_t reserved;
+    int32_t spmv_ilp;    /* row groups each lane of the PCG product keeps in flight
+                            at once: 0 (default, 1), 1 or 2 */
     double ms_per_iteration; /* sgp_autotune: time of one PCG iteration with the
                                 chosen values; 0 from sgp_get_tuning */
 } sgp_tuning;
@@ -323,7 +324,7 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *tuning);
  * {0, 8192, 32768, 131072} (tree
  * preconditioner only; *factor is rebuilt from `tree` for each candidate
  * and left built with the chosen values), then spmv_lpr in
- * {1, 2, 4, 8}, then, when n_instances > 0 (a batch with host `offsets`, as
+ * {1, 2, 4, 8} with spmv_ilp in {1, 2}, then, when n_instances > 0 (a batch with host `offsets`, as
  * for sgp_pcg_solve_batched), batch_chunk in {512, ..., 8192} with the
  * batched solver timed throughout.  The choice is stored in the context and
  * copied to `out` (may be NULL).  F_dev is only read.  On failure the

@@ -66,7 +66,9 @@ __global__ void k_spmv(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, 
 // array; the lanes' partial sums meet by shuffles.  The difference form is
 // accumulated with fused multiply-adds (9 FMA + 3 subtractions per slot).
 // Loops are warp-uniform so the shuffles always see all 32 lanes.
-template <typename T, int LPR>
+// ILP row groups are in flight per lane at once (their slot loads and
+// gathers interleave), which hides the block-load -> gather latency chain.
+template <typename T, int LPR, int ILP>
 __global__ void __launch_bounds__(RB) k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0,
                                                 int64_t n, const T *__restrict__ p, T *q, double *partials,
                                                 Scal *sc)
@@ -77,43 +79,67 @@ __global__ void __launch_bounds__(RB) k_spmv_pq(Blk<T> B, const int32_t *__restr
     const int lane = threadIdx.x & 31, g = lane % LPR;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t stride = nwarps * RPW;
     double acc = 0.0;
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
-        const int64_t i = base + lane / LPR;
-        const bool active = i < n;
-        T y0 = 0, y1 = 0, y2 = 0, v0 = 0, v1 = 0, v2 = 0;
-        if (active) {
-            v0 = p[3 * i]; v1 = p[3 * i + 1]; v2 = p[3 * i + 2];
-            const int32_t s1 = row_ptr[i + 1];
-            for (int32_t s = row_ptr[i] + g; s < s1; s += LPR) {
-                T S[6];
-                int32_t j;
-                B.load(s, S, j);
-                const T d0 = v0 - p[3 * (int64_t)j], d1 = v1 - p[3 * (int64_t)j + 1],
-                        d2 = v2 - p[3 * (int64_t)j + 2];
-                y0 = fma(S[0], d0, y0); y0 = fma(S[1], d1, y0); y0 = fma(S[2], d2, y0);
-                y1 = fma(S[1], d0, y1); y1 = fma(S[3], d1, y1); y1 = fma(S[4], d2, y1);
-                y2 = fma(S[2], d0, y2); y2 = fma(S[4], d1, y2); y2 = fma(S[5], d2, y2);
+    for (int64_t base = warp * RPW; base < n; base += ILP * stride) {
+        int64_t i[ILP];
+        bool active[ILP];
+        T y0[ILP], y1[ILP], y2[ILP], v0[ILP], v1[ILP], v2[ILP];
+        int32_t s[ILP], e[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            i[u] = base + u * stride + lane / LPR;
+            active[u] = i[u] < n;
+            y0[u] = y1[u] = y2[u] = v0[u] = v1[u] = v2[u] = 0;
+            s[u] = e[u] = 0;
+            if (active[u]) {
+                v0[u] = p[3 * i[u]]; v1[u] = p[3 * i[u] + 1]; v2[u] = p[3 * i[u] + 2];
+                s[u] = row_ptr[i[u]] + g;
+                e[u] = row_ptr[i[u] + 1];
             }
+        }
+        bool more = true;
+        while (more) {
+            more = false;
+            T S[ILP][6];
+            int32_t j[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (s[u] < e[u]) B.load(s[u], S[u], j[u]);
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (s[u] < e[u]) {
+                    const T d0 = v0[u] - p[3 * (int64_t)j[u]], d1 = v1[u] - p[3 * (int64_t)j[u] + 1],
+                            d2 = v2[u] - p[3 * (int64_t)j[u] + 2];
+                    y0[u] = fma(S[u][0], d0, y0[u]); y0[u] = fma(S[u][1], d1, y0[u]); y0[u] = fma(S[u][2], d2, y0[u]);
+                    y1[u] = fma(S[u][1], d0, y1[u]); y1[u] = fma(S[u][3], d1, y1[u]); y1[u] = fma(S[u][4], d2, y1[u]);
+                    y2[u] = fma(S[u][2], d0, y2[u]); y2[u] = fma(S[u][4], d1, y2[u]); y2[u] = fma(S[u][5], d2, y2[u]);
+                    s[u] += LPR;
+                    more = more || s[u] < e[u];
+                }
         }
 #pragma unroll
-        for (int o = LPR / 2; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-            y2 += __shfl_xor_sync(0xffffffffu, y2, o);
-        }
-        if (active) {
-            y0 = fma(gamma0, v0, y0);
-            y1 = fma(gamma0, v1, y1);
-            y2 = fma(gamma0, v2, y2);
-            if (LPR >= 3) {
-                if (g < 3) q[3 * i + g] = g == 0 ? y0 : (g == 1 ? y1 : y2);
-            } else if (g == 0) {
-                q[3 * i] = y0; q[3 * i + 1] = y1; q[3 * i + 2] = y2;
+        for (int u = 0; u < ILP; ++u) {
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) {
+                y0[u] += __shfl_xor_sync(0xffffffffu, y0[u], o);
+                y1[u] += __shfl_xor_sync(0xffffffffu, y1[u], o);
+                y2[u] += __shfl_xor_sync(0xffffffffu, y2[u], o);
             }
-            // the row's three products are summed in T, the running sum in
-            // FP64 (one conversion per row keeps FP32 rows off the FP64 pipe)
-            if (g == 0) acc += (double)fma(v0, y0, fma(v1, y1, v2 * y2));
+            if (active[u]) {
+                const T a0 = fma(gamma0, v0[u], y0[u]);
+                const T a1 = fma(gamma0, v1[u], y1[u]);
+                const T a2 = fma(gamma0, v2[u], y2[u]);
+                if (LPR >= 3) {
+                    if (g < 3) q[3 * i[u] + g] = g == 0 ? a0 : (g == 1 ? a1 : a2);
+                } else if (g == 0) {
+                    q[3 * i[u]] = a0; q[3 * i[u] + 1] = a1; q[3 * i[u] + 2] = a2;
+                }
+                // the row's three products are summed in T, the running sum
+                // in FP64 (one conversion per row keeps FP32 rows off the
+                // FP64 pipe)
+                if (g == 0) acc += (double)fma(v0[u], a0, fma(v1[u], a1, v2[u] * a2));
+            }
         }
     }
     double s = block_sum<RB>(acc, sh);
@@ -457,6 +483,7 @@ sgp_status launch_spmv_pq(sgp_ctx *ctx, Blk<T> B, const int32_t *row_ptr, T g0, 
                           T *q, double *partials, Scal *sc)
 {
     const int lpr = ctx->spmv_lpr > 0 ? ctx->spmv_lpr : (sizeof(T) == 8 ? 1 : 2);
+    const int ilp = ctx->spmv_ilp > 0 ? ctx->spmv_ilp : 1;
     const int64_t want = (n * lpr + RB - 1) / RB;
     auto go = [&](auto kern) -> sgp_status {
         unsigned G;
@@ -464,11 +491,19 @@ sgp_status launch_spmv_pq(sgp_ctx *ctx, Blk<T> B, const int32_t *row_ptr, T g0, 
         LAUNCH(ctx, kern, G, RB, 0, B, row_ptr, g0, n, p, q, partials, sc);
         return SGP_OK;
     };
+    if (ilp == 2) {
+        switch (lpr) {
+        case 1: return go(k_spmv_pq<T, 1, 2>);
+        case 2: return go(k_spmv_pq<T, 2, 2>);
+        case 8: return go(k_spmv_pq<T, 8, 2>);
+        default: return go(k_spmv_pq<T, 4, 2>);
+        }
+    }
     switch (lpr) {
-    case 1: return go(k_spmv_pq<T, 1>);
-    case 2: return go(k_spmv_pq<T, 2>);
-    case 8: return go(k_spmv_pq<T, 8>);
-    default: return go(k_spmv_pq<T, 4>);
+    case 1: return go(k_spmv_pq<T, 1, 1>);
+    case 2: return go(k_spmv_pq<T, 2, 1>);
+    case 8: return go(k_spmv_pq<T, 8, 1>);
+    default: return go(k_spmv_pq<T, 4, 1>);
     }
 }
 
@@ -574,7 +609,7 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
                             (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q, (uint64_t)(uintptr_t)w,
                             (uint64_t)(uintptr_t)partials, (uint64_t)(uintptr_t)sc,
                             (uint64_t)(uintptr_t)jac, (uint64_t)ctx->timing, (uint64_t)chunk,
-                            (uint64_t)ctx->spmv_lpr};
+                            (uint64_t)ctx->spmv_lpr, (uint64_t)ctx->spmv_ilp};
     GraphEntry *ge = nullptr;
     SGP_TRY(graph_lookup(ctx, key, sizeof(key) / sizeof(key[0]), &ge));
     if (!ge->exec) SGP_TRY(graph_capture(ctx, ge, [&]() { return iterate(chunk); }));

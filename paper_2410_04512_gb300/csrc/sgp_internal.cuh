@@ -61,6 +61,7 @@ struct sgp_ctx {
     size_t d_scan_bytes = 0;
     // tuning knobs (0 = built-in default)
     int spmv_lpr = 0;
+    int spmv_ilp = 0;       // row groups in flight per lane in the product (0: 1)
     int tail_cap = 1024;    // largest tail of the tree solve in vertices (-1: what fits)
     int comp_size = 0;      // block of the local phase of the tree factor (0: none)
     int coop_cap = 0;       // vertices left when one cooperative kernel takes over the levels (0: none)

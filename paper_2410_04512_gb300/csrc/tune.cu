@@ -62,6 +62,7 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *t)
     t->batch_chunk = ctx->batch_chunk;
     t->comp_size = ctx->comp_size;
     t->coop_cap = ctx->coop_cap;
+    t->spmv_ilp = ctx->spmv_ilp;
     t->ms_per_iteration = 0.0;
     return SGP_OK;
 }
@@ -72,6 +73,8 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     if (!(t->spmv_lpr == 0 || t->spmv_lpr == 1 || t->spmv_lpr == 2 || t->spmv_lpr == 4 || t->spmv_lpr == 8))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_lpr must be 0, 1, 2, 4 or 8");
     if (t->tail_cap < -1) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: tail_cap must be >= -1");
+    if (t->spmv_ilp < 0 || t->spmv_ilp > 2)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_ilp must be 0, 1 or 2");
     if (t->coop_cap != 0 && (t->coop_cap < 256 || t->coop_cap > (1 << 24)))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: coop_cap must be 0 or in [256, 16777216]");
     if (t->batch_chunk != 0 && (t->batch_chunk < 256 || t->batch_chunk > 65536))
@@ -83,6 +86,7 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     ctx->tail_cap = t->tail_cap;
     ctx->comp_size = t->comp_size;
     ctx->coop_cap = t->coop_cap;
+    ctx->spmv_ilp = t->spmv_ilp;
     ctx->batch_chunk = t->batch_chunk;
     return SGP_OK;
 }
@@ -162,19 +166,22 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
         ctx->coop_cap = best_coop;
         if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
     }
-    // 2. lanes per block row of the product
+    // 2. lanes per block row of the product and rows in flight per lane
     {
         const int lprs[] = {1, 2, 4, 8};
-        int best_lpr = ctx->spmv_lpr;
+        int best_lpr = ctx->spmv_lpr, best_ilp = ctx->spmv_ilp;
         best_ms = 1e300;
-        for (int lpr : lprs) {
-            if (n_instances > 0 && lpr == 8) continue;   // the batched product stops at 4
-            ctx->spmv_lpr = lpr;
-            double ms;
-            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
-            if (ms < best_ms) best_ms = ms, best_lpr = lpr;
-        }
+        for (int ilp = 1; ilp <= (n_instances > 0 ? 1 : 2); ++ilp)
+            for (int lpr : lprs) {
+                if (n_instances > 0 && lpr == 8) continue;   // the batched product stops at 4
+                ctx->spmv_lpr = lpr;
+                ctx->spmv_ilp = ilp;
+                double ms;
+                if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
+                if (ms < best_ms) best_ms = ms, best_lpr = lpr, best_ilp = ilp;
+            }
         ctx->spmv_lpr = best_lpr;
+        ctx->spmv_ilp = best_ilp;
     }
     // 3. rows per work item of the batched solver
     if (n_instances > 0) {

@@ -20,12 +20,12 @@ def ctx(cuda_device):
 def test_set_tuning_validates(ctx):
     for bad in (dict(spmv_lpr=3), dict(tail_cap=-2), dict(batch_chunk=100), dict(batch_chunk=70000),
                 dict(comp_size=1000), dict(comp_size=32), dict(comp_size=16384), dict(coop_cap=100),
-                dict(coop_cap=1 << 25)):
+                dict(coop_cap=1 << 25), dict(spmv_ilp=3)):
         with pytest.raises(sgp.SgpError):
             ctx.set_tuning(**bad)
-    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096)
+    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096, spmv_ilp=2)
     assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "comp_size": 256,
-                                "coop_cap": 4096, "ms_per_iteration": 0.0}
+                                "coop_cap": 4096, "spmv_ilp": 2, "ms_per_iteration": 0.0}
 
 
 @pytest.mark.parametrize("cap,cs,coop", [(0, 0, 0), (64, 1024, 0), (256, 64, 2048), (-1, 256, 0), (1024, 8192, 0),
@@ -44,13 +44,14 @@ def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, coop
     assert rel_err(v.cpu().numpy(), vr.cpu().numpy()) <= 1e-8
 
 
+@pytest.mark.parametrize("ilp", [1, 2])
 @pytest.mark.parametrize("lpr", [1, 2, 4, 8])
-def test_lanes_per_row_do_not_change_the_solution(ctx, lpr):
+def test_lanes_per_row_do_not_change_the_solution(ctx, lpr, ilp):
     c = small_cube(3000, seed=1003)
     s = GpuSystem(ctx, c)
     o = oracle_system(c)
     F = c.forces()
-    ctx.set_tuning(spmv_lpr=lpr)
+    ctx.set_tuning(spmv_lpr=lpr, spmv_ilp=ilp)
     v, info = ctx.pcg_solve(s.M, s.Fac, dev_tensor(F), tol=1e-12)
     ref, _ = oracle.solve_system(o, F, tol=1e-13)
     assert rel_err(v.cpu().numpy(), ref.x) <= 1e-9
@@ -64,7 +65,7 @@ def test_autotune_single_system(ctx):
     assert t["tail_cap"] in (0, 256, 512, 1024, 2048, 4096, -1)
     assert t["comp_size"] in (0, 256, 512, 1024, 2048, 4096)
     assert t["coop_cap"] in (0, 8192, 32768, 131072)
-    assert t["spmv_lpr"] in (1, 2, 4, 8)
+    assert t["spmv_lpr"] in (1, 2, 4, 8) and t["spmv_ilp"] in (1, 2)
     assert t["ms_per_iteration"] > 0
     assert ctx.get_tuning()["tail_cap"] == t["tail_cap"]
     # the factor handle was left built with the chosen tail and still solves

@@ -139,6 +139,19 @@ def test_contacts_against_kdtree():
     np.testing.assert_array_equal(sub, ij[np.isin(ij[:, 0], rows)])
 
 
+@pytest.mark.parametrize("kind", ["cube", "ball", "sheet"])
+def test_kdtree_contacts_equal_the_brute_force_scan(kind):
+    c = {"cube": lambda: small_cells(900, seed=8),
+         "ball": lambda: workloads.ball(n=1500, seed=9),
+         "sheet": lambda: workloads.hex_sheet(nx=40, ny=30, seed=10)}[kind]()
+    np.testing.assert_array_equal(oracle.contacts_kdtree(c.pos, c.radii), oracle.contacts(c.pos, c.radii))
+    # pairs exactly at the contact distance stay out on both sides
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [2.25, 0.0, 0.0]])
+    radii = np.array([0.5, 0.5, 0.9])
+    np.testing.assert_array_equal(oracle.contacts_kdtree(pos, radii), oracle.contacts(pos, radii))
+    assert oracle.contacts(pos, radii).tolist() == [[1, 2]]
+
+
 def test_degenerate_coincident_centres():
     pos = np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0]])
     ij = oracle.contacts(pos, np.array([0.5, 0.5]))
