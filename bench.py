@@ -271,7 +271,7 @@ def run_gpu(args):
         # (outside the timed region; the factor is rebuilt every step anyway)
         chosen.step(pos, radii, F, torch.zeros_like(F))
         tuning = ctx.autotune(chosen.H["M"], chosen.H["T"], chosen.H["Fh"], F, precond=chosen.precond,
-                              precision=chosen.precision, iterations=args.autotune)
+                              precision=chosen.precision, iterations=0, tol=args.tol)
     with ClockSampler(local) as clk:
         res = chosen.timed(args.steps, args.warmup, kernel_timing=True)
     elapsed = res["elapsed"]
@@ -421,8 +421,7 @@ def run_batch(args):
     tuning = None
     if args.autotune:
         step(v)
-        tuning = ctx.autotune(H["M"], H["T"], H["Fh"], F, offsets=off, precision=prec,
-                              iterations=max(5, args.autotune // 3))
+        tuning = ctx.autotune(H["M"], H["T"], H["Fh"], F, offsets=off, precision=prec, iterations=0, tol=args.tol)
     for _ in range(args.warmup):
         step(v)
     torch.cuda.synchronize()
@@ -680,8 +679,9 @@ def main():
     ap.add_argument("--compare", type=int, default=1, help="also time plain FP64 and block-Jacobi")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-sample-cells", type=int, default=20000)
-    ap.add_argument("--autotune", type=int, default=30,
-                    help="PCG iterations per autotuner candidate before timing (0: built-in defaults)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick the launch shapes with the library's autotuner before timing "
+                         "(whole solves plus factor builds per candidate); 0: built-in defaults")
     ap.add_argument("--warm-steps", dest="warm_steps", type=int, default=200)
     ap.add_argument("--warm-train", dest="warm_train", type=int, default=50)
     ap.add_argument("--warm-epochs", dest="warm_epochs", type=int, default=8)

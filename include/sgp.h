@@ -311,24 +311,28 @@ typedef struct {
                             default) or 256..16777216; read when a factor is built */
     int32_t spmv_ilp;    /* row groups each lane of the PCG product keeps in flight
                             at once: 0 (default, 1), 1 or 2 */
-    double ms_per_iteration; /* sgp_autotune: time of one PCG iteration with the
-                                chosen values; 0 from sgp_get_tuning */
+    double ms_per_iteration; /* sgp_autotune: the winning objective (ms per PCG
+                                iteration, or per factor build + solve); 0 from
+                                sgp_get_tuning */
 } sgp_tuning;
 sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *tuning);
 /* INVALID_ARG for a value outside the ranges above (nothing is changed). */
 sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *tuning);
-/* Time `iterations` PCG iterations (opts' precision and preconditioner, the
- * tolerance ignored) of the caller's system for each candidate and keep the
- * fastest, one knob after the other: comp_size in {0, 256, 512, 1024, 2048,
- * 4096}, tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} and coop_cap in
- * {0, 8192, 32768, 131072} (tree
- * preconditioner only; *factor is rebuilt from `tree` for each candidate
- * and left built with the chosen values), then spmv_lpr in
- * {1, 2, 4, 8} with spmv_ilp in {1, 2}, then, when n_instances > 0 (a batch with host `offsets`, as
- * for sgp_pcg_solve_batched), batch_chunk in {512, ..., 8192} with the
- * batched solver timed throughout.  The choice is stored in the context and
- * copied to `out` (may be NULL).  F_dev is only read.  On failure the
- * previous tuning is restored.  Synchronises. */
+/* Pick the knobs by timing the caller's own system for each candidate, one
+ * knob after the other: comp_size in {0, 256, 512, 1024, 2048, 4096},
+ * tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} and coop_cap in
+ * {0, 8192, 32768, 131072} (tree preconditioner only; *factor is rebuilt
+ * from `tree` for each candidate and left built with the chosen values), then
+ * spmv_lpr in {1, 2, 4, 8} with spmv_ilp in {1, 2}, then, when n_instances > 0
+ * (a batch with host `offsets`, as for sgp_pcg_solve_batched), batch_chunk in
+ * {512, ..., 8192} with the batched solver timed throughout.  The objective
+ * is the time of one PCG iteration when iterations > 0 (each timed solve
+ * runs exactly that many iterations; opts->tol is ignored), or, when
+ * iterations == 0, the time of a whole solve to opts->tol plus the factor
+ * build of the candidate (the cost of one time step).  The choice is stored
+ * in the context and copied to `out` (may be NULL; ms_per_iteration then
+ * holds the winning objective).  F_dev is only read.  On failure the previous
+ * tuning is restored.  Synchronises. */
 sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_tree *tree, sgp_factor **factor,
                         int64_t n_instances, const int64_t *offsets, const double *F_dev,
                         const sgp_solve_opts *opts, int32_t iterations, sgp_tuning *out);

@@ -422,12 +422,14 @@ class Context:
         self._ok(_lib.sgp_set_tuning(self.ptr, ctypes.byref(t)))
 
     def autotune(self, M: Matrix, T: Tree | None, Fh: Factor | None, F: torch.Tensor, offsets=None,
-                 precond: int = PRECOND_TREE, precision: int = PREC_F64, iterations: int = 30) -> dict:
-        """Pick the launch-shape knobs by timing `iterations` PCG iterations
-        per candidate (rebuilds Fh in place for each tail size)."""
+                 precond: int = PRECOND_TREE, precision: int = PREC_F64, iterations: int = 30,
+                 tol: float = 1e-8, maxit: int = 100000) -> dict:
+        """Pick the launch-shape knobs: per candidate, `iterations` PCG
+        iterations, or (iterations=0) a whole solve to `tol` plus the factor
+        build.  Fh is rebuilt in place for each factor-shape candidate."""
         import numpy as np
         _check_vec(F, M.n, name="F")
-        o = SolveOpts(1e-8, iterations, precond, precision, 0, 0, 0.0)
+        o = SolveOpts(tol, maxit if iterations == 0 else iterations, precond, precision, 0, 0, 0.0)
         t = Tuning()
         if offsets is not None:
             off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))

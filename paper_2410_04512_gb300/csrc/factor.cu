@@ -1500,11 +1500,9 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     F->comp_size = local ? B : 0;
     F->local_levels = 0;
     F->ncomp = 0;
-    {
-        if (local) {
-            while ((1 << shift) < B) ++shift;
-            F->ncomp = (int32_t)((n + B - 1) >> shift);
-        }
+    if (local) {
+        while ((1 << shift) < B) ++shift;
+        F->ncomp = (int32_t)((n + B - 1) >> shift);
         SGP_TRY(buf_ensure(ctx, F->pre, sizeof(int32_t) * n1));
         SGP_TRY(buf_ensure(ctx, F->inv_pre, sizeof(int32_t) * n1));
         SGP_TRY(buf_ensure(ctx, F->pinned, sizeof(int32_t) * n1));
@@ -1554,8 +1552,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
                (const int32_t *)nbr, (const int32_t *)twin, (const int32_t *)dist, (const int32_t *)tid,
                (const int32_t *)voff, (const int32_t *)tsize, (const int32_t *)dflag, comp, n, ns, pre, perr);
         LAUNCH(ctx, k_blocks, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
-               (const int32_t *)nbr, (const int32_t *)pre, n, local ? shift : 31, bp<int32_t>(F->inv_pre), pinned,
-               perr);
+               (const int32_t *)nbr, (const int32_t *)pre, n, shift, bp<int32_t>(F->inv_pre), pinned, perr);
         int herr8 = 0;
         SGP_TRY(read_back(ctx, &herr8, perr, sizeof(int)));
         if (herr8) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: the depth-first order is not a permutation");

@@ -20,8 +20,11 @@ struct Run {
     sgp_solve_opts opts;
     cudaEvent_t e0, e1;
 
-    // One untimed solve (graph capture, caches), then one timed solve of
-    // opts.maxit iterations; returns milliseconds per iteration.
+    // One untimed solve (graph capture, caches), then one timed solve;
+    // returns milliseconds per iteration, or per solve when `whole` is set
+    // (the time then includes `extra_ms`, the factor build of the candidate).
+    bool whole = false;
+    double extra_ms = 0.0;
     sgp_status time_it(double *ms_per_it)
     {
         double best = 0.0;
@@ -43,7 +46,7 @@ struct Run {
             SGP_CUDA(ctx, cudaEventSynchronize(e1));
             float ms = 0.f;
             SGP_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
-            best = (double)ms / (double)std::max<int64_t>(its, 1);
+            best = whole ? (double)ms + extra_ms : (double)ms / (double)std::max<int64_t>(its, 1);
         }
         *ms_per_it = best;
         return SGP_OK;
@@ -96,8 +99,8 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
                         const sgp_solve_opts *opts, int32_t iterations, sgp_tuning *out)
 {
     if (!ctx || !M || !opts || !F) return SGP_ERR_INVALID_ARG;
-    if (iterations < 1 || iterations > 100000)
-        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "autotune: iterations must be in [1, 100000]");
+    if (iterations < 0 || iterations > 100000)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "autotune: iterations must be in [0, 100000]");
     const bool tree = opts->precond == SGP_PRECOND_TREE;
     if (tree && (!T || !factor || !*factor))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "autotune: the tree preconditioner needs the tree and a factor");
@@ -112,9 +115,24 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
     SGP_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void **>(&v), sizeof(double) * 3 * n, ctx->stream));
     const sgp_factor *no_factor = nullptr;
     Run run{ctx, M, factor ? factor : &no_factor, n_instances, offsets, F, v, *opts, nullptr, nullptr};
-    run.opts.tol = 1e-300;          // never met: every timed solve runs exactly `iterations`
-    run.opts.maxit = iterations;
+    if (iterations > 0) {
+        run.opts.tol = 1e-300;      // never met: every timed solve runs exactly `iterations`
+        run.opts.maxit = iterations;
+    } else {
+        run.whole = true;           // whole solves to opts->tol, plus the factor build
+    }
     run.opts.x0_given = 0;
+    // factor build timed with events (its host synchronisations included)
+    auto build = [&]() -> sgp_status {
+        SGP_CUDA(ctx, cudaEventRecord(run.e0, ctx->stream));
+        SGP_TRY(sgp_tree_factor(ctx, M, T, factor));
+        SGP_CUDA(ctx, cudaEventRecord(run.e1, ctx->stream));
+        SGP_CUDA(ctx, cudaEventSynchronize(run.e1));
+        float ms = 0.f;
+        SGP_CUDA(ctx, cudaEventElapsedTime(&ms, run.e0, run.e1));
+        run.extra_ms = ms;
+        return SGP_OK;
+    };
     sgp_tuning keep{};
     sgp_get_tuning(ctx, &keep);
     sgp_status st = SGP_OK;
@@ -136,7 +154,7 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
         best_ms = 1e300;
         for (int cs : sizes) {
             ctx->comp_size = cs;
-            if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
+            if ((st = build()) != SGP_OK) return finish(st);
             double ms;
             if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
             if (ms < best_ms) best_ms = ms, best_cs = cs;
@@ -147,7 +165,7 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
         best_ms = 1e300;
         for (int cap : caps) {
             ctx->tail_cap = cap;
-            if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
+            if ((st = build()) != SGP_OK) return finish(st);
             double ms;
             if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
             if (ms < best_ms) best_ms = ms, best_cap = cap;
@@ -158,13 +176,13 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
         best_ms = 1e300;
         for (int cc : coops) {
             ctx->coop_cap = cc;
-            if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
+            if ((st = build()) != SGP_OK) return finish(st);
             double ms;
             if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
             if (ms < best_ms) best_ms = ms, best_coop = cc;
         }
         ctx->coop_cap = best_coop;
-        if ((st = sgp_tree_factor(ctx, M, T, factor)) != SGP_OK) return finish(st);
+        if ((st = build()) != SGP_OK) return finish(st);
     }
     // 2. lanes per block row of the product and rows in flight per lane
     {

@@ -71,6 +71,11 @@ def test_autotune_single_system(ctx):
     # the factor handle was left built with the chosen tail and still solves
     v, info = ctx.pcg_solve(s.M, s.Fac, F, tol=1e-8, precision=sgp.PREC_MIXED)
     assert info.status == 0 and info.true_rel_residual <= 1e-8
+    # whole-step objective (factor build + solve to the tolerance)
+    t2 = ctx.autotune(s.M, s.T, s.Fac, F, precision=sgp.PREC_MIXED, iterations=0, tol=1e-8)
+    assert t2["ms_per_iteration"] > t["ms_per_iteration"]
+    v, info = ctx.pcg_solve(s.M, s.Fac, F, tol=1e-8, precision=sgp.PREC_MIXED)
+    assert info.status == 0 and info.true_rel_residual <= 1e-8
 
 
 def test_autotune_batch(ctx):
