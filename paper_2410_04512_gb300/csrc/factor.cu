@@ -679,7 +679,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // the L blocks in contributor-list order and ctv the contributor vertices,
 // so the level streams both arrays.
 template <typename T>
-__global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 8) k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
                            const int32_t *__restrict__ ctv, const T *__restrict__ Lf, int32_t r0,
                            int32_t cnt, T *w, const int *done)
 {
@@ -691,7 +691,7 @@ __global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__rest
     // Contributor ids and L blocks do not depend on the previous level: load
     // the first FWD_PRE of them before waiting, so that after the wait all
     // their w loads go out together (one memory round trip per level).
-    constexpr int FWD_PRE = 4;
+    constexpr int FWD_PRE = 2;
     T Lr[FWD_PRE][9];
     int32_t cr[FWD_PRE];
 #pragma unroll
@@ -733,7 +733,7 @@ __global__ void k_tree_fwd(const int32_t *__restrict__ rv, const int32_t *__rest
 // Diagonal solve and backward substitution of one level:
 // z_c = D_c^-1 w_c - sum_q L_qc^T z_q, in place.
 template <typename T>
-__global__ void k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__restrict__ pr_ptr,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 8) k_tree_bwd(const int32_t *__restrict__ ord, const int32_t *__restrict__ pr_ptr,
                            const int32_t *__restrict__ pr_q, const T *__restrict__ L,
                            const T *__restrict__ Dinv, int32_t p0, int32_t cnt, T *w, const int *done)
 {

@@ -69,7 +69,7 @@ __global__ void k_spmv(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, 
 // ILP row groups are in flight per lane at once (their slot loads and
 // gathers interleave), which hides the block-load -> gather latency chain.
 template <typename T, int LPR, int ILP>
-__global__ void __launch_bounds__(RB) k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0,
+__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? (ILP == 1 ? 8 : 4) : (ILP == 1 ? 4 : 2)) k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0,
                                                 int64_t n, const T *__restrict__ p, T *q, double *partials,
                                                 Scal *sc)
 {
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(RB) k_update_v(int64_t n, T *x, const T *__res
 
 // rho' = r^T w after the tree solve; beta = rho'/rho.
 template <typename T>
-__global__ void __launch_bounds__(RB) k_rz(int64_t n, const T *__restrict__ r, const T *__restrict__ w,
+__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 4) k_rz(int64_t n, const T *__restrict__ r, const T *__restrict__ w,
                                            double *partials, Scal *sc)
 {
     __shared__ double sh[RB / 32];
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(RB) k_rz(int64_t n, const T *__restrict__ r, c
 
 // p = w + beta p
 template <typename T>
-__global__ void __launch_bounds__(RB) k_pupd(int64_t n, const T *__restrict__ w, T *p, const Scal *sc)
+__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 6 : 4) k_pupd(int64_t n, const T *__restrict__ w, T *p, const Scal *sc)
 {
     if (sc->done) return;
     constexpr int K = Pack<T>::K;
