@@ -311,6 +311,14 @@ typedef struct {
                             default) or 256..16777216; read when a factor is built */
     int32_t spmv_ilp;    /* row groups each lane of the PCG product keeps in flight
                             at once: 0 (default, 1), 1 or 2 */
+    int32_t ctail_cap;   /* the last contraction levels, from the first one with at
+                            most ctail_cap vertices left, run in one cluster of
+                            thread blocks (16 or 8, whatever the device schedules)
+                            that keeps the tail in distributed shared memory; used
+                            when it starts before the one-block tail and fits;
+                            0 (none, default) or 256..16777216; read when a
+                            factor is built */
+    int32_t reserved;
     double ms_per_iteration; /* sgp_autotune: the winning objective (ms per PCG
                                 iteration, or per factor build + solve); 0 from
                                 sgp_get_tuning */
@@ -320,8 +328,9 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *tuning);
 sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *tuning);
 /* Pick the knobs by timing the caller's own system for each candidate, one
  * knob after the other: comp_size in {0, 256, 512, 1024, 2048, 4096},
- * tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} and coop_cap in
- * {0, 8192, 32768, 131072} (tree preconditioner only; *factor is rebuilt
+ * tail_cap in {0, 256, 512, 1024, 2048, 4096, -1}, ctail_cap in
+ * {0, 8192, 16384, 32768} and coop_cap in {0, 8192, 32768, 131072} (tree
+ * preconditioner only; *factor is rebuilt
  * from `tree` for each candidate and left built with the chosen values), then
  * spmv_lpr in {1, 2, 4, 8} with spmv_ilp in {1, 2}, then, when n_instances > 0
  * (a batch with host `offsets`, as for sgp_pcg_solve_batched), batch_chunk in

@@ -46,10 +46,10 @@ class SolveOpts(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("spmv_lpr", ctypes.c_int32), ("tail_cap", ctypes.c_int32), ("batch_chunk", ctypes.c_int32),
                 ("comp_size", ctypes.c_int32), ("coop_cap", ctypes.c_int32), ("spmv_ilp", ctypes.c_int32),
-                ("ms_per_iteration", ctypes.c_double)]
+                ("ctail_cap", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class SolveInfo(ctypes.Structure):
@@ -416,9 +416,9 @@ class Context:
         return t.as_dict()
 
     def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, comp_size: int = 0,
-                   coop_cap: int = 0, spmv_ilp: int = 0):
+                   coop_cap: int = 0, spmv_ilp: int = 0, ctail_cap: int = 0):
         """Set the launch-shape knobs (the defaults are the library's)."""
-        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, coop_cap, spmv_ilp, 0.0)
+        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, coop_cap, spmv_ilp, ctail_cap, 0, 0.0)
         self._ok(_lib.sgp_set_tuning(self.ptr, ctypes.byref(t)))
 
     def autotune(self, M: Matrix, T: Tree | None, Fh: Factor | None, F: torch.Tensor, offsets=None,

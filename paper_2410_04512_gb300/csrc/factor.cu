@@ -1246,6 +1246,202 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
     }
 }
 
+// The tail in one thread-block cluster: tail position i belongs to block
+// i / S of the cluster, which keeps w_i, D_i^-1 and the L blocks of the
+// pairs it eliminates (backward) and of the receiver entries it owns
+// (forward) in its shared memory; values of other blocks are read through
+// distributed shared memory.  Levels are separated by cluster barriers.
+struct CTail {
+    int32_t nlev, n, S, P0, Q0, C0;
+    const int32_t *lvl_pos;  // nlev + 1 absolute positions
+    const int32_t *tb;       // local receiver of each tail pair
+    const int32_t *fo;       // R x (nlev + 1): forward entries of block r by level (block-relative)
+    const int32_t *eoff, *coff;  // R + 1: block offsets into fq/fbeg and fcon/fidx
+    const int32_t *fq, *fbeg;    // per forward entry: receiver slot, first contributor (block-relative)
+    const int32_t *fcon, *fidx;  // per contributor: local position, tail contributor entry
+};
+
+template <typename T>
+__host__ __device__ inline size_t ctail_smem(int32_t S, int32_t nlev, int32_t npair, int32_t ne, int32_t nc)
+{
+    return tail_align(sizeof(T) * 3 * (size_t)S) + tail_align(sizeof(T) * 6 * (size_t)S) +
+           tail_align(sizeof(T) * 9 * (size_t)npair) + tail_align(4 * (size_t)npair) +
+           tail_align(4 * ((size_t)S + 1)) + tail_align(4 * (size_t)ne) + tail_align(4 * ((size_t)ne + 1)) +
+           tail_align(sizeof(T) * 9 * (size_t)nc) + tail_align(4 * (size_t)nc) + tail_align(4 * ((size_t)nlev + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tree_ctail(CTail a, const int32_t *__restrict__ ord,
+                                                     const int32_t *__restrict__ pr_ptr, const T *__restrict__ L,
+                                                     const T *__restrict__ Lf, const T *__restrict__ Dinv, T *w,
+                                                     const int *done)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    if (done && *done) return;   // the same in every block of the cluster
+    const int32_t r = (int32_t)cl.block_rank();
+    const int32_t i0 = r * a.S;
+    const int32_t cnt = max(0, min(a.S, a.n - i0));
+    const int32_t pa = cnt > 0 ? pr_ptr[a.P0 + i0] : 0, pb = cnt > 0 ? pr_ptr[a.P0 + i0 + cnt] : 0;
+    const int32_t np = pb - pa;
+    const int32_t e0 = a.eoff[r], ne = a.eoff[r + 1] - e0, c0 = a.coff[r], nc = a.coff[r + 1] - c0;
+    unsigned char *cur = smem_raw;
+    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
+    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * a.S));
+    T *sD = reinterpret_cast<T *>(take(sizeof(T) * 6 * a.S));
+    T *sLb = reinterpret_cast<T *>(take(sizeof(T) * 9 * np));
+    int32_t *sbq = reinterpret_cast<int32_t *>(take(4 * np));
+    int32_t *spr = reinterpret_cast<int32_t *>(take(4 * (a.S + 1)));
+    int32_t *sq = reinterpret_cast<int32_t *>(take(4 * ne));
+    int32_t *sb = reinterpret_cast<int32_t *>(take(4 * (ne + 1)));
+    T *sLf = reinterpret_cast<T *>(take(sizeof(T) * 9 * nc));
+    int32_t *sc = reinterpret_cast<int32_t *>(take(4 * nc));
+    int32_t *sfo = reinterpret_cast<int32_t *>(take(4 * (a.nlev + 1)));
+    // stage the factor (independent of the previous kernel)
+    for (int32_t k = threadIdx.x; k < 6 * cnt; k += blockDim.x) sD[k] = Dinv[6 * ((int64_t)a.P0 + i0) + k];
+    for (int32_t k = threadIdx.x; k < 9 * np; k += blockDim.x) sLb[k] = L[9 * (int64_t)pa + k];
+    for (int32_t k = threadIdx.x; k < np; k += blockDim.x) sbq[k] = a.tb[pa - a.Q0 + k];
+    for (int32_t k = threadIdx.x; k <= cnt; k += blockDim.x) spr[k] = pr_ptr[a.P0 + i0 + k] - pa;
+    for (int32_t k = threadIdx.x; k < ne; k += blockDim.x) {
+        sq[k] = a.fq[e0 + k];
+        sb[k] = a.fbeg[e0 + k];
+    }
+    if (threadIdx.x == 0) sb[ne] = nc;
+    for (int32_t k = threadIdx.x; k < nc; k += blockDim.x) sc[k] = a.fcon[c0 + k];
+    for (int32_t k = threadIdx.x; k < 9 * nc; k += blockDim.x) {
+        const int32_t j = k / 9, e = k - 9 * j;
+        sLf[k] = Lf[9 * ((int64_t)a.C0 + a.fidx[c0 + j]) + e];
+    }
+    for (int32_t k = threadIdx.x; k <= a.nlev; k += blockDim.x) sfo[k] = a.fo[r * (a.nlev + 1) + k];
+    pdl_wait();
+    for (int32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int64_t v = ord[a.P0 + i0 + k];
+        sw[3 * k] = w[3 * v];
+        sw[3 * k + 1] = w[3 * v + 1];
+        sw[3 * k + 2] = w[3 * v + 2];
+    }
+    cl.sync();
+    auto value = [&](int32_t i) -> const T * {   // w of tail position i, wherever it lives
+        const int32_t o = i / a.S, slot = i - o * a.S;
+        return o == r ? sw + 3 * slot : cl.map_shared_rank(sw, (unsigned)o) + 3 * slot;
+    };
+    for (int l = 0; l < a.nlev; ++l) {
+        const int32_t k1 = sfo[l + 1];
+        for (int32_t k = sfo[l] + threadIdx.x; k < k1; k += blockDim.x) {
+            T s[3] = {0, 0, 0};
+            for (int32_t j = sb[k]; j < sb[k + 1]; ++j) {
+                const T *x = value(sc[j]);
+                T xv[3] = {x[0], x[1], x[2]};
+                T y[3];
+                full_mv(sLf + 9 * j, xv, y);
+                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
+            }
+            const int32_t q = sq[k];
+            sw[3 * q] -= s[0];
+            sw[3 * q + 1] -= s[1];
+            sw[3 * q + 2] -= s[2];
+        }
+        cl.sync();
+    }
+    for (int l = a.nlev - 1; l >= 0; --l) {
+        const int32_t g0 = max(a.lvl_pos[l] - a.P0, i0), g1 = min(a.lvl_pos[l + 1] - a.P0, i0 + cnt);
+        for (int32_t i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
+            const int32_t k = i - i0;
+            T z[3];
+            sym_mv(sD + 6 * k, sw + 3 * k, z);
+            for (int32_t p = spr[k]; p < spr[k + 1]; ++p) {
+                const T *y = value(sbq[p]);
+                T yv[3] = {y[0], y[1], y[2]};
+                T u[3];
+                full_mtv(sLb + 9 * p, yv, u);
+                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
+            }
+            sw[3 * k] = z[0];
+            sw[3 * k + 1] = z[1];
+            sw[3 * k + 2] = z[2];
+        }
+        cl.sync();
+    }
+    for (int32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int64_t v = ord[a.P0 + i0 + k];
+        w[3 * v] = sw[3 * k];
+        w[3 * v + 1] = sw[3 * k + 1];
+        w[3 * v + 2] = sw[3 * k + 2];
+    }
+}
+
+static CTail ctail_of(const sgp_factor *F)
+{
+    CTail t;
+    t.nlev = F->levels - F->tail_level;
+    t.n = (int32_t)(F->n - F->tail_P0);
+    t.S = F->ctail_S;
+    t.P0 = F->tail_P0;
+    t.Q0 = F->tail_Q0;
+    t.C0 = F->tail_C0;
+    t.lvl_pos = bp<const int32_t>(F->tail_idx);
+    t.tb = bp<const int32_t>(F->tail_b);
+    t.fo = bp<const int32_t>(F->ct_fo);
+    t.eoff = bp<const int32_t>(F->ct_eoff);
+    t.coff = bp<const int32_t>(F->ct_coff);
+    t.fq = bp<const int32_t>(F->ct_fq);
+    t.fbeg = bp<const int32_t>(F->ct_fbeg);
+    t.fcon = bp<const int32_t>(F->ct_fcon);
+    t.fidx = bp<const int32_t>(F->ct_fidx);
+    return t;
+}
+
+template <typename T>
+static cudaLaunchConfig_t ctail_config(sgp_ctx *ctx, int R, size_t smem, cudaLaunchAttribute *attr, bool pdl)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(R);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = pdl ? ctx->use_pdl : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cfg;
+}
+
+// Cluster size for the cluster tail on this device: 16 (non-portable) or 8
+// thread blocks of 1024 threads with the full shared-memory budget, whichever
+// the device can schedule; -1 if neither.
+static sgp_status ctail_probe(sgp_ctx *ctx)
+{
+    if (ctx->ctail_R != 0) return SGP_OK;
+    ctx->ctail_R = -1;
+    const int bytes = TREE_TAIL_SMEM;
+    for (auto k : {(const void *)k_tree_ctail<float>, (const void *)k_tree_ctail<double>}) {
+        SGP_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        SGP_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
+    for (int R : {16, 8}) {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = ctail_config<float>(ctx, R, bytes, attr, false);
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, k_tree_ctail<float>, &cfg);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (ncl >= 1) {
+            ctx->ctail_R = R;
+            break;
+        }
+    }
+    return SGP_OK;
+}
+
 static Tail tail_of(const sgp_factor *F)
 {
     Tail t;
@@ -1283,8 +1479,12 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
     // MIXED factor whose tail does not fit runs every level as its own kernel
     int lt = F->tail_level;
     if (lt < F->levels) {
-        const Tail tl = tail_of(F);
-        if (tail_smem_bytes<T>(tl.n, tl.np, tl.nr) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
+        if (F->ctail) {
+            if ((f64 ? F->ctail_smem64 : F->ctail_smem32) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
+        } else {
+            const Tail tl = tail_of(F);
+            if (tail_smem_bytes<T>(tl.n, tl.np, tl.nr) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
+        }
     }
     const int L1 = F->local_levels;
     Local la{L1, F->ncomp, 0, (int32_t)F->n, bp<const int32_t>(F->inv_pre), bp<const int32_t>(F->roff),
@@ -1317,7 +1517,17 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
     }
     if (lc < lt)
         SGP_TRY((launch_coop<T, true>(ctx, F, lt - lc, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done)));
-    if (lt < F->levels) {
+    if (lt < F->levels && F->ctail) {
+        const CTail ctl = ctail_of(F);
+        cudaLaunchAttribute attr[2];
+        const size_t sm = f64 ? F->ctail_smem64 : F->ctail_smem32;
+        cudaLaunchConfig_t cfg = ctail_config<T>(ctx, F->ctail_R, sm, attr, true);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_tree_ctail<T>, ctl, ord, prp, L, Lf, Dinv, w, done);
+        ctx->launches++;
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return sgp_fail(ctx, SGP_ERR_CUDA, "launch of k_tree_ctail failed: %s", cudaGetErrorString(e));
+    } else if (lt < F->levels) {
         const Tail tl = tail_of(F);
         const size_t staged = tail_smem_staged<T>(tl.n, tl.np, tl.nr);
         if (staged <= (size_t)TREE_TAIL_SMEM)
@@ -1756,6 +1966,122 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
                               (ctx->tail_cap >= 0 && n - F->lvl_ptr[lt] > ctx->tail_cap)))
         ++lt;
     F->tail_level = lt;
+    // the tail's local index lists for levels >= t
+    auto build_tail = [&](int t) -> sgp_status {
+        SGP_TRY(tail_smem_optin(ctx));
+        const int nl = F->levels - t;
+        F->tail_P0 = F->lvl_ptr[t];
+        F->tail_R0 = F->rl_ptr[t];
+        F->tail_C0 = F->cl_ptr[t];
+        F->tail_Q0 = F->pl_ptr[t];
+        std::vector<int32_t> idx(2 * (nl + 1));
+        for (int l = 0; l <= nl; ++l) {
+            idx[l] = F->lvl_ptr[t + l];
+            idx[nl + 1 + l] = F->rl_ptr[t + l];
+        }
+        SGP_TRY(buf_ensure(ctx, F->tail_idx, sizeof(int32_t) * idx.size()));
+        SGP_CUDA(ctx, cudaMemcpyAsync(F->tail_idx.p, idx.data(), sizeof(int32_t) * idx.size(),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+        // every pair of the tail is one contributor entry of the tail
+        const int32_t nq = nrecv - F->tail_R0, nc = ncontrib - F->tail_C0, nb = npair - F->tail_Q0;
+        if (nc != nb) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent tail (%d/%d)", nc, nb);
+        SGP_TRY(buf_ensure(ctx, F->tail_q, sizeof(int32_t) * std::max(nq, 1)));
+        SGP_TRY(buf_ensure(ctx, F->tail_c, sizeof(int32_t) * 2 * std::max(nb, 1)));
+        SGP_TRY(buf_ensure(ctx, F->tail_b, sizeof(int32_t) * std::max(nb, 1)));
+        LAUNCH(ctx, k_tail_index, grid_for(nq, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv,
+               (const int32_t *)pos, F->tail_R0, nq, F->tail_P0, bp<int32_t>(F->tail_q));
+        LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_q,
+               (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_b));
+        LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_c,
+               (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_c));
+        LAUNCH(ctx, k_tail_pairs, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ct, F->tail_C0,
+               nb, F->tail_Q0, bp<int32_t>(F->tail_c) + nb);
+        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
+        return SGP_OK;
+    };
+    // the cluster tail: blocks own consecutive tail positions; each block's
+    // forward entries are grouped by level on the host from the tail lists
+    auto build_ctail = [&](int t, bool *fits) -> sgp_status {
+        *fits = false;
+        SGP_TRY(build_tail(t));
+        const int R = ctx->ctail_R, nl = F->levels - t;
+        const int32_t tn = (int32_t)(n - F->tail_P0), nq = nrecv - F->tail_R0, nb = npair - F->tail_Q0;
+        const int32_t S = (tn + R - 1) / R;
+        std::vector<int32_t> tq(std::max(nq, 1)), tcl(2 * std::max(nb, 1)), rcr(nq + 1), prr(tn + 1);
+        SGP_TRY(read_back(ctx, tq.data(), F->tail_q.p, sizeof(int32_t) * nq));
+        SGP_TRY(read_back(ctx, tcl.data(), F->tail_c.p, sizeof(int32_t) * 2 * nb));
+        SGP_TRY(read_back(ctx, rcr.data(), rc_ptr + F->tail_R0, sizeof(int32_t) * (nq + 1)));
+        SGP_TRY(read_back(ctx, prr.data(), pr_ptr + F->tail_P0, sizeof(int32_t) * (tn + 1)));
+        const int32_t *tpc = tcl.data(), *tct = tcl.data() + nb;
+        std::vector<int32_t> fo((size_t)R * (nl + 1)), eoff(R + 1, 0), coff(R + 1, 0), fq, fbeg, fcon, fidx;
+        size_t m32 = 0, m64 = 0;
+        for (int r = 0; r < R; ++r) {
+            eoff[r] = (int32_t)fq.size();
+            coff[r] = (int32_t)fcon.size();
+            for (int l = 0; l < nl; ++l) {
+                fo[(size_t)r * (nl + 1) + l] = (int32_t)fq.size() - eoff[r];
+                for (int32_t k = F->rl_ptr[t + l] - F->tail_R0; k < F->rl_ptr[t + l + 1] - F->tail_R0; ++k) {
+                    if (tq[k] / S != r) continue;
+                    fq.push_back(tq[k] - r * S);
+                    fbeg.push_back((int32_t)fcon.size() - coff[r]);
+                    for (int32_t j = rcr[k] - F->tail_C0; j < rcr[k + 1] - F->tail_C0; ++j) {
+                        fcon.push_back(tpc[tct[j]]);
+                        fidx.push_back(j);
+                    }
+                }
+            }
+            fo[(size_t)r * (nl + 1) + nl] = (int32_t)fq.size() - eoff[r];
+            const int32_t i0 = std::min(r * S, tn), i1 = std::min(i0 + S, tn);
+            const int32_t npr = prr[i1] - prr[i0];
+            const int32_t ner = (int32_t)fq.size() - eoff[r], ncr = (int32_t)fcon.size() - coff[r];
+            m32 = std::max(m32, ctail_smem<float>(S, nl, npr, ner, ncr));
+            m64 = std::max(m64, ctail_smem<double>(S, nl, npr, ner, ncr));
+        }
+        eoff[R] = (int32_t)fq.size();
+        coff[R] = (int32_t)fcon.size();
+        const size_t need = F->precision == SGP_PREC_MIXED ? m32 : m64;
+        if (need > (size_t)TREE_TAIL_SMEM) return SGP_OK;
+        auto up = [&](DBuf &b, const std::vector<int32_t> &v) -> sgp_status {
+            SGP_TRY(buf_ensure(ctx, b, sizeof(int32_t) * std::max<size_t>(v.size(), 1)));
+            if (!v.empty())
+                SGP_CUDA(ctx, cudaMemcpyAsync(b.p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice,
+                                              ctx->stream));
+            return SGP_OK;
+        };
+        SGP_TRY(up(F->ct_fo, fo));
+        SGP_TRY(up(F->ct_eoff, eoff));
+        SGP_TRY(up(F->ct_coff, coff));
+        SGP_TRY(up(F->ct_fq, fq));
+        SGP_TRY(up(F->ct_fbeg, fbeg));
+        SGP_TRY(up(F->ct_fcon, fcon));
+        SGP_TRY(up(F->ct_fidx, fidx));
+        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the vectors live on the host stack
+        F->ctail_R = R;
+        F->ctail_S = S;
+        F->ctail_smem32 = m32;
+        F->ctail_smem64 = m64;
+        *fits = true;
+        return SGP_OK;
+    };
+    F->ctail = 0;
+    if (ctx->ctail_cap > 0) {
+        SGP_TRY(ctail_probe(ctx));
+        if (ctx->ctail_R > 0) {
+            int t = L1;
+            while (t < F->levels && n - F->lvl_ptr[t] > ctx->ctail_cap) ++t;
+            for (; t < lt; ++t) {   // a cluster tail only pays when it starts before the one-block tail
+                bool fits = false;
+                SGP_TRY(build_ctail(t, &fits));
+                if (fits) {
+                    F->ctail = 1;
+                    lt = t;
+                    F->tail_level = lt;
+                    break;
+                }
+            }
+        }
+    }
+    if (!F->ctail && lt < F->levels) SGP_TRY(build_tail(lt));
     // the cooperative middle: from the first level with at most coop_cap
     // vertices left up to the tail
     {
@@ -1779,37 +2105,6 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
                                           cudaMemcpyHostToDevice, ctx->stream));
             SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
         }
-    }
-    if (lt < F->levels) {
-        SGP_TRY(tail_smem_optin(ctx));
-        const int nl = F->levels - lt;
-        F->tail_P0 = F->lvl_ptr[lt];
-        F->tail_R0 = F->rl_ptr[lt];
-        F->tail_C0 = F->cl_ptr[lt];
-        F->tail_Q0 = F->pl_ptr[lt];
-        std::vector<int32_t> idx(2 * (nl + 1));
-        for (int l = 0; l <= nl; ++l) {
-            idx[l] = F->lvl_ptr[lt + l];
-            idx[nl + 1 + l] = F->rl_ptr[lt + l];
-        }
-        SGP_TRY(buf_ensure(ctx, F->tail_idx, sizeof(int32_t) * idx.size()));
-        SGP_CUDA(ctx, cudaMemcpyAsync(F->tail_idx.p, idx.data(), sizeof(int32_t) * idx.size(),
-                                      cudaMemcpyHostToDevice, ctx->stream));
-        // every pair of the tail is one contributor entry of the tail
-        const int32_t nq = nrecv - F->tail_R0, nc = ncontrib - F->tail_C0, nb = npair - F->tail_Q0;
-        if (nc != nb) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent tail (%d/%d)", nc, nb);
-        SGP_TRY(buf_ensure(ctx, F->tail_q, sizeof(int32_t) * std::max(nq, 1)));
-        SGP_TRY(buf_ensure(ctx, F->tail_c, sizeof(int32_t) * 2 * std::max(nb, 1)));
-        SGP_TRY(buf_ensure(ctx, F->tail_b, sizeof(int32_t) * std::max(nb, 1)));
-        LAUNCH(ctx, k_tail_index, grid_for(nq, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv,
-               (const int32_t *)pos, F->tail_R0, nq, F->tail_P0, bp<int32_t>(F->tail_q));
-        LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_q,
-               (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_b));
-        LAUNCH(ctx, k_tail_index, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_c,
-               (const int32_t *)pos, F->tail_Q0, nb, F->tail_P0, bp<int32_t>(F->tail_c));
-        LAUNCH(ctx, k_tail_pairs, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ct, F->tail_C0,
-               nb, F->tail_Q0, bp<int32_t>(F->tail_c) + nb);
-        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
     }
     int herr = 0;
     SGP_TRY(read_back(ctx, &herr, err, sizeof(int)));
@@ -1852,7 +2147,8 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->et_dist2, &F->et_tid, &F->et_size, &F->et_flag, &F->pinned, &F->bm_tab,
                     &F->bm_tot, &F->bm_base, &F->bm_max, &F->bm_q, &F->bm_beg, &F->bm_cloc, &F->bm_oloc,
                     &F->bm_pbeg, &F->bm_qloc, &F->bm_Lf, &F->bm_Lf32, &F->bm_Lb, &F->bm_Lb32, &F->bm_D,
-                    &F->bm_D32, &F->coop_idx};
+                    &F->bm_D32, &F->coop_idx, &F->ct_fo, &F->ct_eoff, &F->ct_coff, &F->ct_fq,
+                    &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete F;

@@ -65,6 +65,8 @@ struct sgp_ctx {
     int tail_cap = 1024;    // largest tail of the tree solve in vertices (-1: what fits)
     int comp_size = 0;      // block of the local phase of the tree factor (0: none)
     int coop_cap = 0;       // vertices left when one cooperative kernel takes over the levels (0: none)
+    int ctail_cap = 0;      // vertices left when the thread-block-cluster tail takes over (0: none)
+    int ctail_R = 0;        // cluster size of that tail on this device (0: not probed, -1: none)
     int use_pdl = 1;        // programmatic dependent launch of the level kernels
     int batch_chunk = 0;    // rows per work item of the batched solver
     int num_sms = 0;
@@ -222,6 +224,11 @@ struct sgp_factor {
     DBuf Lf, Lf32;  // L blocks in ct order (forward pass streams them)
     // tail: levels >= tail_level run in one thread block (positions >= tail_P0)
     int32_t tail_level = 0, tail_P0 = 0, tail_R0 = 0, tail_C0 = 0, tail_Q0 = 0;
+    // cluster tail: levels >= tail_level in one cluster of ctail_R thread
+    // blocks; position i of the tail belongs to block i / ctail_S
+    int32_t ctail = 0, ctail_R = 0, ctail_S = 0, ctail_ne = 0, ctail_nc = 0;
+    size_t ctail_smem32 = 0, ctail_smem64 = 0;
+    DBuf ct_fo, ct_eoff, ct_coff, ct_fq, ct_fbeg, ct_fcon, ct_fidx;
     // levels [coop_level, tail_level) run in one cooperative kernel per direction
     int32_t coop_level = 0;
     DBuf coop_idx;  // (nlev + 1) positions, then (nlev + 1) receiver offsets

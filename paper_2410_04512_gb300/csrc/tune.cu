@@ -66,6 +66,8 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *t)
     t->comp_size = ctx->comp_size;
     t->coop_cap = ctx->coop_cap;
     t->spmv_ilp = ctx->spmv_ilp;
+    t->ctail_cap = ctx->ctail_cap;
+    t->reserved = 0;
     t->ms_per_iteration = 0.0;
     return SGP_OK;
 }
@@ -76,6 +78,8 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     if (!(t->spmv_lpr == 0 || t->spmv_lpr == 1 || t->spmv_lpr == 2 || t->spmv_lpr == 4 || t->spmv_lpr == 8))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_lpr must be 0, 1, 2, 4 or 8");
     if (t->tail_cap < -1) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: tail_cap must be >= -1");
+    if (t->ctail_cap != 0 && (t->ctail_cap < 256 || t->ctail_cap > (1 << 24)))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: ctail_cap must be 0 or in [256, 16777216]");
     if (t->spmv_ilp < 0 || t->spmv_ilp > 2)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_ilp must be 0, 1 or 2");
     if (t->coop_cap != 0 && (t->coop_cap < 256 || t->coop_cap > (1 << 24)))
@@ -90,6 +94,7 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     ctx->comp_size = t->comp_size;
     ctx->coop_cap = t->coop_cap;
     ctx->spmv_ilp = t->spmv_ilp;
+    ctx->ctail_cap = t->ctail_cap;
     ctx->batch_chunk = t->batch_chunk;
     return SGP_OK;
 }
@@ -171,6 +176,17 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
             if (ms < best_ms) best_ms = ms, best_cap = cap;
         }
         ctx->tail_cap = best_cap;
+        const int ctails[] = {0, 8192, 16384, 32768};
+        int best_ct = ctx->ctail_cap;
+        best_ms = 1e300;
+        for (int cc : ctails) {
+            ctx->ctail_cap = cc;
+            if ((st = build()) != SGP_OK) return finish(st);
+            double ms;
+            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
+            if (ms < best_ms) best_ms = ms, best_ct = cc;
+        }
+        ctx->ctail_cap = best_ct;
         const int coops[] = {0, 8192, 32768, 131072};
         int best_coop = ctx->coop_cap;
         best_ms = 1e300;

@@ -20,20 +20,23 @@ def ctx(cuda_device):
 def test_set_tuning_validates(ctx):
     for bad in (dict(spmv_lpr=3), dict(tail_cap=-2), dict(batch_chunk=100), dict(batch_chunk=70000),
                 dict(comp_size=1000), dict(comp_size=32), dict(comp_size=16384), dict(coop_cap=100),
-                dict(coop_cap=1 << 25), dict(spmv_ilp=3)):
+                dict(coop_cap=1 << 25), dict(spmv_ilp=3), dict(ctail_cap=100)):
         with pytest.raises(sgp.SgpError):
             ctx.set_tuning(**bad)
-    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096, spmv_ilp=2)
+    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096, spmv_ilp=2,
+                   ctail_cap=8192)
     assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "comp_size": 256,
-                                "coop_cap": 4096, "spmv_ilp": 2, "ms_per_iteration": 0.0}
+                                "coop_cap": 4096, "spmv_ilp": 2, "ctail_cap": 8192, "ms_per_iteration": 0.0}
 
 
-@pytest.mark.parametrize("cap,cs,coop", [(0, 0, 0), (64, 1024, 0), (256, 64, 2048), (-1, 256, 0), (1024, 8192, 0),
-                                         (0, 4096, 0), (1024, 0, 8192), (0, 0, 20000), (256, 1024, 4096)])
+@pytest.mark.parametrize("cap,cs,coop,ct", [(0, 0, 0, 0), (64, 1024, 0, 0), (256, 64, 2048, 0), (-1, 256, 0, 0),
+                                            (1024, 8192, 0, 0), (0, 4096, 0, 0), (1024, 0, 8192, 0),
+                                            (0, 0, 20000, 0), (256, 1024, 4096, 0), (1024, 0, 0, 8192),
+                                            (256, 0, 0, 20000), (1024, 0, 16384, 4096), (256, 1024, 0, 16384)])
 @pytest.mark.parametrize("prec", [sgp.PREC_F64, sgp.PREC_MIXED])
-def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, coop, prec):
+def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, coop, ct, prec):
     c = workloads.ball(n=20000, seed=2002, gamma0=1e-3)
-    ctx.set_tuning(tail_cap=cap, comp_size=cs, coop_cap=coop)
+    ctx.set_tuning(tail_cap=cap, comp_size=cs, coop_cap=coop, ctail_cap=ct)
     s = GpuSystem(ctx, c, precision=prec)
     F = c.forces()
     v, info = ctx.pcg_solve(s.M, s.Fac, dev_tensor(F), tol=1e-10, precision=prec)
@@ -65,6 +68,7 @@ def test_autotune_single_system(ctx):
     assert t["tail_cap"] in (0, 256, 512, 1024, 2048, 4096, -1)
     assert t["comp_size"] in (0, 256, 512, 1024, 2048, 4096)
     assert t["coop_cap"] in (0, 8192, 32768, 131072)
+    assert t["ctail_cap"] in (0, 8192, 16384, 32768)
     assert t["spmv_lpr"] in (1, 2, 4, 8) and t["spmv_ilp"] in (1, 2)
     assert t["ms_per_iteration"] > 0
     assert ctx.get_tuning()["tail_cap"] == t["tail_cap"]
