@@ -67,7 +67,7 @@ typedef struct {
     int32_t precision;   /* sgp_precision; MIXED needs a matrix assembled with MIXED */
     int32_t x0_given;    /* 0: start from v = 0; 1: v holds the initial guess on entry */
     int32_t max_outer;   /* MIXED: refinement steps cap (<= 0 means 30) */
-    double inner_tol;    /* MIXED: relative residual target of each FP32 inner solve (<= 0: 1e-4) */
+    double inner_tol;    /* MIXED: relative residual target of each FP32 inner solve (<= 0: 1e-3) */
 } sgp_solve_opts;
 
 typedef struct {

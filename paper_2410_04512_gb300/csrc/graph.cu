@@ -82,6 +82,7 @@ struct Grid {
     double inv_h;
     int dim[3];
     int32_t base;   // first cell of this grid in the cell array
+    float delta;    // bound on the FP32 distance error of the candidate filter
 };
 
 __global__ void k_inst_of(const int64_t *__restrict__ off, int32_t *inst)
@@ -114,7 +115,7 @@ __global__ void k_cell_id(const double *__restrict__ pos, int64_t n, const Grid 
 // deterministic; nothing downstream depends on it (rows are sorted).
 __global__ void k_scatter(const double *__restrict__ pos, const double *__restrict__ radii, int64_t n,
                           const int32_t *__restrict__ cell_id, const int32_t *__restrict__ cell_start,
-                          int32_t *cursor, int32_t *perm, double4_32a *spos)
+                          int32_t *cursor, int32_t *perm, double4_32a *spos, float4 *spos32)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -122,6 +123,7 @@ __global__ void k_scatter(const double *__restrict__ pos, const double *__restri
     int32_t s = cell_start[c] + atomicAdd(cursor + c, 1);
     perm[s] = (int32_t)i;
     spos[s] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], radii[i]);
+    spos32[s] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], (float)radii[i]);
 }
 
 // The contact predicate, with explicit round-to-nearest operations in the
@@ -143,13 +145,14 @@ __device__ __forceinline__ bool contact(double4_32a pi, double4_32a pj)
 template <bool EMIT>
 __global__ void k_contacts(int64_t n, const Grid *__restrict__ grids, const int32_t *__restrict__ inst,
                            const int32_t *__restrict__ perm, const double4_32a *__restrict__ spos,
-                           const int32_t *__restrict__ cell_start, int32_t *cnt,
-                           const int32_t *__restrict__ up_ptr, int32_t *ij)
+                           const float4 *__restrict__ spos32, const int32_t *__restrict__ cell_start,
+                           int32_t *cnt, const int32_t *__restrict__ up_ptr, int32_t *ij)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int32_t i = perm[t];
     const double4_32a pi = spos[t];
+    const float4 fi = spos32[t];
     const Grid g = grids[inst ? inst[i] : 0];
     int cx = cell_coord(pi.x, g.lo[0], g.inv_h, g.dim[0]);
     int cy = cell_coord(pi.y, g.lo[1], g.inv_h, g.dim[1]);
@@ -163,6 +166,13 @@ __global__ void k_contacts(int64_t n, const Grid *__restrict__ grids, const int3
             // grid cells (ax, ay, z0..z1) are contiguous in grid-cell order
             int32_t s0 = cell_start[row + z0], s1 = cell_start[row + z1 + 1];
             for (int32_t s = s0; s < s1; ++s) {
+                // FP32 filter: a pair farther apart than R_i + R_j + delta in
+                // FP32 cannot be in contact (delta bounds the FP32 error);
+                // every pair that passes is decided by the exact FP64 test
+                const float4 fj = spos32[s];
+                const float dx = fj.x - fi.x, dy = fj.y - fi.y, dz = fj.z - fi.z;
+                const float lim = fi.w + fj.w + g.delta;
+                if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
                 int32_t j = perm[s];
                 if (j <= i) continue;
                 if (contact(pi, spos[s])) {
@@ -214,6 +224,13 @@ Grid make_grid(const double *hb, int64_t n_s, int64_t base)
     g.inv_h = 1.0 / h;
     for (int a = 0; a < 3; ++a) g.dim[a] = (int)(std::floor(ext[a] / h) + 1.0);
     g.base = (int32_t)base;
+    // |x_f - x| <= X 2^-24 per coordinate (X the largest coordinate
+    // magnitude), so an FP32 difference is within 3 X 2^-24 of the exact one
+    // and the FP32 distance within sqrt(3) of that plus a few roundings of
+    // the distance and of R_i + R_j: 16 (X + 2 max R) 2^-24 covers all
+    double X = 0.0;
+    for (int a = 0; a < 3; ++a) X = std::max(X, std::max(std::fabs(hb[a]), std::fabs(hb[3 + a])));
+    g.delta = (float)(16.0 * (X + 2.0 * hb[6]) * std::ldexp(1.0, -24));
     return g;
 }
 
@@ -285,10 +302,12 @@ static sgp_status collision_graph(sgp_ctx *ctx, int64_t n, int64_t n_inst, const
     SGP_TRY(buf_ensure(ctx, G->cell_start, sizeof(int32_t) * (ncell + 1)));
     SGP_TRY(buf_ensure(ctx, G->perm, sizeof(int32_t) * n));
     SGP_TRY(buf_ensure(ctx, G->spos, sizeof(double4_32a) * n));
+    SGP_TRY(buf_ensure(ctx, G->spos32, sizeof(float4) * n));
     SGP_TRY(buf_ensure(ctx, G->cnt, sizeof(int32_t) * (n + 1)));
     int32_t *cell_id = bp<int32_t>(G->cell_id), *cell_cnt = bp<int32_t>(G->cell_cnt);
     int32_t *cell_start = bp<int32_t>(G->cell_start), *perm = bp<int32_t>(G->perm);
     double4_32a *spos = bp<double4_32a>(G->spos);
+    float4 *spos32 = bp<float4>(G->spos32);
     int32_t *cnt = bp<int32_t>(G->cnt), *up = bp<int32_t>(G->up_ptr);
     SGP_CUDA(ctx, cudaMemsetAsync(cell_cnt, 0, sizeof(int32_t) * (ncell + 1), ctx->stream));
     LAUNCH(ctx, k_cell_id, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, pos, n, dgrids, (const int32_t *)inst, cell_id,
@@ -296,10 +315,10 @@ static sgp_status collision_graph(sgp_ctx *ctx, int64_t n, int64_t n_inst, const
     SGP_TRY(scan_exclusive_i32(ctx, cell_cnt, cell_start, ncell));
     SGP_CUDA(ctx, cudaMemsetAsync(cell_cnt, 0, sizeof(int32_t) * (ncell + 1), ctx->stream));
     LAUNCH(ctx, k_scatter, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, pos, radii, n,
-           (const int32_t *)cell_id, (const int32_t *)cell_start, cell_cnt, perm, spos);
+           (const int32_t *)cell_id, (const int32_t *)cell_start, cell_cnt, perm, spos, spos32);
     LAUNCH(ctx, k_contacts<false>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
-           (const int32_t *)perm, (const double4_32a *)spos, (const int32_t *)cell_start, cnt,
-           (const int32_t *)nullptr, (int32_t *)nullptr);
+           (const int32_t *)perm, (const double4_32a *)spos, (const float4 *)spos32, (const int32_t *)cell_start,
+           cnt, (const int32_t *)nullptr, (int32_t *)nullptr);
     SGP_TRY(scan_exclusive_i32(ctx, cnt, up, n));
     int32_t m32 = 0;
     SGP_TRY(read_back(ctx, &m32, up + n, sizeof(int32_t)));
@@ -307,8 +326,8 @@ static sgp_status collision_graph(sgp_ctx *ctx, int64_t n, int64_t n_inst, const
     G->m = m32;
     SGP_TRY(buf_ensure(ctx, G->ij, sizeof(int32_t) * 2 * (size_t)G->m));
     LAUNCH(ctx, k_contacts<true>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
-           (const int32_t *)perm, (const double4_32a *)spos, (const int32_t *)cell_start, cnt,
-           (const int32_t *)up, bp<int32_t>(G->ij));
+           (const int32_t *)perm, (const double4_32a *)spos, (const float4 *)spos32, (const int32_t *)cell_start,
+           cnt, (const int32_t *)up, bp<int32_t>(G->ij));
     return SGP_OK;
 }
 
@@ -355,7 +374,7 @@ void sgp_graph_destroy(sgp_graph *G)
     if (!G) return;
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&G->ij, &G->up_ptr, &G->cell_id, &G->cell_cnt, &G->cell_start, &G->perm,
-                    &G->spos, &G->cnt, &G->bbox, &G->inst, &G->grids};
+                    &G->spos, &G->spos32, &G->cnt, &G->bbox, &G->inst, &G->grids};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete G;

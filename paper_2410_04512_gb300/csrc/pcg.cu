@@ -734,7 +734,7 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         float *w32 = reinterpret_cast<float *>(take(v32));
         float *d32 = reinterpret_cast<float *>(take(v32));
         const int max_outer = opts->max_outer > 0 ? opts->max_outer : 30;
-        const double itol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+        const double itol = opts->inner_tol > 0 ? opts->inner_tol : 1e-3;
         if (!opts->x0_given) SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
         int64_t total = 0;
         int outer = 0;

@@ -173,7 +173,7 @@ struct sgp_graph {
     DBuf ij;       // m x 2 int32, canonical (i < j), sorted
     DBuf up_ptr;   // n + 1 int32: edges of row i are [up_ptr[i], up_ptr[i+1])
     // cell-list scratch kept for reuse
-    DBuf cell_id, cell_cnt, cell_start, perm, spos, cnt, bbox, inst, grids;
+    DBuf cell_id, cell_cnt, cell_start, perm, spos, spos32, cnt, bbox, inst, grids;
 };
 
 struct sgp_matrix {
