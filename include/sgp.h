@@ -129,7 +129,11 @@ void sgp_graph_destroy(sgp_graph *graph);
  * directions) in FP64, plus FP32 copies when precision is MIXED, and the
  * spanning-tree weight of Section 3.1, min(g_par, g_perp) = lambda_min
  * (Lemma 2.1).  gamma0 > 0.  DEGENERATE if two cells in contact coincide.
- * pos_dev must be the positions the graph was built from. */
+ * pos_dev must be the positions the graph was built from.  The rows are kept
+ * in the graph's internal cell order (the cells sorted by uniform-grid cell,
+ * by index inside a cell), so that cells close in space are close in memory;
+ * every call below takes and returns cell vectors in the caller's order and
+ * permutes them on the device. */
 sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *graph, const double *pos_dev,
                                  const double *gamma_par_dev, const double *gamma_perp_dev,
                                  double gamma0, int32_t precision, sgp_matrix **matrix);
@@ -222,7 +226,9 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_facto
  * opts as for sgp_pcg_solve (maxit per instance).  infos (host, n_instances
  * entries, may be NULL) receives each instance's statistics.  Returns the
  * first failing status (NOT_SPD before NO_CONVERGENCE); INVALID_ARG if an
- * edge joins two instances.  Synchronises. */
+ * edge joins two instances or if the matrix's internal cell order mixes
+ * instances (a matrix built on a graph from sgp_collision_graph over the
+ * whole union instead of sgp_collision_graph_batched).  Synchronises. */
 sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_factor *factor,
                                  int64_t n_instances, const int64_t *offsets, const double *F_dev,
                                  double *v_dev, const sgp_solve_opts *opts, sgp_solve_info *infos);

@@ -8,65 +8,50 @@
 // with explicit round-to-nearest FP64 operations.  The matrix stores, per
 // directed slot of each block row, the column and the symmetric block
 // (Gamma_ij = -Upsilon_e); the diagonal is never assembled -- products use the
-// difference form of Appendix B.2.  Columns are ascending within a row.
+// difference form of Appendix B.2.  Rows and columns follow the solvers'
+// internal cell order (the collision graph's grid-cell order); columns are
+// ascending within a row.
 #include "sgp_internal.cuh"
 
 namespace {
 
-__global__ void k_low_count(const int32_t *__restrict__ ij, int64_t m, int32_t *lowcnt)
-{
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < m) atomicAdd(lowcnt + ij[2 * e + 1], 1);
-}
-
-__global__ void k_row_len(const int32_t *__restrict__ up_ptr, const int32_t *__restrict__ lowcnt,
-                          int64_t n, int32_t *len)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) len[i] = (up_ptr[i + 1] - up_ptr[i]) + lowcnt[i];
-}
-
-// Upper slots (j > i) are placed in edge order after the row's lower slots;
-// also validates the coefficients and computes the tree weight.
-__global__ void k_place_upper(const int32_t *__restrict__ ij, int64_t m,
-                              const int32_t *__restrict__ up_ptr, const int32_t *__restrict__ lowcnt,
-                              const int32_t *__restrict__ row_ptr, const double *__restrict__ gpar,
-                              const double *__restrict__ gperp, int32_t *col, int32_t *slot_edge,
-                              int32_t *edge_slot, double *w, int *err)
+// Rows and columns in the solvers' internal cell order (int_of): every edge
+// gives a slot in both of its rows.
+__global__ void k_slot_count(const int32_t *__restrict__ ij, int64_t m, const int32_t *__restrict__ int_of,
+                             int32_t *cnt)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= m) return;
-    int32_t i = ij[2 * e], j = ij[2 * e + 1];
-    int32_t s = row_ptr[i] + lowcnt[i] + (int32_t)(e - up_ptr[i]);
-    col[s] = j;
-    slot_edge[s] = (int32_t)e;
-    edge_slot[e] = s;
-    double a = gpar[e], b = gperp[e];
-    if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b)) atomicOr(err, 1);
-    w[e] = a < b ? a : b;  // lambda_min of the block (Lemma 2.1)
+    atomicAdd(cnt + int_of[ij[2 * e]], 1);
+    atomicAdd(cnt + int_of[ij[2 * e + 1]], 1);
 }
 
-__global__ void k_place_lower(const int32_t *__restrict__ ij, int64_t m,
-                              const int32_t *__restrict__ row_ptr, int32_t *cursor, int32_t *col,
-                              int32_t *slot_edge)
+__global__ void k_slot_place(const int32_t *__restrict__ ij, int64_t m, const int32_t *__restrict__ int_of,
+                             const int32_t *__restrict__ row_ptr, int32_t *cursor, int32_t *col,
+                             int32_t *slot_edge)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= m) return;
-    int32_t i = ij[2 * e], j = ij[2 * e + 1];
-    int32_t s = row_ptr[j] + atomicAdd(cursor + j, 1);
-    col[s] = i;
-    slot_edge[s] = (int32_t)e;
+    const int32_t a = int_of[ij[2 * e]], b = int_of[ij[2 * e + 1]];
+    const int32_t sa = row_ptr[a] + atomicAdd(cursor + a, 1);
+    const int32_t sb = row_ptr[b] + atomicAdd(cursor + b, 1);
+    col[sa] = b;
+    slot_edge[sa] = (int32_t)e;
+    col[sb] = a;
+    slot_edge[sb] = (int32_t)e;
 }
 
-// Sort the lower part of each row by column (makes the layout deterministic).
-__global__ void k_sort_lower(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ lowcnt,
-                             int64_t n, int32_t *col, int32_t *slot_edge)
+// Sort each row by column (makes the layout deterministic) and record, for
+// every edge (i, j), its slot in row int_of[i].
+__global__ void k_sort_rows(const int32_t *__restrict__ row_ptr, int64_t n, const int32_t *__restrict__ ij,
+                            const int32_t *__restrict__ int_of, int32_t *col, int32_t *slot_edge,
+                            int32_t *edge_slot)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t b0 = row_ptr[i], k = lowcnt[i];
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int32_t b0 = row_ptr[r], k = row_ptr[r + 1] - b0;
     for (int32_t a = 1; a < k; ++a) {
-        int32_t c = col[b0 + a], se = slot_edge[b0 + a];
+        const int32_t c = col[b0 + a], se = slot_edge[b0 + a];
         int32_t b = a - 1;
         while (b >= 0 && col[b0 + b] > c) {
             col[b0 + b + 1] = col[b0 + b];
@@ -76,6 +61,21 @@ __global__ void k_sort_lower(const int32_t *__restrict__ row_ptr, const int32_t 
         col[b0 + b + 1] = c;
         slot_edge[b0 + b + 1] = se;
     }
+    for (int32_t a = 0; a < k; ++a) {
+        const int32_t e = slot_edge[b0 + a];
+        if (int_of[ij[2 * e]] == (int32_t)r) edge_slot[e] = b0 + a;
+    }
+}
+
+// Coefficient check and the spanning-tree weight of every edge.
+__global__ void k_edge_weight(int64_t m, const double *__restrict__ gpar, const double *__restrict__ gperp,
+                              double *w, int *err)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    const double a = gpar[e], b = gperp[e];
+    if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b)) atomicOr(err, 1);
+    w[e] = a < b ? a : b;  // lambda_min of the block (Lemma 2.1)
 }
 
 // eq. (1) for the edge of each slot.
@@ -222,25 +222,31 @@ sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *G, const double 
     if (m > 0)
         SGP_CUDA(ctx, cudaMemcpyAsync(M->ij.p, G->ij.p, sizeof(int32_t) * 2 * m,
                                       cudaMemcpyDeviceToDevice, ctx->stream));
-    int32_t *lowcnt = bp<int32_t>(M->lowcnt), *cursor = bp<int32_t>(M->cursor);
+    int32_t *cnt = bp<int32_t>(M->lowcnt), *cursor = bp<int32_t>(M->cursor);
     int32_t *row_ptr = bp<int32_t>(M->row_ptr), *col = bp<int32_t>(M->col);
     int32_t *slot_edge = bp<int32_t>(M->slot_edge), *edge_slot = bp<int32_t>(M->edge_slot);
-    const int32_t *ij = bp<const int32_t>(M->ij), *up = bp<const int32_t>(G->up_ptr);
+    const int32_t *ij = bp<const int32_t>(M->ij);
+    // the internal cell order of the graph
+    SGP_TRY(buf_ensure(ctx, M->orig_of, sizeof(int32_t) * std::max<int64_t>(n, 1)));
+    SGP_TRY(buf_ensure(ctx, M->int_of, sizeof(int32_t) * std::max<int64_t>(n, 1)));
+    if (n > 0) {
+        SGP_CUDA(ctx, cudaMemcpyAsync(M->orig_of.p, G->perm.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+        SGP_CUDA(ctx, cudaMemcpyAsync(M->int_of.p, G->int_of.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    }
+    const int32_t *int_of = bp<const int32_t>(M->int_of);
     int *err = ctx->d_flags;
     SGP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-    SGP_CUDA(ctx, cudaMemsetAsync(lowcnt, 0, sizeof(int32_t) * (n + 1), ctx->stream));
+    SGP_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), ctx->stream));
     SGP_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (n + 1), ctx->stream));
-    LAUNCH(ctx, k_low_count, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, m, lowcnt);
-    LAUNCH(ctx, k_row_len, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, up, (const int32_t *)lowcnt, n,
-           row_ptr);
-    SGP_TRY(scan_exclusive_i32(ctx, row_ptr, row_ptr, n));
-    LAUNCH(ctx, k_place_upper, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, m, up,
-           (const int32_t *)lowcnt, (const int32_t *)row_ptr, gpar, gperp, col, slot_edge,
-           edge_slot, bp<double>(M->w), err);
-    LAUNCH(ctx, k_place_lower, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, m,
-           (const int32_t *)row_ptr, cursor, col, slot_edge);
-    LAUNCH(ctx, k_sort_lower, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)row_ptr,
-           (const int32_t *)lowcnt, n, col, slot_edge);
+    LAUNCH(ctx, k_slot_count, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, m, int_of, cnt);
+    SGP_TRY(scan_exclusive_i32(ctx, cnt, row_ptr, n));
+    LAUNCH(ctx, k_slot_place, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, m, int_of, (const int32_t *)row_ptr, cursor,
+           col, slot_edge);
+    LAUNCH(ctx, k_sort_rows, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)row_ptr, n, ij, int_of, col,
+           slot_edge, edge_slot);
+    LAUNCH(ctx, k_edge_weight, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, m, gpar, gperp, bp<double>(M->w), err);
     LAUNCH(ctx, k_blocks, grid_for(ns, SGP_BLOCK), SGP_BLOCK, 0, ij, pos, gpar, gperp,
            (const int32_t *)slot_edge, (const int32_t *)col, ns, bp<double>(M->blk), blk32, err);
     int herr = 0;
@@ -271,7 +277,7 @@ void sgp_matrix_destroy(sgp_matrix *M)
     if (!M) return;
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&M->ij, &M->row_ptr, &M->col, &M->blk, &M->blk32, &M->edge_slot, &M->w,
-                    &M->slot_edge, &M->lowcnt, &M->cursor, &M->jac, &M->jac32};
+                    &M->slot_edge, &M->lowcnt, &M->cursor, &M->jac, &M->jac32, &M->orig_of, &M->int_of};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete M;

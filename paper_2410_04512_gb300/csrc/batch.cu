@@ -355,6 +355,14 @@ __global__ void k_b_check_edges(const int32_t *__restrict__ ij, int64_t m, const
     if (e < m && row_inst[ij[2 * e]] != row_inst[ij[2 * e + 1]]) atomicOr(err, 1);
 }
 
+// The matrix's internal cell order must keep every instance on its own rows.
+__global__ void k_b_check_order(int64_t n, const int32_t *__restrict__ orig_of, const int32_t *__restrict__ row_inst,
+                                int *err)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n && row_inst[orig_of[r]] != row_inst[r]) atomicOr(err, 2);
+}
+
 __global__ void k_b_row_inst(const int32_t *__restrict__ inst_row, int32_t *row_inst)
 {
     const int s = blockIdx.x;
@@ -505,8 +513,8 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *M, const sgp_fa
     // workspace
     const size_t v64 = sizeof(double) * 3 * n, v32 = sizeof(float) * 3 * n;
     const size_t tbl = sizeof(int32_t) * (2 * nch + 2 * n_inst + 4 + n);
-    size_t need = 4 * v64 + (mixed ? 6 * v32 : 0) + sizeof(double) * 2 * nch + sizeof(BScal) * n_inst +
-                  sizeof(double) * 6 * n_inst + tbl + 16 * 4096;
+    size_t need = 6 * v64 + (mixed ? 6 * v32 : 0) + sizeof(double) * 2 * nch + sizeof(BScal) * n_inst +
+                  sizeof(double) * 6 * n_inst + tbl + 18 * 4096;
     SGP_TRY(scratch_ensure(ctx, need));
     char *base = reinterpret_cast<char *>(ctx->d_scratch) + 256;
     auto take = [&](size_t bytes) {
@@ -540,9 +548,27 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *M, const sgp_fa
     LAUNCH(ctx, k_b_row_inst, (unsigned)n_inst, BB, 0, (const int32_t *)d_inst_row, d_row_inst);
     LAUNCH(ctx, k_b_check_edges, grid_for(M->m, BB), BB, 0, bp<const int32_t>(M->ij), M->m,
            (const int32_t *)d_row_inst, d_flags + 8);
+    const int32_t *orig_of = bp<const int32_t>(M->orig_of);
+    LAUNCH(ctx, k_b_check_order, grid_for(n, BB), BB, 0, n, orig_of, (const int32_t *)d_row_inst, d_flags + 8);
     int herr = 0;
     SGP_TRY(read_back(ctx, &herr, d_flags + 8, sizeof(int)));
-    if (herr) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg_batched: an edge joins two instances");
+    if (herr & 1) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg_batched: an edge joins two instances");
+    if (herr & 2)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG,
+                        "pcg_batched: the matrix's cell order mixes instances (build its graph with "
+                        "sgp_collision_graph_batched and the same offsets)");
+    // the solve runs in the matrix's internal cell order, which keeps each
+    // instance on the rows [offsets[s], offsets[s+1])
+    const double *F_user = F;
+    double *v_user = v;
+    double *F_in = reinterpret_cast<double *>(take(v64));
+    double *v_in = reinterpret_cast<double *>(take(v64));
+    LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, F_user, F_in);
+    if (opts->x0_given)
+        LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v_user,
+               v_in);
+    F = F_in;
+    v = v_in;
 
     Batch b{d_chunk_inst, d_chunk_row, d_inst_chunk, d_sc, d_part, d_flags, d_flags + 1, (int)n_inst};
     const unsigned G = (unsigned)nch;
@@ -632,6 +658,7 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *M, const sgp_fa
     SGP_CUDA(ctx, cudaMemsetAsync(d_out, 0, sizeof(double) * 2 * n_inst, ctx->stream));
     LAUNCH(ctx, k_b_resid64, G, BB, 0, B64, row_ptr, M->gamma0, b, F, (const double *)v, (double *)nullptr, d_out);
     SGP_TRY(read_back(ctx, hres.data(), d_out, sizeof(double) * 2 * n_inst));
+    LAUNCH(ctx, k_to_caller<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v, v_user);
     sgp_status rc = SGP_OK;
     for (int64_t s = 0; s < n_inst; ++s) {
         inf[s].true_rel_residual = hres[2 * s + 1] > 0 ? std::sqrt(hres[2 * s] / hres[2 * s + 1]) : 0.0;

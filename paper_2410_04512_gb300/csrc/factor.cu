@@ -32,24 +32,26 @@
 namespace {
 
 // ------------------------------------------------------------------ adjacency
+// The factor works in the matrix's internal cell order: tree edge endpoints
+// are mapped through int_of.
 __global__ void k_tdeg(const int32_t *__restrict__ ij, const int32_t *__restrict__ edges, int64_t nt,
-                       int32_t *deg)
+                       const int32_t *__restrict__ int_of, int32_t *deg)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
     int32_t e = edges[t];
-    atomicAdd(deg + ij[2 * e], 1);
-    atomicAdd(deg + ij[2 * e + 1], 1);
+    atomicAdd(deg + int_of[ij[2 * e]], 1);
+    atomicAdd(deg + int_of[ij[2 * e + 1]], 1);
 }
 
 __global__ void k_adj_fill(const int32_t *__restrict__ ij, const int32_t *__restrict__ edges,
-                           int64_t nt, const int32_t *__restrict__ adj_ptr, int32_t *cursor,
-                           int32_t *nbr, int32_t *eref)
+                           int64_t nt, const int32_t *__restrict__ int_of, const int32_t *__restrict__ adj_ptr,
+                           int32_t *cursor, int32_t *nbr, int32_t *eref)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
     int32_t e = edges[t];
-    int32_t a = ij[2 * e], b = ij[2 * e + 1];
+    int32_t a = int_of[ij[2 * e]], b = int_of[ij[2 * e + 1]];
     int32_t sa = adj_ptr[a] + atomicAdd(cursor + a, 1);
     int32_t sb = adj_ptr[b] + atomicAdd(cursor + b, 1);
     nbr[sa] = b;
@@ -154,6 +156,13 @@ __global__ void k_et_jump(int64_t m2, const int32_t *__restrict__ succ, const in
         succ2[s] = succ[nx];
         dist2[s] = dist[s] + dist[nx];
     }
+}
+
+__global__ void k_comp_internal(int64_t n, const int32_t *__restrict__ comp, const int32_t *__restrict__ int_of,
+                                const int32_t *__restrict__ orig_of, int32_t *out)
+{
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) out[v] = int_of[comp[orig_of[v]]];
 }
 
 __global__ void k_root_flag(const int32_t *__restrict__ comp, int64_t n, int32_t *flag)
@@ -1672,7 +1681,10 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     SGP_TRY(buf_ensure(ctx, F->L, sizeof(double) * 9 * P));
     SGP_TRY(buf_ensure(ctx, F->Dinv, sizeof(double) * 6 * n1));
     SGP_TRY(buf_ensure(ctx, F->work, sizeof(double) * 3 * n1));
+    SGP_TRY(buf_ensure(ctx, F->orig_of, sizeof(int32_t) * n1));
     if (n == 0) return SGP_OK;
+    SGP_CUDA(ctx, cudaMemcpyAsync(F->orig_of.p, M->orig_of.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
 
     int32_t *adj_ptr = bp<int32_t>(F->adj_ptr), *deg = bp<int32_t>(F->deg);
     int32_t *nbr = bp<int32_t>(F->nbr), *twin = bp<int32_t>(F->twin), *eref = bp<int32_t>(F->eref);
@@ -1687,10 +1699,11 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
 
     // adjacency of the forest, sorted by neighbour, with twin entries
     SGP_CUDA(ctx, cudaMemsetAsync(deg, 0, sizeof(int32_t) * n1, ctx->stream));
-    LAUNCH(ctx, k_tdeg, grid_for(nt, SGP_BLOCK), SGP_BLOCK, 0, ij, edges, nt, deg);
+    const int32_t *int_of = bp<const int32_t>(M->int_of), *orig_of = bp<const int32_t>(M->orig_of);
+    LAUNCH(ctx, k_tdeg, grid_for(nt, SGP_BLOCK), SGP_BLOCK, 0, ij, edges, nt, int_of, deg);
     SGP_TRY(scan_exclusive_i32(ctx, deg, adj_ptr, n));
     SGP_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n1, ctx->stream));
-    LAUNCH(ctx, k_adj_fill, grid_for(nt, SGP_BLOCK), SGP_BLOCK, 0, ij, edges, nt,
+    LAUNCH(ctx, k_adj_fill, grid_for(nt, SGP_BLOCK), SGP_BLOCK, 0, ij, edges, nt, int_of,
            (const int32_t *)adj_ptr, cnt, nbr, eref);
     LAUNCH(ctx, k_adj_sort, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr, n, nbr, eref);
     LAUNCH(ctx, k_twin, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr, n,
@@ -1728,7 +1741,11 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
         int32_t *succ = bp<int32_t>(F->et_succ), *dist = bp<int32_t>(F->et_dist);
         int32_t *succ2 = bp<int32_t>(F->et_succ2), *dist2 = bp<int32_t>(F->et_dist2);
         int32_t *dflag = bp<int32_t>(F->et_flag);
-        const int32_t *comp = bp<const int32_t>(T->comp);
+        // tree labels in internal ids: the root of v's tree is int_of[comp[orig_of[v]]]
+        SGP_TRY(buf_ensure(ctx, F->comp_int, sizeof(int32_t) * n1));
+        LAUNCH(ctx, k_comp_internal, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, bp<const int32_t>(T->comp), int_of,
+               orig_of, bp<int32_t>(F->comp_int));
+        const int32_t *comp = bp<const int32_t>(F->comp_int);
         pinned = bp<int32_t>(F->pinned);
         // trees: rank of each root among roots, sizes, exclusive size sums
         LAUNCH(ctx, k_root_flag, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n, flag);
@@ -2117,9 +2134,13 @@ sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *F, const double *b, do
     if (!ctx || !F || (F->n > 0 && (!b || !x))) return SGP_ERR_INVALID_ARG;
     if (F->n == 0) return SGP_OK;
     SGP_CUDA(ctx, cudaSetDevice(ctx->device));
-    if (x != b)
-        SGP_CUDA(ctx, cudaMemcpyAsync(x, b, sizeof(double) * 3 * F->n, cudaMemcpyDeviceToDevice, ctx->stream));
-    return tree_apply_inplace<double>(ctx, F, x, nullptr);
+    // caller order -> internal order (the factor's workspace) -> caller order
+    double *wi = bp<double>(F->work);
+    const int32_t *orig_of = bp<const int32_t>(F->orig_of);
+    LAUNCH(ctx, k_to_internal<double>, grid_for(F->n, SGP_BLOCK), SGP_BLOCK, 0, F->n, orig_of, b, wi);
+    SGP_TRY(tree_apply_inplace<double>(ctx, F, wi, nullptr));
+    LAUNCH(ctx, k_to_caller<double>, grid_for(F->n, SGP_BLOCK), SGP_BLOCK, 0, F->n, orig_of, (const double *)wi, x);
+    return SGP_OK;
 }
 
 sgp_status sgp_factor_info(const sgp_factor *F, int32_t *rounds, int32_t *levels, int64_t *l_blocks,
@@ -2148,7 +2169,7 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->bm_tot, &F->bm_base, &F->bm_max, &F->bm_q, &F->bm_beg, &F->bm_cloc, &F->bm_oloc,
                     &F->bm_pbeg, &F->bm_qloc, &F->bm_Lf, &F->bm_Lf32, &F->bm_Lb, &F->bm_Lb32, &F->bm_D,
                     &F->bm_D32, &F->coop_idx, &F->ct_fo, &F->ct_eoff, &F->ct_coff, &F->ct_fq,
-                    &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx};
+                    &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx, &F->comp_int, &F->orig_of};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete F;

@@ -126,6 +126,37 @@ __global__ void k_scatter(const double *__restrict__ pos, const double *__restri
     spos32[s] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], (float)radii[i]);
 }
 
+// Order the cells inside each grid cell by index, which makes the grid-cell
+// order (the solvers' internal cell order) deterministic.
+__global__ void k_sort_cells(int64_t ncell, const int32_t *__restrict__ cell_start, int32_t *perm,
+                             double4_32a *spos, float4 *spos32)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int32_t b0 = cell_start[c], k = cell_start[c + 1] - b0;
+    for (int32_t a = 1; a < k; ++a) {
+        const int32_t v = perm[b0 + a];
+        const double4_32a p = spos[b0 + a];
+        const float4 f = spos32[b0 + a];
+        int32_t b = a - 1;
+        while (b >= 0 && perm[b0 + b] > v) {
+            perm[b0 + b + 1] = perm[b0 + b];
+            spos[b0 + b + 1] = spos[b0 + b];
+            spos32[b0 + b + 1] = spos32[b0 + b];
+            --b;
+        }
+        perm[b0 + b + 1] = v;
+        spos[b0 + b + 1] = p;
+        spos32[b0 + b + 1] = f;
+    }
+}
+
+__global__ void k_inverse_perm(int64_t n, const int32_t *__restrict__ perm, int32_t *inv)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) inv[perm[t]] = (int32_t)t;
+}
+
 // The contact predicate, with explicit round-to-nearest operations in the
 // order sqrt((dx*dx + dy*dy) + dz*dz) < R_i + R_j, dx = x_j - x_i.
 __device__ __forceinline__ bool contact(double4_32a pi, double4_32a pj)
@@ -316,6 +347,10 @@ static sgp_status collision_graph(sgp_ctx *ctx, int64_t n, int64_t n_inst, const
     SGP_CUDA(ctx, cudaMemsetAsync(cell_cnt, 0, sizeof(int32_t) * (ncell + 1), ctx->stream));
     LAUNCH(ctx, k_scatter, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, pos, radii, n,
            (const int32_t *)cell_id, (const int32_t *)cell_start, cell_cnt, perm, spos, spos32);
+    LAUNCH(ctx, k_sort_cells, grid_for(ncell, SGP_BLOCK), SGP_BLOCK, 0, ncell, (const int32_t *)cell_start, perm,
+           spos, spos32);
+    SGP_TRY(buf_ensure(ctx, G->int_of, sizeof(int32_t) * n));
+    LAUNCH(ctx, k_inverse_perm, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, (const int32_t *)perm, bp<int32_t>(G->int_of));
     LAUNCH(ctx, k_contacts<false>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
            (const int32_t *)perm, (const double4_32a *)spos, (const float4 *)spos32, (const int32_t *)cell_start,
            cnt, (const int32_t *)nullptr, (int32_t *)nullptr);
@@ -374,7 +409,7 @@ void sgp_graph_destroy(sgp_graph *G)
     if (!G) return;
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&G->ij, &G->up_ptr, &G->cell_id, &G->cell_cnt, &G->cell_start, &G->perm,
-                    &G->spos, &G->spos32, &G->cnt, &G->bbox, &G->inst, &G->grids};
+                    &G->spos, &G->spos32, &G->cnt, &G->bbox, &G->inst, &G->grids, &G->int_of};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete G;

@@ -382,7 +382,7 @@ static sgp_status mpnn_ensure(sgp_ctx *ctx, sgp_mpnn *N, int64_t n)
     const int64_t nblk = (n + CHUNK - 1) / CHUNK + 1;
     SGP_TRY(buf_ensure(ctx, N->part, sizeof(float) * (size_t)nblk * (H * H2 + H)));
     SGP_TRY(buf_ensure(ctx, N->red, sizeof(double) * 2 * 1024 + 256));
-    SGP_TRY(buf_ensure(ctx, N->tmp, sizeof(double) * 9 * nn));
+    SGP_TRY(buf_ensure(ctx, N->tmp, sizeof(double) * 12 * nn));
     N->n = n;
     return SGP_OK;
 }
@@ -463,10 +463,15 @@ sgp_status sgp_mpnn_params(sgp_ctx *ctx, const sgp_mpnn *N, float *params, float
     return SGP_OK;
 }
 
-sgp_status sgp_mpnn_forward(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix *M, const sgp_factor *Fh,
-                            const double *F, const double *v_prev, double *v0)
+}  // extern "C"
+
+// The forward pass in the matrix's internal cell order: F (and v_prev) are
+// taken from the caller's order into N->tmp[9n, 12n) (and the third basis
+// vector); the output stays in N->v0w, in internal order.
+static sgp_status mpnn_forward_internal(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix *M, const sgp_factor *Fh,
+                                        const double *F, const double *v_prev)
 {
-    if (!ctx || !N || !M || !Fh || !F || !v0) return SGP_ERR_INVALID_ARG;
+    if (!ctx || !N || !M || !Fh || !F) return SGP_ERR_INVALID_ARG;
     if (Fh->n != M->n) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "mpnn_forward: factor and matrix differ in size");
     SGP_CUDA(ctx, cudaSetDevice(ctx->device));
     const int64_t n = M->n;
@@ -474,12 +479,15 @@ sgp_status sgp_mpnn_forward(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix *M, cons
     N->M = M;
     if (n == 0) return SGP_OK;
     double *b0 = bp<double>(N->basis), *b1 = b0 + 3 * n, *b2 = b1 + 3 * n;
+    double *Fi = bp<double>(N->tmp) + 9 * n;
+    const int32_t *orig_of = bp<const int32_t>(M->orig_of);
+    LAUNCH(ctx, k_to_internal<double>, grid_for(n, TB), TB, 0, n, orig_of, F, Fi);
     // basis: block-Jacobi solve, spanning-forest solve, previous velocity
     SGP_TRY(matrix_block_jacobi(ctx, const_cast<sgp_matrix *>(M)));
-    LAUNCH(ctx, k_mp_jacobi, grid_for(n, TB), TB, 0, n, bp<const double>(M->jac), F, b0);
-    SGP_CUDA(ctx, cudaMemcpyAsync(b1, F, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    LAUNCH(ctx, k_mp_jacobi, grid_for(n, TB), TB, 0, n, bp<const double>(M->jac), (const double *)Fi, b0);
+    SGP_CUDA(ctx, cudaMemcpyAsync(b1, Fi, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
     SGP_TRY(tree_apply_inplace<double>(ctx, Fh, b1, nullptr));
-    if (v_prev) SGP_CUDA(ctx, cudaMemcpyAsync(b2, v_prev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (v_prev) LAUNCH(ctx, k_to_internal<double>, grid_for(n, TB), TB, 0, n, orig_of, v_prev, b2);
     else SGP_CUDA(ctx, cudaMemsetAsync(b2, 0, sizeof(double) * 3 * n, ctx->stream));
     double *red = bp<double>(N->red);
     unsigned *counter = reinterpret_cast<unsigned *>(red + 2 * 1024 + 8);
@@ -502,8 +510,21 @@ sgp_status sgp_mpnn_forward(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix *M, cons
         SGP_TRY((dense<H, H, H, false, true>(ctx, n, h, a, pb + off, pb + off + H * H2, hn)));
     }
     LAUNCH(ctx, k_mp_out, grid_for(n, TB), TB, 0, n, (const float *)(hs + 3 * H * n), pb + OFF_WOUT, pb + OFF_BOUT,
-           (const double *)b0, (const double *)b1, (const double *)b2, bp<float>(N->c), v0);
-    SGP_CUDA(ctx, cudaMemcpyAsync(N->v0w.p, v0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+           (const double *)b0, (const double *)b1, (const double *)b2, bp<float>(N->c), bp<double>(N->v0w));
+    return SGP_OK;
+}
+
+extern "C" {
+
+sgp_status sgp_mpnn_forward(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix *M, const sgp_factor *Fh,
+                            const double *F, const double *v_prev, double *v0)
+{
+    if (!v0) return SGP_ERR_INVALID_ARG;
+    SGP_TRY(mpnn_forward_internal(ctx, N, M, Fh, F, v_prev));
+    const int64_t n = M->n;
+    if (n > 0)
+        LAUNCH(ctx, k_to_caller<double>, grid_for(n, TB), TB, 0, n, bp<const int32_t>(M->orig_of),
+               bp<const double>(N->v0w), v0);
     return SGP_OK;
 }
 
@@ -526,7 +547,9 @@ sgp_status sgp_mpnn_backward(sgp_ctx *ctx, sgp_mpnn *N, const double *v_target, 
     double *red = bp<double>(N->red);
     unsigned *counter = reinterpret_cast<unsigned *>(red + 2 * 1024 + 8);
     double *nd = red + 2 * 1024 + 2, *lossout = red + 2 * 1024 + 4;
-    double *e = bp<double>(N->tmp), *Ge = e + 3 * n, *Gt = Ge + 3 * n;
+    double *e = bp<double>(N->tmp), *Ge = e + 3 * n, *Gt = Ge + 3 * n, *vt = Gt + 3 * n;
+    LAUNCH(ctx, k_to_internal<double>, grid_for(n, TB), TB, 0, n, bp<const int32_t>(M->orig_of), v_target, vt);
+    v_target = vt;
     const unsigned G = red_blocks(3 * n);
     LAUNCH(ctx, k_mp_diff, grid_for(3 * n, TB), TB, 0, 3 * n, v0, v_target, e);
     const double *g = e;
@@ -587,20 +610,31 @@ extern "C" sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix
                                      int32_t *used)
 {
     if (flags & ~SGP_WARM_MR_SCALE) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "warm_start: unknown flags");
-    SGP_TRY(sgp_mpnn_forward(ctx, N, M, Fh, F, v_prev, v0));
+    if (!v0) return SGP_ERR_INVALID_ARG;
+    SGP_TRY(mpnn_forward_internal(ctx, N, M, Fh, F, v_prev));
     const int64_t n = M->n;
-    if (n > 0 && (flags & SGP_WARM_MR_SCALE)) {
+    if (n == 0) {
+        if (used) *used = 0;
+        return SGP_OK;
+    }
+    // scaling and acceptance on a copy of the network output (internal order);
+    // N->v0w stays the network's own output for a following backward pass
+    double *Gv = bp<double>(N->tmp), *w = Gv + 3 * n;
+    const double *Fi = bp<const double>(N->tmp) + 9 * n;
+    SGP_CUDA(ctx, cudaMemcpyAsync(w, N->v0w.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (flags & SGP_WARM_MR_SCALE) {
         double *red = bp<double>(N->red);
         unsigned *counter = reinterpret_cast<unsigned *>(red + 2 * 1024 + 8);
         double *nd = red + 2 * 1024 + 2;
-        double *Gv = bp<double>(N->tmp);
-        SGP_TRY(spmv64(ctx, M, v0, Gv));
-        LAUNCH(ctx, k_mp_dot2, red_blocks(3 * n), TB, 0, 3 * n, (const double *)Gv, F, (const double *)Gv,
+        SGP_TRY(spmv64(ctx, M, w, Gv));
+        LAUNCH(ctx, k_mp_dot2, red_blocks(3 * n), TB, 0, 3 * n, (const double *)Gv, Fi, (const double *)Gv,
                (const double *)Gv, red, counter, nd);
-        LAUNCH(ctx, k_mp_scale, grid_for(3 * n, TB), TB, 0, 3 * n, (const double *)nd, v0);
+        LAUNCH(ctx, k_mp_scale, grid_for(3 * n, TB), TB, 0, 3 * n, (const double *)nd, w);
     }
     int u = 0;
-    SGP_TRY(mpnn_residual_check(ctx, M, F, v0, &u));
+    SGP_TRY(mpnn_residual_check(ctx, M, Fi, w, &u));
+    LAUNCH(ctx, k_to_caller<double>, grid_for(n, TB), TB, 0, n, bp<const int32_t>(M->orig_of), (const double *)w,
+           v0);
     if (used) *used = u;
     return SGP_OK;
 }

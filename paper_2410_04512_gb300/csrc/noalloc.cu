@@ -33,19 +33,23 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_mu;
 void *g_addr[NA_MAX_DEVICES] = {nullptr};
 
-// Row i of the Appendix B.2 product, same operation order as the solver's.
+// Internal row r (cell orig_of[r]) of the Appendix B.2 product, same
+// operation order as the solver's.  v is in the caller's cell order: the
+// matrix's rows and columns are mapped through orig_of, so no permuted copy
+// (and no workspace) is needed.
 __device__ __forceinline__ void na_row(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                       const double *__restrict__ blk, double gamma0,
-                                       const double *__restrict__ v, int64_t i, double *vi, double *y)
+                                       const double *__restrict__ blk, const int32_t *__restrict__ orig_of,
+                                       double gamma0, const double *__restrict__ v, int64_t r, int64_t i,
+                                       double *vi, double *y)
 {
     vi[0] = v[3 * i]; vi[1] = v[3 * i + 1]; vi[2] = v[3 * i + 2];
     y[0] = gamma0 * vi[0]; y[1] = gamma0 * vi[1]; y[2] = gamma0 * vi[2];
-    int32_t s1 = row_ptr[i + 1];
-    for (int32_t s = row_ptr[i]; s < s1; ++s) {
+    int32_t s1 = row_ptr[r + 1];
+    for (int32_t s = row_ptr[r]; s < s1; ++s) {
         const double2 *b2 = reinterpret_cast<const double2 *>(blk + 6 * (int64_t)s);
         double2 a = b2[0], b = b2[1], c = b2[2];
         double S[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
-        int32_t j = col[s];
+        int32_t j = orig_of[col[s]];
         double d[3] = {vi[0] - v[3 * (int64_t)j], vi[1] - v[3 * (int64_t)j + 1], vi[2] - v[3 * (int64_t)j + 2]};
         double t[3];
         sym_mv(S, d, t);
@@ -56,18 +60,19 @@ __device__ __forceinline__ void na_row(const int32_t *__restrict__ row_ptr, cons
 // One thread per row; one partial per block in the scratch array; the last
 // block to arrive sums the partials in block order and writes *dot.
 __global__ void k_spmv_dot_noalloc(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                   const double *__restrict__ blk, double gamma0, int64_t n,
-                                   const double *__restrict__ v, double *y, double *dot,
+                                   const double *__restrict__ blk, const int32_t *__restrict__ orig_of,
+                                   double gamma0, int64_t n, const double *__restrict__ v, double *y, double *dot,
                                    unsigned char *scratch)
 {
     __shared__ double sh[NA_BLOCK / 32];
     double *partials = reinterpret_cast<double *>(scratch);
     unsigned *counter = reinterpret_cast<unsigned *>(scratch + NA_MAX_BLOCKS * sizeof(double));
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (i < n) {
+    if (r < n) {
+        const int64_t i = orig_of[r];
         double vi[3], yi[3];
-        na_row(row_ptr, col, blk, gamma0, v, i, vi, yi);
+        na_row(row_ptr, col, blk, orig_of, gamma0, v, r, i, vi, yi);
         y[3 * i] = yi[0]; y[3 * i + 1] = yi[1]; y[3 * i + 2] = yi[2];
         acc = vi[0] * yi[0] + vi[1] * yi[1] + vi[2] * yi[2];
     }
@@ -125,7 +130,8 @@ sgp_status sgp_spmv_dot_noalloc(sgp_ctx *ctx, const sgp_matrix *M, const double 
         return SGP_OK;
     }
     LAUNCH(ctx, k_spmv_dot_noalloc, grid_for(n, NA_BLOCK), NA_BLOCK, 0, bp<const int32_t>(M->row_ptr),
-           bp<const int32_t>(M->col), bp<const double>(M->blk), M->gamma0, n, v, y, dot, base);
+           bp<const int32_t>(M->col), bp<const double>(M->blk), bp<const int32_t>(M->orig_of), M->gamma0, n, v, y,
+           dot, base);
     return SGP_OK;
 }
 

@@ -664,11 +664,19 @@ sgp_status sgp_spmv(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *
     if (!ctx || !M || (M->n > 0 && (!v || !y))) return SGP_ERR_INVALID_ARG;
     if (v == y) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "spmv: v and y must differ");
     SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = M->n;
+    if (n == 0) return SGP_OK;
+    // caller order -> internal order -> product -> caller order
+    SGP_TRY(scratch_ensure(ctx, sizeof(double) * 6 * n + 1024));
+    double *vi = reinterpret_cast<double *>(ctx->d_scratch), *yi = vi + 3 * n;
+    const int32_t *orig_of = bp<const int32_t>(M->orig_of);
+    LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, v, vi);
     cudaEvent_t ev;
     SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
-    LAUNCH(ctx, k_spmv<double>, grid_for(M->n, 128), 128, 0, make_blk<double>(M),
-           bp<const int32_t>(M->row_ptr), M->gamma0, M->n, v, y);
+    LAUNCH(ctx, k_spmv<double>, grid_for(n, 128), 128, 0, make_blk<double>(M), bp<const int32_t>(M->row_ptr),
+           M->gamma0, n, (const double *)vi, yi);
     SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
+    LAUNCH(ctx, k_to_caller<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)yi, y);
     return SGP_OK;
 }
 
@@ -698,7 +706,7 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     // workspace: FP64 r, p, q, w (4 x 3n), FP32 rhs, r, p, q, w, d (6 x 3n),
     // partials, scalars
     const size_t v64 = sizeof(double) * 3 * n, v32 = sizeof(float) * 3 * n;
-    size_t need = 4 * v64 + (mixed ? 6 * v32 : 0) + sizeof(double) * 2 * MAXP + 2 * sizeof(Scal) + 4096;
+    size_t need = 6 * v64 + (mixed ? 6 * v32 : 0) + sizeof(double) * 2 * MAXP + 2 * sizeof(Scal) + 4096;
     SGP_TRY(scratch_ensure(ctx, need + 4096));
     char *base = reinterpret_cast<char *>(ctx->d_scratch) + 256;
     auto take = [&](size_t b) {
@@ -713,6 +721,18 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     double *p = reinterpret_cast<double *>(take(v64));
     double *q = reinterpret_cast<double *>(take(v64));
     double *w = reinterpret_cast<double *>(take(v64));
+    // the solve runs in the matrix's internal cell order
+    const double *F_user = F;
+    double *v_user = v;
+    double *F_in = reinterpret_cast<double *>(take(v64));
+    double *v_in = reinterpret_cast<double *>(take(v64));
+    const int32_t *orig_of = bp<const int32_t>(M->orig_of);
+    LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, F_user, F_in);
+    if (opts->x0_given)
+        LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v_user,
+               v_in);
+    F = F_in;
+    v = v_in;
     Scal hs{};
     sgp_status rc = SGP_OK;
     Blk<double> B64 = make_blk<double>(M);
@@ -781,6 +801,7 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
            partials, o2);
     SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
     inf.true_rel_residual = hres[1] > 0 ? std::sqrt(hres[0] / hres[1]) : 0.0;
+    LAUNCH(ctx, k_to_caller<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v, v_user);
     if (info) *info = inf;
     if (inf.status == SGP_ERR_NOT_SPD)
         rc = sgp_fail(ctx, SGP_ERR_NOT_SPD, "pcg: breakdown (p^T Gamma p or r^T z not positive)");

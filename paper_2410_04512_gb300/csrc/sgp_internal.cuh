@@ -174,6 +174,7 @@ struct sgp_graph {
     DBuf up_ptr;   // n + 1 int32: edges of row i are [up_ptr[i], up_ptr[i+1])
     // cell-list scratch kept for reuse
     DBuf cell_id, cell_cnt, cell_start, perm, spos, spos32, cnt, bbox, inst, grids;
+    DBuf int_of;   // n int32: position of each cell in grid-cell order (perm is the inverse)
 };
 
 struct sgp_matrix {
@@ -190,6 +191,11 @@ struct sgp_matrix {
     DBuf w;          // m float64 tree weight min(g_par, g_perp)
     DBuf slot_edge;  // 2m int32 (scratch)
     DBuf lowcnt, cursor;
+    // The matrix rows (and every vector the solvers use internally) follow
+    // the grid-cell order of the collision graph, so that cells in contact
+    // sit close together in memory; orig_of / int_of translate to and from
+    // the caller's cell order.  ij, edge_slot and w stay in edge order.
+    DBuf orig_of, int_of;  // n int32 each
     DBuf jac;        // n x sym6 float64 block-Jacobi inverse (built lazily)
     DBuf jac32;      // n x sym6 float32
     int jac_valid = 0;
@@ -235,6 +241,7 @@ struct sgp_factor {
     DBuf tail_idx;  // level positions and receiver offsets of the tail levels
     DBuf tail_q, tail_c, tail_b;  // local indices (position - tail_P0)
     DBuf work;      // n x 3 float64 apply workspace
+    DBuf orig_of;   // n int32: the matrix's internal cell order (vectors are solved in it)
     // local phase: the forest is cut into blocks of comp_size consecutive
     // vertices of a depth-first preorder; levels < local_levels eliminate
     // only vertices whose tree neighbours are all in their own block, and the
@@ -250,7 +257,7 @@ struct sgp_factor {
     DBuf bm_q, bm_beg, bm_cloc, bm_oloc, bm_pbeg, bm_qloc;
     DBuf bm_Lf, bm_Lf32, bm_Lb, bm_Lb32, bm_D, bm_D32;
     int32_t bm_maxv[4] = {0, 0, 0, 0};      // largest per-block count of each kind
-    DBuf et_succ, et_dist, et_succ2, et_dist2, et_tid, et_size, et_flag, pinned;  // Euler tour scratch
+    DBuf et_succ, et_dist, et_succ2, et_dist2, et_tid, et_size, et_flag, pinned, comp_int;  // Euler tour scratch
     // structure-simulation scratch
     DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,
         acc, fill, sbuf, tmp, rflag, cnt;
@@ -398,6 +405,31 @@ __device__ __forceinline__ double sum_partials(const double *partials, int n, do
     double v = 0.0;
     for (int k = threadIdx.x; k < n; k += BS) v += __ldcg(partials + k);
     return block_sum<BS>(v, sh);
+}
+
+// Vectors between the caller's cell order and the solvers' internal order
+// (the matrix's orig_of): dst[r] = src[orig_of[r]] and back.  One thread per
+// cell, n x 3 entries.
+template <typename T>
+__global__ void k_to_internal(int64_t n, const int32_t *__restrict__ orig_of, const T *__restrict__ src, T *dst)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t i = orig_of[r];
+    dst[3 * r] = src[3 * i];
+    dst[3 * r + 1] = src[3 * i + 1];
+    dst[3 * r + 2] = src[3 * i + 2];
+}
+
+template <typename T>
+__global__ void k_to_caller(int64_t n, const int32_t *__restrict__ orig_of, const T *__restrict__ src, T *dst)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t i = orig_of[r];
+    dst[3 * i] = src[3 * r];
+    dst[3 * i + 1] = src[3 * r + 1];
+    dst[3 * i + 2] = src[3 * r + 2];
 }
 
 // internal entry points shared between translation units
