@@ -424,12 +424,9 @@ struct Sim {
 // once equals eliminating them one by one: the forest stays a forest.
 // Pinned vertices (local phase: a tree neighbour in another block) are never
 // chosen, and the rules that defer to a neighbour ignore pinned neighbours.
-__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt,
-                         const int32_t *__restrict__ pin)
+__device__ __forceinline__ void select_vertex(const Sim &S, int32_t v, int32_t level, uint32_t salt,
+                                              const int32_t *__restrict__ pin)
 {
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= na) return;
-    const int32_t v = A[k];
     if (pin && pin[v]) return;
     auto free_ = [&](int32_t u) { return !(pin && pin[u]); };
     const int32_t d = S.deg[v];
@@ -466,6 +463,13 @@ __global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32
     S.rq[v] = sw ? make_int2(b, a) : make_int2(a, b);
     S.re[v] = sw ? make_int2(S.eref[e2], S.eref[e1]) : make_int2(S.eref[e1], S.eref[e2]);
     S.ren[v] = sw ? make_int2(e2, e1) : make_int2(e1, e2);
+}
+
+__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt,
+                         const int32_t *__restrict__ pin)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < na) select_vertex(S, A[k], level, salt, pin);
 }
 
 // ----------------------------------------------------- structure: bookkeeping
@@ -551,11 +555,8 @@ __global__ void k_contrib(Sim S, const int32_t *__restrict__ rv, int32_t r0, int
 
 // Structural update of a merged level: a leaf leaves its neighbour's list;
 // a degree-2 vertex splices its two neighbours together (fill edge nt + v).
-__global__ void k_apply(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt, int32_t nt)
+__device__ __forceinline__ void apply_vertex(const Sim &S, int32_t v, int32_t nt)
 {
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cnt) return;
-    const int32_t v = ord[p0 + k];
     const int32_t r = S.nrec[v];
     if (r == 1) {
         S.nbr[S.twin[S.ren[v].x]] = -1;
@@ -569,6 +570,174 @@ __global__ void k_apply(Sim S, const int32_t *__restrict__ ord, int32_t p0, int3
         S.twin[tb] = ta;
         S.eref[ta] = nt + v;
         S.eref[tb] = nt + v;
+    }
+}
+
+__global__ void k_apply(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt, int32_t nt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < cnt) apply_vertex(S, ord[p0 + k], nt);
+}
+
+// ------------------------------------------------- structure: the short tail
+// Once the alive list is short (at most SMALL_NA vertices) the remaining
+// levels run in one block of SB threads: the same selection, the same stable
+// compactions and the same contributor lists as the per-level kernels above
+// (hence the same structure), with block-wide scans and __syncthreads()
+// between the steps instead of kernel boundaries and a host round trip per
+// count.  Thread t owns a contiguous chunk of every list, so each compaction
+// keeps list order.  rec[l] = (eliminated, pairs, receivers, contributor
+// entries) of the l-th level run here; hdr = (levels run, vertices still
+// alive, error: 1 = a level eliminated nothing, 2 = inconsistent contributor
+// count).
+constexpr int SMALL_NA = 8192;
+constexpr int SMALL_MAXL = 96;
+constexpr int SB = 1024;
+
+__device__ __forceinline__ int32_t sb_scan(int32_t v, int32_t *sh, int32_t *total)
+{
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (l >= o) x += y;
+    }
+    if (l == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int32_t u = sh[l];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, u, o);
+            if (l >= o) u += y;
+        }
+        sh[l] = u;
+    }
+    __syncthreads();
+    const int32_t before = (w > 0 ? sh[w - 1] : 0) + x - v;
+    *total = sh[SB / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(SB) k_levels_small(Sim S, int32_t *A, int32_t *Bl, int32_t na, int32_t level,
+                                                     int32_t phase, int32_t *rflag, int32_t *ord, int32_t npos,
+                                                     int32_t *pos, int32_t *pr_ptr, int32_t *pr_q, int32_t *pr_c,
+                                                     int32_t npair, int32_t *rv, int32_t nrecv, int32_t *rc_ptr,
+                                                     int32_t *ct, int32_t ncontrib, int32_t nt, int4 *rec,
+                                                     int32_t *hdr)
+{
+    __shared__ int32_t sh[SB / 32];
+    const int32_t t = threadIdx.x;
+    int32_t done = 0, err = 0;
+    auto chunk = [&](int32_t cnt, int32_t &lo, int32_t &hi) {
+        const int32_t per = (cnt + SB - 1) / SB;
+        lo = min(cnt, t * per);
+        hi = min(cnt, lo + per);
+    };
+    while (na > 0 && done < SMALL_MAXL) {
+        const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
+        int32_t lo, hi;
+        chunk(na, lo, hi);
+        for (int32_t k = lo; k < hi; ++k) select_vertex(S, A[k], level, salt, nullptr);
+        __syncthreads();
+        // eliminated vertices -> ord, pos
+        int32_t c = 0, ne;
+        for (int32_t k = lo; k < hi; ++k) c += (S.lev[A[k]] == level);
+        int32_t off = sb_scan(c, sh, &ne);
+        for (int32_t k = lo; k < hi; ++k) {
+            const int32_t v = A[k];
+            if (S.lev[v] == level) {
+                const int32_t at = npos + off++;
+                ord[at] = v;
+                pos[v] = at;
+            }
+        }
+        if (ne == 0) { err = 1; break; }
+        __syncthreads();
+        // pairs of the eliminated vertices; receivers flagged
+        int32_t elo, ehi, lp;
+        chunk(ne, elo, ehi);
+        c = 0;
+        for (int32_t k = elo; k < ehi; ++k) c += S.nrec[ord[npos + k]];
+        off = sb_scan(c, sh, &lp);
+        for (int32_t k = elo; k < ehi; ++k) {
+            const int32_t cv = ord[npos + k];
+            const int32_t p = npair + off;
+            pr_ptr[npos + k] = p;
+            const int32_t r = S.nrec[cv];
+            const int2 q = S.rq[cv];
+            if (r > 0) { pr_q[p] = q.x; pr_c[p] = cv; rflag[q.x] = 1; }
+            if (r > 1) { pr_q[p + 1] = q.y; pr_c[p + 1] = cv; rflag[q.y] = 1; }
+            off += r;
+        }
+        __syncthreads();
+        // receivers, in list order (each flag is cleared by its owner only)
+        int32_t nr;
+        c = 0;
+        for (int32_t k = lo; k < hi; ++k) c += (rflag[A[k]] != 0);
+        off = sb_scan(c, sh, &nr);
+        for (int32_t k = lo; k < hi; ++k) {
+            const int32_t v = A[k];
+            if (rflag[v]) {
+                rv[nrecv + off++] = v;
+                rflag[v] = 0;
+            }
+        }
+        __syncthreads();
+        // contributors of each receiver
+        int32_t rlo, rhi, lc;
+        chunk(nr, rlo, rhi);
+        c = 0;
+        for (int32_t k = rlo; k < rhi; ++k) {
+            const int32_t q = rv[nrecv + k];
+            for (int32_t s = S.adj_ptr[q]; s < S.adj_ptr[q + 1]; ++s) {
+                const int32_t cv = S.nbr[s];
+                c += (cv >= 0 && S.lev[cv] == level);
+            }
+        }
+        off = sb_scan(c, sh, &lc);
+        for (int32_t k = rlo; k < rhi; ++k) {
+            const int32_t q = rv[nrecv + k];
+            rc_ptr[nrecv + k] = ncontrib + off;
+            for (int32_t s = S.adj_ptr[q]; s < S.adj_ptr[q + 1]; ++s) {
+                const int32_t cv = S.nbr[s];
+                if (cv < 0 || S.lev[cv] != level) continue;
+                const int32_t which = (S.rq[cv].x == q) ? 0 : 1;
+                ct[ncontrib + off++] = pr_ptr[pos[cv]] + which;
+            }
+        }
+        if (lc != lp) { err = 2; break; }
+        __syncthreads();
+        // structural update
+        for (int32_t k = elo; k < ehi; ++k) apply_vertex(S, ord[npos + k], nt);
+        __syncthreads();
+        // the alive list of the next level
+        int32_t nal;
+        c = 0;
+        for (int32_t k = lo; k < hi; ++k) c += (S.lev[A[k]] == -1);
+        off = sb_scan(c, sh, &nal);
+        for (int32_t k = lo; k < hi; ++k)
+            if (S.lev[A[k]] == -1) Bl[off++] = A[k];
+        if (t == 0) rec[done] = make_int4(ne, lp, nr, lc);
+        npos += ne;
+        npair += lp;
+        nrecv += nr;
+        ncontrib += lc;
+        ++level;
+        ++phase;
+        ++done;
+        int32_t *sw = A;
+        A = Bl;
+        Bl = sw;
+        na = nal;
+        __syncthreads();
+    }
+    if (t == 0) {
+        hdr[0] = done;
+        hdr[1] = na;
+        hdr[2] = err;
     }
 }
 
@@ -1682,6 +1851,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     SGP_TRY(buf_ensure(ctx, F->Dinv, sizeof(double) * 6 * n1));
     SGP_TRY(buf_ensure(ctx, F->work, sizeof(double) * 3 * n1));
     SGP_TRY(buf_ensure(ctx, F->orig_of, sizeof(int32_t) * n1));
+    SGP_TRY(buf_ensure(ctx, F->small, sizeof(int32_t) * (4 + 4 * SMALL_MAXL)));
     if (n == 0) return SGP_OK;
     SGP_CUDA(ctx, cudaMemcpyAsync(F->orig_of.p, M->orig_of.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
                                   ctx->stream));
@@ -1794,6 +1964,36 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     for (int phase = 0; na > 0; ++phase) {
         if (phase > max_phases)
             return sgp_fail(ctx, SGP_ERR_TIMEOUT, "tree_factor: contraction did not finish");
+        if (!phase1 && na <= SMALL_NA) {
+            // the short tail: all remaining levels in one block, one read-back
+            int32_t *hdr = bp<int32_t>(F->small);
+            int4 *rec = reinterpret_cast<int4 *>(hdr + 4);
+            LAUNCH(ctx, k_levels_small, 1, SB, 0, S, A, Bl, na, level, phase, rflag, ord, npos, pos, pr_ptr, pr_q,
+                   pr_c, npair, rv, nrecv, rc_ptr, ct, ncontrib, (int32_t)nt, rec, hdr);
+            std::vector<int32_t> h(4 + 4 * SMALL_MAXL);
+            SGP_TRY(read_back(ctx, h.data(), hdr, sizeof(int32_t) * h.size()));
+            if (h[2] == 1) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
+            if (h[2] == 2) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent contraction");
+            const int32_t done = h[0];
+            if (done < 1 || done > SMALL_MAXL) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: short tail failed");
+            for (int32_t l = 0; l < done; ++l) {
+                const int32_t *r = &h[4 + 4 * l];
+                npos += r[0];
+                npair += r[1];
+                nrecv += r[2];
+                ncontrib += r[3];
+                F->lvl_ptr.push_back(npos);
+                F->rl_ptr.push_back(nrecv);
+                F->pl_ptr.push_back(npair);
+                F->cl_ptr.push_back(ncontrib);
+                F->rounds++;
+                level++;
+            }
+            if (done & 1) std::swap(A, Bl);
+            na = h[1];
+            phase += done - 1;
+            continue;
+        }
         const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
         LAUNCH(ctx, k_select, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt,
                (const int32_t *)(phase1 ? pinned : nullptr));
@@ -2169,7 +2369,7 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->bm_tot, &F->bm_base, &F->bm_max, &F->bm_q, &F->bm_beg, &F->bm_cloc, &F->bm_oloc,
                     &F->bm_pbeg, &F->bm_qloc, &F->bm_Lf, &F->bm_Lf32, &F->bm_Lb, &F->bm_Lb32, &F->bm_D,
                     &F->bm_D32, &F->coop_idx, &F->ct_fo, &F->ct_eoff, &F->ct_coff, &F->ct_fq,
-                    &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx, &F->comp_int, &F->orig_of};
+                    &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx, &F->comp_int, &F->orig_of, &F->small};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete F;

@@ -242,6 +242,7 @@ struct sgp_factor {
     DBuf tail_q, tail_c, tail_b;  // local indices (position - tail_P0)
     DBuf work;      // n x 3 float64 apply workspace
     DBuf orig_of;   // n int32: the matrix's internal cell order (vectors are solved in it)
+    DBuf small;     // counts of the short-tail contraction kernel (header + per-level records)
     // local phase: the forest is cut into blocks of comp_size consecutive
     // vertices of a depth-first preorder; levels < local_levels eliminate
     // only vertices whose tree neighbours are all in their own block, and the
