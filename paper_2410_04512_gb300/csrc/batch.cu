@@ -16,8 +16,6 @@
 // batch until every instance has converged.
 #include "solver_common.cuh"
 
-template <typename T>
-sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
 
 namespace {
 

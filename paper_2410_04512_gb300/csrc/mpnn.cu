@@ -22,8 +22,6 @@
 
 #include "sgp_internal.cuh"
 
-template <typename T>
-sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
 sgp_status spmv64(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *y);
 
 namespace {

@@ -13,21 +13,10 @@
 // launches iterations in chunks and polls the `done` word between chunks.
 #include "solver_common.cuh"
 
-template <typename T>
-sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
-
 namespace {
 
 constexpr int RB = 256;        // block size of reduction kernels
 constexpr int MAXP = 4096;     // max blocks (partials) of a reduction kernel
-
-struct Scal {
-    double rho, alpha, beta, FF, stop2, rr, rz, pq;
-    long long it, maxit;
-    int done, status;
-    unsigned cnt;
-    int pad;
-};
 
 // y_i of the Appendix B.2 product for row i
 template <typename T>
@@ -378,16 +367,7 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 4) k_rz(int64_t n, co
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
     if (last_block(&sc->cnt)) {
         double rz = sum_partials<RB>(partials, gridDim.x, sh);
-        if (threadIdx.x == 0) {
-            if (!(rz > 0.0) || !isfinite(rz)) {
-                sc->status = SGP_ERR_NOT_SPD;
-                sc->done = 1;
-            } else {
-                sc->beta = rz / sc->rho;
-                sc->rho = rz;
-                sc->rz = rz;
-            }
-        }
+        if (threadIdx.x == 0) rz_finish(sc, rz);
     }
 }
 
@@ -411,16 +391,19 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 6 : 4) k_pupd(int64_t n, 
 }
 
 // FP64 residual r = F - Gamma x with |r|^2 and |F|^2 (exit check, outer loop)
-__global__ void k_resid64(Blk<double> B, const int32_t *__restrict__ row_ptr, double gamma0, int64_t n,
-                          const double *__restrict__ F, const double *__restrict__ x, double *r,
-                          double *partials, double *out2)
+// ZX: the iterate is zero, so r = F without the product.
+template <bool ZX>
+__global__ void __launch_bounds__(RB) k_resid64(Blk<double> B, const int32_t *__restrict__ row_ptr, double gamma0,
+                                                int64_t n, const double *__restrict__ F,
+                                                const double *__restrict__ x, double *r, double *partials,
+                                                double *out2)
 {
     __shared__ double sh[RB / 32];
     double rr = 0.0, ff = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double vi[3], yi[3];
-        row_product(B, row_ptr, gamma0, x, i, vi, yi);
+        double vi[3], yi[3] = {0.0, 0.0, 0.0};
+        if (!ZX) row_product(B, row_ptr, gamma0, x, i, vi, yi);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double f = F[3 * i + c];
@@ -645,7 +628,9 @@ sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *
     double *partials = reinterpret_cast<double *>(ctx->d_scratch);
     double *o2 = partials + 2 * MAXP;
     SGP_CUDA(ctx, cudaMemsetAsync(o2, 0, 32, ctx->stream));
-    LAUNCH(ctx, k_resid64, red_grid(n), RB, 0, make_blk<double>(M), bp<const int32_t>(M->row_ptr), M->gamma0,
+    unsigned Gr = 1;
+    SGP_TRY(resident_grid(ctx, (const void *)k_resid64<false>, RB, (n + RB - 1) / RB, &Gr));
+    LAUNCH(ctx, k_resid64<false>, Gr, RB, 0, make_blk<double>(M), bp<const int32_t>(M->row_ptr), M->gamma0,
            n, F, (const double *)v0, (double *)nullptr, partials, o2);
     double h[2] = {0, 0};
     SGP_TRY(read_back(ctx, h, o2, sizeof(h)));
@@ -738,6 +723,8 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     Blk<double> B64 = make_blk<double>(M);
     const int32_t *row_ptr = bp<const int32_t>(M->row_ptr);
     const unsigned G = red_grid(n);
+    unsigned Gr = 1;
+    SGP_TRY(resident_grid(ctx, (const void *)k_resid64<false>, RB, (n + RB - 1) / RB, &Gr));
     double hres[2] = {0, 0};
     if (!mixed) {
         SGP_TRY(pcg_run<double, double>(ctx, M, Fac, opts->precond, F, v, opts->x0_given, opts->tol,
@@ -760,8 +747,12 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         int outer = 0;
         for (;;) {
             SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
-            LAUNCH(ctx, k_resid64, G, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, r,
-                   partials, o2);
+            if (outer == 0 && !opts->x0_given)
+                LAUNCH(ctx, k_resid64<true>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, r,
+                       partials, o2);
+            else
+                LAUNCH(ctx, k_resid64<false>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, r,
+                       partials, o2);
             SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
             const double rr = hres[0], ff = hres[1];
             inf.rel_residual = ff > 0 ? std::sqrt(rr / ff) : 0.0;
@@ -795,11 +786,14 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         inf.iterations = total;
         inf.outer_iterations = outer;
     }
-    // true FP64 residual at exit
-    SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
-    LAUNCH(ctx, k_resid64, G, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, (double *)nullptr,
-           partials, o2);
-    SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
+    // true FP64 residual at exit (the mixed loop ends on one: the residual
+    // of the final v, from the FP64 product)
+    if (!mixed) {
+        SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
+        LAUNCH(ctx, k_resid64<false>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v,
+               (double *)nullptr, partials, o2);
+        SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
+    }
     inf.true_rel_residual = hres[1] > 0 ? std::sqrt(hres[0] / hres[1]) : 0.0;
     LAUNCH(ctx, k_to_caller<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v, v_user);
     if (info) *info = inf;

@@ -160,6 +160,11 @@ sgp_status scratch_ensure(sgp_ctx *ctx, size_t bytes);
 // the total.  `in` and `out` may alias.  Deterministic.
 sgp_status scan_exclusive_i32(sgp_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 
+// z = P^-1 w in place (internal cell order); kernels return at once when
+// *done is set.
+template <typename T>
+sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
+
 // Kernel timing hooks (no-ops unless enabled on the context).
 sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev);
 sgp_status kt_end(sgp_ctx *ctx, int kclass, cudaEvent_t ev);

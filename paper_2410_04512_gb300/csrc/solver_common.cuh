@@ -7,6 +7,30 @@
 
 namespace {
 
+// The device scalars of one PCG run (rho = r^T z, the step lengths, the
+// stopping test, the arrival counter of the last-block reductions).
+struct Scal {
+    double rho, alpha, beta, FF, stop2, rr, rz, pq;
+    long long it, maxit;
+    int done, status;
+    unsigned cnt;
+    int pad;
+};
+
+// The end of a step's r^T z reduction: beta = rz / rho, rho = rz, or a
+// breakdown when rz is not positive.
+__device__ __forceinline__ void rz_finish(Scal *sc, double rz)
+{
+    if (!(rz > 0.0) || !isfinite(rz)) {
+        sc->status = SGP_ERR_NOT_SPD;
+        sc->done = 1;
+    } else {
+        sc->beta = rz / sc->rho;
+        sc->rho = rz;
+        sc->rz = rz;
+    }
+}
+
 // One directed slot of the block-sparse rows: the symmetric 3x3 block and
 // the column.  FP64: 6 doubles (three 16-byte loads) plus the column array;
 // FP32: an 8-float record (6 floats, the column's bits, pad; two loads).
