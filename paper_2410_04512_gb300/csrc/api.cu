@@ -341,6 +341,74 @@ sgp_status graph_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l
     return SGP_OK;
 }
 
+__global__ void k_while_cond(cudaGraphConditionalHandle h, const int *done, int *bodies, int max_bodies)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int b = *bodies + 1;
+        *bodies = b;
+        cudaGraphSetConditional(h, (*done == 0 && b < max_bodies) ? 1u : 0u);
+    }
+}
+
+sgp_status graph_while_begin(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t *saved, int64_t *l0, cudaGraph_t *g,
+                             cudaGraphConditionalHandle *h)
+{
+    if (!ctx->cap_stream) SGP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    SGP_CUDA(ctx, cudaGraphCreate(g, 0));
+    cudaError_t e = cudaGraphConditionalHandleCreate(h, *g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = *h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, *g, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(*g);
+        *g = nullptr;
+        return sgp_fail(ctx, SGP_ERR_CUDA, "conditional graph setup failed: %s", cudaGetErrorString(e));
+    }
+    *saved = ctx->stream;
+    *l0 = ctx->launches;
+    ctx->stream = ctx->cap_stream;
+    ctx->capture_sink = nullptr;
+    return SGP_OK;
+}
+
+sgp_status graph_while_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l0, cudaGraph_t g,
+                           cudaGraphConditionalHandle h, const int *done, int *bodies, int max_bodies,
+                           sgp_status st)
+{
+    if (st == SGP_OK) {
+        k_while_cond<<<1, 32, 0, ctx->cap_stream>>>(h, done, bodies, max_bodies);
+        ctx->launches++;
+    }
+    cudaGraph_t body = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &body);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    ctx->stream = saved;
+    ge->kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    if (st != SGP_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (st != SGP_OK) return st;
+        return sgp_fail(ctx, SGP_ERR_CUDA, "conditional graph capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&ge->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ge->exec = nullptr;
+        cudaGetLastError();
+        return sgp_fail(ctx, SGP_ERR_CUDA, "conditional graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return SGP_OK;
+}
+
 // After a replay has completed (the caller synchronised): add the replay's
 // event-pair durations to the kernel-time totals.
 sgp_status graph_collect_timing(sgp_ctx *ctx, GraphEntry *ge)
@@ -396,6 +464,8 @@ sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
     ctx->use_graphs = (ng && ng[0] == '1') ? 0 : 1;
     const char *lpr = getenv("SGP_SPMV_LPR");
     if (lpr) ctx->spmv_lpr = atoi(lpr);
+    const char *nw = getenv("SGP_NO_WHILE");
+    ctx->use_while = (nw && nw[0] == '1') ? 0 : 1;
     const char *np = getenv("SGP_NO_PDL");
     ctx->use_pdl = (np && np[0] == '1') ? 0 : 1;
     const char *tc = getenv("SGP_TAIL_CAP");

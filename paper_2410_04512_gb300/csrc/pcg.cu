@@ -585,6 +585,37 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
         }
         return SGP_OK;
     }
+    // Without per-kernel timing the iterations run as a device-side loop:
+    // chunks of 4 iterations form the body of a conditional WHILE graph node
+    // that repeats until the done word is set (or 1024 bodies have run), so
+    // the host waits once per launch instead of once per chunk.
+    if (ctx->use_while && !ctx->timing) {
+        const int wchunk = 4, max_bodies = 1024;
+        const uint64_t wkey[] = {0x5748494c45ull, (uint64_t)sizeof(T), (uint64_t)sizeof(X), (uint64_t)precond,
+                                 (uint64_t)n, M->gen, Fac ? Fac->gen : 0ull, (uint64_t)(uintptr_t)x,
+                                 (uint64_t)(uintptr_t)r, (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q,
+                                 (uint64_t)(uintptr_t)w, (uint64_t)(uintptr_t)partials, (uint64_t)(uintptr_t)sc,
+                                 (uint64_t)(uintptr_t)jac, (uint64_t)wchunk, (uint64_t)ctx->spmv_lpr,
+                                 (uint64_t)ctx->spmv_ilp};
+        GraphEntry *we = nullptr;
+        SGP_TRY(graph_lookup(ctx, wkey, sizeof(wkey) / sizeof(wkey[0]), &we));
+        if (!we->exec &&
+            graph_capture_while(ctx, we, &sc->done, &sc->pad, max_bodies, [&]() { return iterate(wchunk); }) !=
+                SGP_OK) {
+            ctx->use_while = 0;   // not supported here: chunked graphs from now on
+            cudaGetLastError();
+        }
+        if (we->exec) {
+            for (;;) {
+                SGP_CUDA(ctx, cudaMemsetAsync(&sc->pad, 0, sizeof(int), ctx->stream));
+                SGP_CUDA(ctx, cudaGraphLaunch(we->exec, ctx->stream));
+                SGP_TRY(read_back(ctx, hs, sc, sizeof(Scal)));
+                ctx->launches += (int64_t)hs->pad * we->kernels;
+                if (hs->done) break;
+            }
+            return SGP_OK;
+        }
+    }
     // Chunks of iterations are captured once into a CUDA graph and replayed;
     // the graph is keyed by everything its nodes point at.
     const uint64_t key[] = {(uint64_t)sizeof(T), (uint64_t)sizeof(X), (uint64_t)precond, (uint64_t)n,

@@ -73,6 +73,7 @@ struct sgp_ctx {
     std::vector<std::pair<const void *, int>> occupancy;  // kernel -> resident blocks/SM
     // CUDA graphs of solver chunks (captured on a private stream)
     int use_graphs = 1;
+    int use_while = 1;      // device-side iteration loops (conditional graph nodes)
     cudaStream_t cap_stream = nullptr;
     std::vector<KtRec> *capture_sink = nullptr;
     std::vector<GraphEntry *> graphs;
@@ -90,6 +91,28 @@ sgp_status graph_begin(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t *saved, int64_
 sgp_status graph_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l0, sgp_status st);
 sgp_status graph_collect_timing(sgp_ctx *ctx, GraphEntry *ge);
 void graph_release_all(sgp_ctx *ctx);
+
+// A device-side loop: `fn` (one chunk of solver iterations) is captured as
+// the body of a conditional WHILE node; a one-thread kernel appended to the
+// body counts the executions in *bodies and keeps the loop going while *done
+// is 0 and fewer than max_bodies bodies have run in this launch.
+sgp_status graph_while_begin(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t *saved, int64_t *l0, cudaGraph_t *g,
+                             cudaGraphConditionalHandle *h);
+sgp_status graph_while_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l0, cudaGraph_t g,
+                           cudaGraphConditionalHandle h, const int *done, int *bodies, int max_bodies,
+                           sgp_status st);
+template <typename Fn>
+sgp_status graph_capture_while(sgp_ctx *ctx, GraphEntry *ge, const int *done, int *bodies, int max_bodies, Fn fn)
+{
+    cudaStream_t saved;
+    int64_t l0;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h{};
+    sgp_status st = graph_while_begin(ctx, ge, &saved, &l0, &g, &h);
+    if (st != SGP_OK) return st;
+    st = fn();
+    return graph_while_end(ctx, ge, saved, l0, g, h, done, bodies, max_bodies, st);
+}
 
 // Capture the work `fn` enqueues on ctx->stream into ge->exec.
 template <typename Fn>

@@ -8,7 +8,8 @@
 namespace {
 
 // The device scalars of one PCG run (rho = r^T z, the step lengths, the
-// stopping test, the arrival counter of the last-block reductions).
+// stopping test, the arrival counter of the last-block reductions, the body
+// count of a device-side iteration loop).
 struct Scal {
     double rho, alpha, beta, FF, stop2, rr, rz, pq;
     long long it, maxit;
