@@ -432,6 +432,37 @@ sgp_status pcg_b_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, i
         }
         return SGP_OK;
     }
+    // device-side loop (see the single-system solver): chunks of 4
+    // iterations as the body of a conditional WHILE node; the body counter
+    // sits in the flag word after n_done and all_done
+    if (ctx->use_while && !ctx->timing) {
+        const int wchunk = 4, max_bodies = 1024;
+        int *bodies = b.n_done + 3;
+        const uint64_t wkey[] = {0xBA7C5ull, (uint64_t)sizeof(T), (uint64_t)pc, (uint64_t)n, (uint64_t)nchunks,
+                                 M->gen, Fac ? Fac->gen : 0ull, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)r,
+                                 (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q, (uint64_t)(uintptr_t)w,
+                                 (uint64_t)(uintptr_t)b.sc, (uint64_t)(uintptr_t)jac, (uint64_t)wchunk,
+                                 (uint64_t)lpr};
+        GraphEntry *we = nullptr;
+        SGP_TRY(graph_lookup(ctx, wkey, sizeof(wkey) / sizeof(wkey[0]), &we));
+        if (!we->exec &&
+            graph_capture_while(ctx, we, b.all_done, bodies, max_bodies, [&]() { return iterate(wchunk); }) !=
+                SGP_OK) {
+            ctx->use_while = 0;
+            cudaGetLastError();
+        }
+        if (we->exec) {
+            int fl[4] = {0, 0, 0, 0};   // n_done, all_done, -, bodies
+            SGP_TRY(read_back(ctx, fl, b.n_done, sizeof(fl)));
+            while (!fl[1]) {
+                SGP_CUDA(ctx, cudaMemsetAsync(bodies, 0, sizeof(int), ctx->stream));
+                SGP_CUDA(ctx, cudaGraphLaunch(we->exec, ctx->stream));
+                SGP_TRY(read_back(ctx, fl, b.n_done, sizeof(fl)));
+                ctx->launches += (int64_t)fl[3] * we->kernels;
+            }
+            return SGP_OK;
+        }
+    }
     const uint64_t key[] = {0xBA7C4ull, (uint64_t)sizeof(T), (uint64_t)pc, (uint64_t)n, (uint64_t)nchunks,
                             M->gen, Fac ? Fac->gen : 0ull, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)r,
                             (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q, (uint64_t)(uintptr_t)w,
