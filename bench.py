@@ -169,9 +169,10 @@ def tree_bytes(n: int, npairs: int, nrecv: int, fp: int) -> int:
 
 def spmv_bytes(n: int, m: int, fp: int) -> int:
     """Algorithmic bytes of one product q = Gamma p with p^T q: per directed
-    slot the symmetric block (6 words) and the column (packed into an 8-word
-    record in FP32); per row the row pointer, p_i and q_i."""
-    slot = 6 * fp + 4 if fp == 8 else 32
+    slot the symmetric block (6 words) and the column in FP64, or the eq. (1)
+    form (g_perp, g_par - g_perp, u: 5 floats) and the column in FP32 (24
+    bytes); per row the row pointer, p_i and q_i."""
+    slot = 6 * fp + 4 if fp == 8 else 24
     return 2 * m * slot + n * (4 + 3 * fp + 3 * fp)
 
 
@@ -361,7 +362,8 @@ def run_gpu(args):
                    "form": "%s precision, %s preconditioner" % (args.precision, args.precond),
                    "tol": args.tol,
                    "step": "collision graph + friction blocks + spanning forest + tree factor + PCG solve",
-                   "l2": "working set > L2 (friction blocks alone %.0f MB)" % (2 * m * (48 if fp == 8 else 32) / 1e6),
+                   "l2": "working set > L2 (friction blocks alone %.0f MB: FP64 %s)"
+                         % (2 * m * (52 + (24 if fp == 4 else 0)) / 1e6, "and FP32 records" if fp == 4 else "only"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "iterations": int(round(res["iters"])), "true_rel_residual": info.true_rel_residual,
         "outer_iterations": info.outer_iterations,

@@ -113,10 +113,10 @@ __global__ void k_blocks(const int32_t *__restrict__ ij, const double *__restric
     o2[0] = make_double2(out[0], out[1]);
     o2[1] = make_double2(out[2], out[3]);
     o2[2] = make_double2(out[4], out[5]);
-    if (blk32) {
-        float4 *f4 = reinterpret_cast<float4 *>(blk32 + 8 * s);
-        f4[0] = make_float4((float)out[0], (float)out[1], (float)out[2], (float)out[3]);
-        f4[1] = make_float4((float)out[4], (float)out[5], __int_as_float(col[s]), 0.f);
+    if (blk32) {   // eq. (1) form: (g_perp, g_par - g_perp, u) and the column
+        reinterpret_cast<float4 *>(blk32)[s] =
+            make_float4((float)gq, (float)__dsub_rn(gp, gq), (float)u[0], (float)u[1]);
+        reinterpret_cast<float2 *>(blk32 + 4 * nslot)[s] = make_float2((float)u[2], __int_as_float(col[s]));
     }
 }
 
@@ -216,7 +216,7 @@ sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *G, const double 
     SGP_TRY(buf_ensure(ctx, M->cursor, sizeof(int32_t) * (n + 1)));
     float *blk32 = nullptr;
     if (precision == SGP_PREC_MIXED) {
-        SGP_TRY(buf_ensure(ctx, M->blk32, sizeof(float) * 8 * ns));
+        SGP_TRY(buf_ensure(ctx, M->blk32, sizeof(float) * 6 * std::max<int64_t>(ns, 1)));
         blk32 = bp<float>(M->blk32);
     }
     if (m > 0)

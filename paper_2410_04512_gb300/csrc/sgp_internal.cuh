@@ -214,7 +214,7 @@ struct sgp_matrix {
     DBuf row_ptr;    // n + 1 int32 over 2m directed slots, columns ascending in a row
     DBuf col;        // 2m int32
     DBuf blk;        // 2m x sym6 float64
-    DBuf blk32;      // 2m x 8 float32: sym6, col (as int bits), pad -- MIXED only
+    DBuf blk32;      // MIXED only: 2m float4 (g_perp, g_par - g_perp, u_x, u_y), then 2m float2 (u_z, col bits)
     DBuf edge_slot;  // m int32: slot of (i, j) in row i
     DBuf w;          // m float64 tree weight min(g_par, g_perp)
     DBuf slot_edge;  // 2m int32 (scratch)

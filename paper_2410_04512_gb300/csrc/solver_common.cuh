@@ -47,15 +47,27 @@ template <> struct Blk<double> {
         j = col[s];
     }
 };
+// FP32: the block is kept in the form of eq. (1), Upsilon = g_perp I +
+// (g_par - g_perp) u u^T: a 16-byte record (g_perp, g_par - g_perp, u_x, u_y)
+// and an 8-byte record (u_z, the column as int bits), 24 bytes per slot
+// instead of 32 for the six entries plus column; the entries are rebuilt in
+// registers.
 template <> struct Blk<float> {
-    const int32_t *col;
-    const float *blk;
+    const float4 *a;
+    const float2 *b;
     __device__ __forceinline__ void load(int32_t s, float *S, int32_t &j) const
     {
-        const float4 *b4 = reinterpret_cast<const float4 *>(blk + 8 * (int64_t)s);
-        float4 a = b4[0], b = b4[1];
-        S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w; S[4] = b.x; S[5] = b.y;
-        j = __float_as_int(b.z);
+        const float4 x = a[s];
+        const float2 y = b[s];
+        const float gq = x.x, dg = x.y, ux = x.z, uy = x.w, uz = y.x;
+        const float dx = dg * ux, dy = dg * uy;
+        S[0] = fmaf(dx, ux, gq);
+        S[1] = dx * uy;
+        S[2] = dx * uz;
+        S[3] = fmaf(dy, uy, gq);
+        S[4] = dy * uz;
+        S[5] = fmaf(dg * uz, uz, gq);
+        j = __float_as_int(y.y);
     }
 };
 
@@ -69,7 +81,8 @@ inline Blk<double> make_blk<double>(const sgp_matrix *M)
 template <>
 inline Blk<float> make_blk<float>(const sgp_matrix *M)
 {
-    return Blk<float>{bp<const int32_t>(M->col), bp<const float>(M->blk32)};
+    const float4 *a = bp<const float4>(M->blk32);
+    return Blk<float>{a, reinterpret_cast<const float2 *>(a + 2 * M->m)};
 }
 
 // Row i of the Appendix B.2 product accumulated with fused multiply-adds:
