@@ -167,6 +167,15 @@ def tree_bytes(n: int, npairs: int, nrecv: int, fp: int) -> int:
     return fwd + bwd
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the current kernels on the default workload and form
+# (cold, serialised launches: the tree solve's levels re-read from DRAM what
+# the previous level left in L2); other workloads report null.
+MEASURED_TRAFFIC = {
+    ("ball1m", "mixed", "tree"): {"tree": 266915072, "spmv": 137288704},
+}
+
+
 def spmv_bytes(n: int, m: int, fp: int) -> int:
     """Algorithmic bytes of one product q = Gamma p with p^T q: per directed
     slot the symmetric block (6 words) and the column in FP64, or the eq. (1)
@@ -317,24 +326,26 @@ def run_gpu(args):
     spmv_ms, spmv_n = kres["kt"][sgp.KT_SPMV]
     tree_ms, tree_n = kres["kt"][sgp.KT_TREE_SOLVE]
 
-    def roof(name, bytes_per, total_ms, launches, unit_note):
+    traffic = MEASURED_TRAFFIC.get((args.workload, args.precision, args.precond), {})
+
+    def roof(name, bytes_per, total_ms, launches, unit_note, traffic_bytes=None):
         avg_s = (total_ms / max(launches, 1)) / 1e3
         gbs = bytes_per / avg_s / 1e9 if avg_s > 0 else 0.0
         return {"kernel": name, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                "frac": round(gbs / hbm_peak, 4), "traffic": traffic_bytes,
                 "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peaks_src == "measured"
                                 else "fallback"),
                 "algorithmic_bytes_per_launch": int(bytes_per), "avg_launch_us": round(avg_s * 1e6, 2),
                 "launches": launches, "unit_of_work": unit_note}
 
     roofs = [roof("k_spmv_pq<%s>" % ("float" if fp == 4 else "double"), spmv_bytes(n, m, fp), spmv_ms, spmv_n,
-                  "one product Gamma p + p^T q over all rows")]
+                  "one product Gamma p + p^T q over all rows", traffic.get("spmv"))]
     if chosen.precond == sgp.PRECOND_TREE:
         _, levels, npairs, nrecv = chosen.H["Fh"].stats()
         roofs.append(roof("tree solve (k_tree_fwd/k_tree_tail/k_tree_bwd<%s>, %d levels)"
                           % ("float" if fp == 4 else "double", levels),
                           tree_bytes(n, npairs, nrecv, fp), tree_ms, tree_n,
-                          "one application of P^-1 (all levels)"))
+                          "one application of P^-1 (all levels)", traffic.get("tree")))
     dominant = max(range(len(roofs)), key=lambda i: [spmv_ms, tree_ms][i])
 
     # ---- the other forms on the same workload (outside the timed region) --

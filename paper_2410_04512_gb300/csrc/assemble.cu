@@ -42,10 +42,10 @@ __global__ void k_slot_place(const int32_t *__restrict__ ij, int64_t m, const in
 }
 
 // Sort each row by column (makes the layout deterministic) and record, for
-// every edge (i, j), its slot in row int_of[i].
+// every edge (i, j), its slot in row int_of[i] and in row int_of[j].
 __global__ void k_sort_rows(const int32_t *__restrict__ row_ptr, int64_t n, const int32_t *__restrict__ ij,
                             const int32_t *__restrict__ int_of, int32_t *col, int32_t *slot_edge,
-                            int32_t *edge_slot)
+                            int32_t *edge_slot, int32_t *edge_slot_j)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -64,6 +64,7 @@ __global__ void k_sort_rows(const int32_t *__restrict__ row_ptr, int64_t n, cons
     for (int32_t a = 0; a < k; ++a) {
         const int32_t e = slot_edge[b0 + a];
         if (int_of[ij[2 * e]] == (int32_t)r) edge_slot[e] = b0 + a;
+        else edge_slot_j[e] = b0 + a;
     }
 }
 
@@ -78,15 +79,16 @@ __global__ void k_edge_weight(int64_t m, const double *__restrict__ gpar, const 
     w[e] = a < b ? a : b;  // lambda_min of the block (Lemma 2.1)
 }
 
-// eq. (1) for the edge of each slot.
+// eq. (1) for each edge, written to its two slots (row i and row j carry the
+// same symmetric block).
 __global__ void k_blocks(const int32_t *__restrict__ ij, const double *__restrict__ pos,
                          const double *__restrict__ gpar, const double *__restrict__ gperp,
-                         const int32_t *__restrict__ slot_edge, const int32_t *__restrict__ col,
-                         int64_t nslot, double *blk, float *blk32, int *err)
+                         const int32_t *__restrict__ edge_slot, const int32_t *__restrict__ edge_slot_j,
+                         const int32_t *__restrict__ col, int64_t m, int64_t nslot, double *blk, float *blk32,
+                         int *err)
 {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= nslot) return;
-    int32_t e = slot_edge[s];
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m) return;
     int32_t i = ij[2 * e], j = ij[2 * e + 1];
     double dx = __dsub_rn(pos[3 * j + 0], pos[3 * i + 0]);
     double dy = __dsub_rn(pos[3 * j + 1], pos[3 * i + 1]);
@@ -109,14 +111,19 @@ __global__ void k_blocks(const int32_t *__restrict__ ij, const double *__restric
         double id = (ra[k] == rb[k]) ? 1.0 : 0.0;
         out[k] = __dadd_rn(__dmul_rn(gp, uu), __dmul_rn(gq, __dsub_rn(id, uu)));
     }
-    double2 *o2 = reinterpret_cast<double2 *>(blk + 6 * s);
-    o2[0] = make_double2(out[0], out[1]);
-    o2[1] = make_double2(out[2], out[3]);
-    o2[2] = make_double2(out[4], out[5]);
-    if (blk32) {   // eq. (1) form: (g_perp, g_par - g_perp, u) and the column
-        reinterpret_cast<float4 *>(blk32)[s] =
-            make_float4((float)gq, (float)__dsub_rn(gp, gq), (float)u[0], (float)u[1]);
-        reinterpret_cast<float2 *>(blk32 + 4 * nslot)[s] = make_float2((float)u[2], __int_as_float(col[s]));
+    const int64_t sl[2] = {edge_slot[e], edge_slot_j[e]};
+    const float4 r4 = make_float4((float)gq, (float)__dsub_rn(gp, gq), (float)u[0], (float)u[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t s = sl[h];
+        double2 *o2 = reinterpret_cast<double2 *>(blk + 6 * s);
+        o2[0] = make_double2(out[0], out[1]);
+        o2[1] = make_double2(out[2], out[3]);
+        o2[2] = make_double2(out[4], out[5]);
+        if (blk32) {   // eq. (1) form: (g_perp, g_par - g_perp, u) and the column
+            reinterpret_cast<float4 *>(blk32)[s] = r4;
+            reinterpret_cast<float2 *>(blk32 + 4 * nslot)[s] = make_float2((float)u[2], __int_as_float(col[s]));
+        }
     }
 }
 
@@ -210,6 +217,7 @@ sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *G, const double 
     SGP_TRY(buf_ensure(ctx, M->col, sizeof(int32_t) * ns));
     SGP_TRY(buf_ensure(ctx, M->blk, sizeof(double) * 6 * ns));
     SGP_TRY(buf_ensure(ctx, M->edge_slot, sizeof(int32_t) * m));
+    SGP_TRY(buf_ensure(ctx, M->edge_slot_j, sizeof(int32_t) * std::max<int64_t>(m, 1)));
     SGP_TRY(buf_ensure(ctx, M->w, sizeof(double) * m));
     SGP_TRY(buf_ensure(ctx, M->slot_edge, sizeof(int32_t) * ns));
     SGP_TRY(buf_ensure(ctx, M->lowcnt, sizeof(int32_t) * (n + 1)));
@@ -244,11 +252,13 @@ sgp_status sgp_friction_assemble(sgp_ctx *ctx, const sgp_graph *G, const double 
     SGP_TRY(scan_exclusive_i32(ctx, cnt, row_ptr, n));
     LAUNCH(ctx, k_slot_place, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, m, int_of, (const int32_t *)row_ptr, cursor,
            col, slot_edge);
+    int32_t *edge_slot_j = bp<int32_t>(M->edge_slot_j);
     LAUNCH(ctx, k_sort_rows, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)row_ptr, n, ij, int_of, col,
-           slot_edge, edge_slot);
+           slot_edge, edge_slot, edge_slot_j);
     LAUNCH(ctx, k_edge_weight, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, m, gpar, gperp, bp<double>(M->w), err);
-    LAUNCH(ctx, k_blocks, grid_for(ns, SGP_BLOCK), SGP_BLOCK, 0, ij, pos, gpar, gperp,
-           (const int32_t *)slot_edge, (const int32_t *)col, ns, bp<double>(M->blk), blk32, err);
+    LAUNCH(ctx, k_blocks, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, pos, gpar, gperp,
+           (const int32_t *)edge_slot, (const int32_t *)edge_slot_j, (const int32_t *)col, m, ns,
+           bp<double>(M->blk), blk32, err);
     int herr = 0;
     SGP_TRY(read_back(ctx, &herr, err, sizeof(int)));
     if (herr & 1)
@@ -277,7 +287,8 @@ void sgp_matrix_destroy(sgp_matrix *M)
     if (!M) return;
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&M->ij, &M->row_ptr, &M->col, &M->blk, &M->blk32, &M->edge_slot, &M->w,
-                    &M->slot_edge, &M->lowcnt, &M->cursor, &M->jac, &M->jac32, &M->orig_of, &M->int_of};
+                    &M->slot_edge, &M->lowcnt, &M->cursor, &M->jac, &M->jac32, &M->orig_of, &M->int_of,
+                    &M->edge_slot_j};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete M;

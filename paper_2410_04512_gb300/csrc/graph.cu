@@ -173,12 +173,19 @@ __device__ __forceinline__ bool contact(double4_32a pi, double4_32a pj)
 
 // One thread per cell (in grid-cell order).  EMIT = false: count the
 // contacts j > i of cell i; EMIT = true: write them at up_ptr[i] and sort.
-template <bool EMIT>
+// MODE 0: count the contacts j > i of cell i; MODE 1: write them at
+// up_ptr[i] and sort; MODE 2: count them and keep the first CAND in the
+// cell's slot of `cand` (grid-cell order), flagging a cell with more.
+constexpr int CAND = 24;
+
+template <int MODE>
 __global__ void k_contacts(int64_t n, const Grid *__restrict__ grids, const int32_t *__restrict__ inst,
                            const int32_t *__restrict__ perm, const double4_32a *__restrict__ spos,
                            const float4 *__restrict__ spos32, const int32_t *__restrict__ cell_start,
-                           int32_t *cnt, const int32_t *__restrict__ up_ptr, int32_t *ij)
+                           int32_t *cnt, const int32_t *__restrict__ up_ptr, int32_t *ij, int32_t *cand,
+                           int *overflow)
 {
+    constexpr bool EMIT = MODE == 1;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int32_t i = perm[t];
@@ -211,12 +218,14 @@ __global__ void k_contacts(int64_t n, const Grid *__restrict__ grids, const int3
                         ij[2 * (base + k)] = i;
                         ij[2 * (base + k) + 1] = j;
                     }
+                    if (MODE == 2 && k < CAND) cand[t * CAND + k] = j;
                     ++k;
                 }
             }
         }
     if (!EMIT) {
         cnt[i] = k;
+        if (MODE == 2 && k > CAND) atomicOr(overflow, 1);
     } else {
         // insertion sort of this row's j values
         for (int32_t a = 1; a < k; ++a) {
@@ -228,6 +237,26 @@ __global__ void k_contacts(int64_t n, const Grid *__restrict__ grids, const int3
             }
             ij[2 * (base + b + 1) + 1] = v;
         }
+    }
+}
+
+// The kept candidates of each cell to its rows of the edge list, sorted.
+__global__ void k_cand_copy(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ cnt,
+                            const int32_t *__restrict__ up_ptr, const int32_t *__restrict__ cand, int32_t *ij)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t i = perm[t], k = cnt[i];
+    const int64_t base = up_ptr[i];
+    for (int32_t a = 0; a < k; ++a) {
+        const int32_t v = cand[t * CAND + a];
+        ij[2 * (base + a)] = i;
+        int32_t b = a - 1;
+        while (b >= 0 && ij[2 * (base + b) + 1] > v) {
+            ij[2 * (base + b + 1) + 1] = ij[2 * (base + b) + 1];
+            --b;
+        }
+        ij[2 * (base + b + 1) + 1] = v;
     }
 }
 
@@ -351,18 +380,30 @@ static sgp_status collision_graph(sgp_ctx *ctx, int64_t n, int64_t n_inst, const
            spos, spos32);
     SGP_TRY(buf_ensure(ctx, G->int_of, sizeof(int32_t) * n));
     LAUNCH(ctx, k_inverse_perm, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, (const int32_t *)perm, bp<int32_t>(G->int_of));
-    LAUNCH(ctx, k_contacts<false>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
+    // one search: counts plus the first CAND contacts of each cell; a second
+    // search (writing straight to the edge list) only if some cell has more
+    SGP_TRY(buf_ensure(ctx, G->cand, sizeof(int32_t) * CAND * (size_t)n));
+    int *ovf = ctx->d_flags + 20;
+    SGP_CUDA(ctx, cudaMemsetAsync(ovf, 0, sizeof(int), ctx->stream));
+    LAUNCH(ctx, k_contacts<2>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
            (const int32_t *)perm, (const double4_32a *)spos, (const float4 *)spos32, (const int32_t *)cell_start,
-           cnt, (const int32_t *)nullptr, (int32_t *)nullptr);
+           cnt, (const int32_t *)nullptr, (int32_t *)nullptr, bp<int32_t>(G->cand), ovf);
     SGP_TRY(scan_exclusive_i32(ctx, cnt, up, n));
-    int32_t m32 = 0;
-    SGP_TRY(read_back(ctx, &m32, up + n, sizeof(int32_t)));
+    SGP_CUDA(ctx, cudaMemcpyAsync(ovf + 1, up + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    int32_t h[2] = {0, 0};
+    SGP_TRY(read_back(ctx, h, ovf, sizeof(h)));
+    const int32_t m32 = h[1];
     if (m32 < 0) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "collision_graph: edge count overflow");
     G->m = m32;
     SGP_TRY(buf_ensure(ctx, G->ij, sizeof(int32_t) * 2 * (size_t)G->m));
-    LAUNCH(ctx, k_contacts<true>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
-           (const int32_t *)perm, (const double4_32a *)spos, (const float4 *)spos32, (const int32_t *)cell_start,
-           cnt, (const int32_t *)up, bp<int32_t>(G->ij));
+    if (h[0] == 0)
+        LAUNCH(ctx, k_cand_copy, grid_for(n, 128), 128, 0, n, (const int32_t *)perm, (const int32_t *)cnt,
+               (const int32_t *)up, (const int32_t *)bp<int32_t>(G->cand), bp<int32_t>(G->ij));
+    else
+        LAUNCH(ctx, k_contacts<1>, grid_for(n, 128), 128, 0, n, dgrids, (const int32_t *)inst,
+               (const int32_t *)perm, (const double4_32a *)spos, (const float4 *)spos32,
+               (const int32_t *)cell_start, cnt, (const int32_t *)up, bp<int32_t>(G->ij), (int32_t *)nullptr,
+               (int *)nullptr);
     return SGP_OK;
 }
 
@@ -409,7 +450,7 @@ void sgp_graph_destroy(sgp_graph *G)
     if (!G) return;
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&G->ij, &G->up_ptr, &G->cell_id, &G->cell_cnt, &G->cell_start, &G->perm,
-                    &G->spos, &G->spos32, &G->cnt, &G->bbox, &G->inst, &G->grids, &G->int_of};
+                    &G->spos, &G->spos32, &G->cnt, &G->bbox, &G->inst, &G->grids, &G->int_of, &G->cand};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete G;

@@ -9,8 +9,10 @@
 // PCG scalars (rho, alpha, beta, convergence) live on the device; each
 // reduction kernel ends with a "last block" step that sums the per-block
 // partials in a fixed order and updates them, so no host round trip is
-// needed per iteration and results are bitwise reproducible.  The host
-// launches iterations in chunks and polls the `done` word between chunks.
+// needed per iteration and results are bitwise reproducible.  Iterations run
+// as a device-side loop (a conditional WHILE graph node over chunks of 4) or,
+// with per-kernel timing on, as replayed chunk graphs with the host polling
+// the `done` word between chunks.
 #include "solver_common.cuh"
 
 namespace {

@@ -203,6 +203,7 @@ struct sgp_graph {
     // cell-list scratch kept for reuse
     DBuf cell_id, cell_cnt, cell_start, perm, spos, spos32, cnt, bbox, inst, grids;
     DBuf int_of;   // n int32: position of each cell in grid-cell order (perm is the inverse)
+    DBuf cand;     // n x 24 int32: the first contacts of each cell found by the search
 };
 
 struct sgp_matrix {
@@ -215,7 +216,8 @@ struct sgp_matrix {
     DBuf col;        // 2m int32
     DBuf blk;        // 2m x sym6 float64
     DBuf blk32;      // MIXED only: 2m float4 (g_perp, g_par - g_perp, u_x, u_y), then 2m float2 (u_z, col bits)
-    DBuf edge_slot;  // m int32: slot of (i, j) in row i
+    DBuf edge_slot;  // m int32: slot of each edge (i, j) in row int_of[i]
+    DBuf edge_slot_j;  // m int32: slot of each edge (i, j) in row int_of[j]
     DBuf w;          // m float64 tree weight min(g_par, g_perp)
     DBuf slot_edge;  // 2m int32 (scratch)
     DBuf lowcnt, cursor;

@@ -54,6 +54,26 @@ def test_collision_graph_tiny_and_empty(ctx):
         np.testing.assert_array_equal(g.edges().cpu().numpy(), oracle.contacts(pos, radii))
 
 
+def test_collision_graph_crowded_cells(ctx):
+    """Cells with more contacts than the single search keeps per cell (24):
+    a large sphere ringed by 60 small ones (its contacts all have larger
+    indices), also with the large sphere last; the second search path must
+    give the same edge list as the oracle."""
+    rng = np.random.default_rng(7)
+    d = rng.standard_normal((60, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    ring = 3.3 * d
+    for big_first, pos, radii in [
+        (True, np.vstack([[0.0, 0, 0], ring]), np.concatenate([[3.0], np.full(60, 0.45)])),
+        (False, np.vstack([ring, [0.0, 0, 0]]), np.concatenate([np.full(60, 0.45), [3.0]])),
+    ]:
+        g = ctx.collision_graph(dev_tensor(pos), dev_tensor(radii))
+        want = oracle.contacts(pos, radii)
+        upper = np.bincount(want[:, 0], minlength=61)
+        assert (upper.max() > 24) == big_first
+        np.testing.assert_array_equal(g.edges().cpu().numpy(), want)
+
+
 def test_collision_graph_rejects_bad_input(ctx):
     pos = dev_tensor(np.zeros((3, 3)))
     with pytest.raises(sgp.SgpError) as e:
