@@ -579,6 +579,87 @@ __global__ void k_apply(Sim S, const int32_t *__restrict__ ord, int32_t p0, int3
     if (k < cnt) apply_vertex(S, ord[p0 + k], nt);
 }
 
+// ------------------------- structure: a level with its counts on the device
+// The same steps as above for a level whose counts stay on the device until
+// its end (one host read per level): grids are sized by the alive count na,
+// the kernels read the actual counts from dc = (eliminated, pairs,
+// receivers, contributor entries, alive), and the scans run over na entries
+// with zeros past the count.  The stable compaction's scatter records the
+// count of its list in *count.
+__global__ void k_scatter_list_d(const int32_t *__restrict__ A, int32_t na, const int32_t *__restrict__ flag,
+                                 const int32_t *__restrict__ off, int32_t *dst, int32_t base, int mode,
+                                 int32_t *pos, int32_t *rflag, int32_t *count)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) *count = off[na];
+    if (k >= na || !flag[k]) return;
+    int32_t v = A[k];
+    int32_t at = base + off[k];
+    dst[at] = v;
+    if (mode == 0) pos[v] = at;
+    if (mode == 1) rflag[v] = 0;
+}
+
+__global__ void k_level_nrec_d(const int32_t *__restrict__ ord, int32_t p0, int32_t bound,
+                               const int32_t *__restrict__ dc, const int32_t *__restrict__ nrec, int32_t *tmp)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < bound) tmp[k] = k < dc[0] ? nrec[ord[p0 + k]] : 0;
+}
+
+__global__ void k_level_pairs_d(const int32_t *__restrict__ ord, int32_t p0, int32_t bound, int32_t *dc,
+                                const int32_t *__restrict__ off, int32_t pair0, const int32_t *__restrict__ nrec,
+                                const int2 *__restrict__ rq, int32_t *pr_ptr, int32_t *pr_q, int32_t *pr_c,
+                                int32_t *rflag)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) dc[1] = off[bound];
+    if (k >= dc[0]) return;
+    int32_t c = ord[p0 + k];
+    int32_t p = pair0 + off[k];
+    pr_ptr[p0 + k] = p;
+    int32_t r = nrec[c];
+    int2 q = rq[c];
+    if (r > 0) { pr_q[p] = q.x; pr_c[p] = c; rflag[q.x] = 1; }
+    if (r > 1) { pr_q[p + 1] = q.y; pr_c[p + 1] = c; rflag[q.y] = 1; }
+}
+
+template <bool FILL>
+__global__ void k_contrib_d(Sim S, const int32_t *__restrict__ rv, int32_t r0, int32_t bound, int32_t *dc,
+                            int32_t level, const int32_t *__restrict__ pos, const int32_t *__restrict__ pr_ptr,
+                            int32_t *count, const int32_t *__restrict__ off, int32_t ct0, int32_t *rc_ptr,
+                            int32_t *ct)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (FILL && k == 0) dc[3] = off[bound];
+    if (k >= bound) return;
+    if (k >= dc[2]) {
+        if (!FILL) count[k] = 0;
+        return;
+    }
+    int32_t q = rv[r0 + k];
+    int32_t c_n = 0;
+    int32_t at = FILL ? ct0 + off[k] : 0;
+    if (FILL) rc_ptr[r0 + k] = at;
+    for (int32_t s = S.adj_ptr[q]; s < S.adj_ptr[q + 1]; ++s) {
+        int32_t c = S.nbr[s];
+        if (c < 0 || S.lev[c] != level) continue;
+        if (FILL) {
+            int32_t which = (S.rq[c].x == q) ? 0 : 1;
+            ct[at + c_n] = pr_ptr[pos[c]] + which;
+        }
+        ++c_n;
+    }
+    if (!FILL) count[k] = c_n;
+}
+
+__global__ void k_apply_d(Sim S, const int32_t *__restrict__ ord, int32_t p0, const int32_t *__restrict__ dc,
+                          int32_t nt)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < dc[0]) apply_vertex(S, ord[p0 + k], nt);
+}
+
 // ------------------------------------------------- structure: the short tail
 // Once the alive list is short (at most SMALL_NA vertices) the remaining
 // levels run in one block of SB threads: the same selection, the same stable
@@ -1798,6 +1879,19 @@ static sgp_status compact(sgp_ctx *ctx, const int32_t *A, int32_t na, int mode, 
     return SGP_OK;
 }
 
+// compact() with the count left on the device (*count).
+static sgp_status compact_dev(sgp_ctx *ctx, const int32_t *A, int32_t na, int mode, int32_t level,
+                              const int32_t *lev, int32_t *rflag, int32_t *flag, int32_t *off, int32_t *dst,
+                              int32_t base, int32_t *pos, int32_t *count)
+{
+    LAUNCH(ctx, k_flags, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, A, na, mode, level, lev,
+           (const int32_t *)rflag, flag);
+    SGP_TRY(scan_exclusive_i32(ctx, flag, off, na));
+    LAUNCH(ctx, k_scatter_list_d, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, A, na, (const int32_t *)flag,
+           (const int32_t *)off, dst, base, mode, pos, rflag, count);
+    return SGP_OK;
+}
+
 extern "C" {
 
 sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sgp_factor **out)
@@ -1851,7 +1945,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     SGP_TRY(buf_ensure(ctx, F->Dinv, sizeof(double) * 6 * n1));
     SGP_TRY(buf_ensure(ctx, F->work, sizeof(double) * 3 * n1));
     SGP_TRY(buf_ensure(ctx, F->orig_of, sizeof(int32_t) * n1));
-    SGP_TRY(buf_ensure(ctx, F->small, sizeof(int32_t) * (4 + 4 * SMALL_MAXL)));
+    SGP_TRY(buf_ensure(ctx, F->small, sizeof(int32_t) * (4 + 4 * SMALL_MAXL + 8)));
     if (n == 0) return SGP_OK;
     SGP_CUDA(ctx, cudaMemcpyAsync(F->orig_of.p, M->orig_of.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
                                   ctx->stream));
@@ -1995,6 +2089,47 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
             continue;
         }
         const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
+        if (!phase1) {
+            // a large level: every count stays on the device until one read at its end
+            int32_t *dc = bp<int32_t>(F->small) + 4 + 4 * SMALL_MAXL;
+            const unsigned gn = grid_for(na, SGP_BLOCK);
+            LAUNCH(ctx, k_select, gn, SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt, (const int32_t *)nullptr);
+            F->rounds++;
+            SGP_TRY(compact_dev(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, dc + 0));
+            LAUNCH(ctx, k_level_nrec_d, gn, SGP_BLOCK, 0, (const int32_t *)ord, npos, na, (const int32_t *)dc,
+                   (const int32_t *)nrec, flag);
+            SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, na));
+            LAUNCH(ctx, k_level_pairs_d, gn, SGP_BLOCK, 0, (const int32_t *)ord, npos, na, dc, (const int32_t *)tmp,
+                   npair, (const int32_t *)nrec, (const int2 *)S.rq, pr_ptr, pr_q, pr_c, rflag);
+            SGP_TRY(compact_dev(ctx, A, na, 1, level, lev, rflag, flag, tmp, rv, nrecv, pos, dc + 2));
+            LAUNCH(ctx, k_contrib_d<false>, gn, SGP_BLOCK, 0, S, (const int32_t *)rv, nrecv, na, dc, level,
+                   (const int32_t *)pos, (const int32_t *)pr_ptr, flag, (const int32_t *)nullptr, 0,
+                   (int32_t *)nullptr, (int32_t *)nullptr);
+            SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, na));
+            LAUNCH(ctx, k_contrib_d<true>, gn, SGP_BLOCK, 0, S, (const int32_t *)rv, nrecv, na, dc, level,
+                   (const int32_t *)pos, (const int32_t *)pr_ptr, flag, (const int32_t *)tmp, ncontrib, rc_ptr, ct);
+            LAUNCH(ctx, k_apply_d, gn, SGP_BLOCK, 0, S, (const int32_t *)ord, npos, (const int32_t *)dc,
+                   (int32_t)nt);
+            level++;
+            SGP_TRY(compact_dev(ctx, A, na, 2, level, lev, rflag, flag, tmp, Bl, 0, pos, dc + 4));
+            int32_t h[5] = {0, 0, 0, 0, 0};
+            SGP_TRY(read_back(ctx, h, dc, sizeof(h)));
+            const int32_t ne = h[0], lp = h[1], nr = h[2], lc = h[3], nalive = h[4];
+            if (ne == 0) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
+            if (lc != lp)
+                return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent contraction (%d/%d)", lc, lp);
+            npos += ne;
+            npair += lp;
+            nrecv += nr;
+            ncontrib += lc;
+            F->lvl_ptr.push_back(npos);
+            F->rl_ptr.push_back(nrecv);
+            F->pl_ptr.push_back(npair);
+            F->cl_ptr.push_back(ncontrib);
+            std::swap(A, Bl);
+            na = nalive;
+            continue;
+        }
         LAUNCH(ctx, k_select, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt,
                (const int32_t *)(phase1 ? pinned : nullptr));
         F->rounds++;

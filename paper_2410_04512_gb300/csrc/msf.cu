@@ -176,12 +176,13 @@ sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *M, sgp_tree **o
         SGP_TRY(scan_exclusive_i32(ctx, keep, off, nlive));
         LAUNCH(ctx, k_compact, grid_for(nlive, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)liveA,
                (const int32_t *)keep, (const int32_t *)off, nlive, liveB);
-        int32_t h[2] = {0, 0};
-        SGP_TRY(read_back(ctx, &h[0], off + nlive, sizeof(int32_t)));
-        SGP_TRY(read_back(ctx, &h[1], any, sizeof(int)));
+        // the live count next to the hook flag: one read per round
+        SGP_CUDA(ctx, cudaMemcpyAsync(any + 1, off + nlive, sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
+        int h[2] = {0, 0};
+        SGP_TRY(read_back(ctx, h, any, sizeof(h)));
         std::swap(liveA, liveB);
-        nlive = h[0];
-        if (!h[1]) break;
+        nlive = h[1];
+        if (!h[0]) break;
     }
     // tree edge ids, ascending
     LAUNCH(ctx, k_u8_to_i32, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, (const uint8_t *)intree, keep, m);

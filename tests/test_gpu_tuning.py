@@ -102,3 +102,46 @@ def test_autotune_batch(ctx):
     v1, infos = ctx.pcg_solve_batched(M, Fh, off, F, tol=1e-10)
     assert all(i.status == 0 for i in infos)
     assert rel_err(v1.cpu().numpy(), v0.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [sgp.PREC_F64, sgp.PREC_MIXED])
+def test_device_loop_matches_chunk_graphs(ctx, prec):
+    """The iterations run as a device-side loop (conditional WHILE graph node)
+    unless per-kernel timing is on, which replays plain chunk graphs and
+    polls between chunks.  Same kernels in the same order: the iterates and
+    the iteration counts must agree bit for bit, single and batched."""
+    c = workloads.ball(n=20000, seed=2003, gamma0=1e-3)
+    s = GpuSystem(ctx, c, precision=prec)
+    F = dev_tensor(c.forces())
+    runs = []
+    for timing in (False, True, False):
+        ctx.set_kernel_timing(timing)
+        v, info = ctx.pcg_solve(s.M, s.Fac, F, tol=1e-9, precision=prec)
+        runs.append((v.cpu().numpy(), info.iterations, info.true_rel_residual))
+    ctx.set_kernel_timing(False)
+    for v, it, res in runs[1:]:
+        np.testing.assert_array_equal(v, runs[0][0])
+        assert it == runs[0][1] and res == runs[0][2]
+    assert runs[0][2] <= 1e-9
+
+
+def test_device_loop_matches_chunk_graphs_batched(ctx):
+    sizes = [1500, 2600, 800, 3100]
+    cells = [workloads.batch_instance(n, k) for k, n in enumerate(sizes)]
+    off = workloads.sphere_offsets(np.array(sizes))
+    pos = dev_tensor(np.concatenate([cl.pos for cl in cells]))
+    radii = dev_tensor(np.concatenate([cl.radii for cl in cells]))
+    g = ctx.collision_graph_batched(off, pos, radii)
+    tab = dev_tensor(workloads.gamma_table(0.1, 10.0))
+    gp, gq = workloads.pair_gamma_torch(4100, g.edges(), tab, tab)
+    M = ctx.friction_assemble(g, pos, gp.contiguous(), gq.contiguous(), 1e-2, sgp.PREC_MIXED)
+    Fh = ctx.tree_factor(M, ctx.max_spanning_tree(M))
+    F = dev_tensor(np.random.default_rng(5).standard_normal((int(off[-1]), 3)))
+    runs = []
+    for timing in (False, True):
+        ctx.set_kernel_timing(timing)
+        v, infos = ctx.pcg_solve_batched(M, Fh, off, F, tol=1e-9, precision=sgp.PREC_MIXED)
+        runs.append((v.cpu().numpy(), [i.iterations for i in infos]))
+    ctx.set_kernel_timing(False)
+    np.testing.assert_array_equal(runs[1][0], runs[0][0])
+    assert runs[1][1] == runs[0][1]
