@@ -930,8 +930,6 @@ __global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n)
 // Programmatic dependent launch: a level kernel lets the next one start its
 // prologue at once (launch_dependents) and waits for the previous level's
 // results (wait) only before it touches the solution vector.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Forward substitution of one level: each receiver q subtracts
 // sum_c L_qc w_c over this level's contributors c (fixed order).  Lf holds

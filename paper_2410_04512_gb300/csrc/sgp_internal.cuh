@@ -326,6 +326,15 @@ static inline sgp_status sgp_launch_pdl(sgp_ctx *ctx, const char *name, void (*k
         return sgp_fail(ctx, SGP_ERR_CUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
     return SGP_OK;
 }
+// Programmatic dependent launch: a kernel launched with LAUNCH_PDL may start
+// while the previous kernel in the stream is still running; pdl_wait()
+// returns once that kernel has completed and its memory is visible, so
+// everything that reads what earlier kernels wrote comes after it.
+// pdl_trigger() lets the next kernel start early.  Both are no-ops for a
+// plain launch.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 #define LAUNCH_PDL(ctx, kern, grid, block, smem, ...) \
     SGP_TRY(sgp_launch_pdl((ctx), #kern, kern, dim3(grid), dim3(block), (smem), __VA_ARGS__))
 
