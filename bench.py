@@ -167,6 +167,22 @@ def tree_bytes(n: int, npairs: int, nrecv: int, fp: int) -> int:
     return fwd + bwd
 
 
+def vector_bytes(n: int, fp: int, precond: str) -> int:
+    """Algorithmic bytes of the vector kernels of one PCG iteration (3n
+    entries each): the update reads p, q, r, x and writes x, r and the
+    preconditioner's input w; the tree form adds r^T z (reads r, w) and the
+    direction update p = z + beta p (reads z, p, writes p)."""
+    e = 3 * n * fp
+    return 7 * e + (2 * e + 3 * e if precond == "tree" else 3 * e)
+
+
+def outer_bytes(n: int, m: int) -> int:
+    """Algorithmic bytes of one FP64 refinement step of the mixed solve: the
+    FP64 residual (blocks and columns, row pointer, v, F, r) and the FP32
+    scaling and accumulation of the inner correction."""
+    return 2 * m * 52 + n * (4 + 4 * 24) + n * (24 + 12 + 12) + n * (12 + 24 + 24)
+
+
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the current kernels on the default workload and form
 # (cold, serialised launches: the tree solve's levels re-read from DRAM what
@@ -347,6 +363,16 @@ def run_gpu(args):
                           tree_bytes(n, npairs, nrecv, fp), tree_ms, tree_n,
                           "one application of P^-1 (all levels)", traffic.get("tree")))
     dominant = max(range(len(roofs)), key=lambda i: [spmv_ms, tree_ms][i])
+    # the solve against the bandwidth roofline: algorithmic bytes of all its
+    # iterations (product + tree solve + vector kernels) and refinement steps
+    it_bytes = spmv_bytes(n, m, fp) + vector_bytes(n, fp, args.precond)
+    if chosen.precond == sgp.PRECOND_TREE:
+        it_bytes += tree_bytes(n, npairs, nrecv, fp)
+    solve_bytes = res["iters"] * it_bytes + (info.outer_iterations + 1) * outer_bytes(n, m) * (fp == 4)
+    roof_ms = solve_bytes / (hbm_peak * 1e9) * 1e3
+    solve_roof = {"bytes": int(solve_bytes), "bytes_per_inner_iteration": int(it_bytes),
+                  "roof_ms": round(roof_ms, 3), "measured_ms": round(res["solve_ms"], 3),
+                  "frac": round(roof_ms / res["solve_ms"], 4), "peak_gbs": hbm_peak}
 
     # ---- the other forms on the same workload (outside the timed region) --
     forms = {}
@@ -384,6 +410,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": F.numel() * 8, "steps": e2e_steps},
         "gpu_launches": int(res["launches"]),
         "roofline": roofs[dominant], "roofline_other": [r for i, r in enumerate(roofs) if i != dominant],
+        "solve_roofline": solve_roof,
         "time_share_ms": {"spmv": round(spmv_ms, 2), "tree_solve": round(tree_ms, 2),
                           "timed": round(kres["elapsed"] * 1e3, 2),
                           "note": "kernel events over a repeat of the timed steps (%d steps, %.2f solves/s "
