@@ -22,6 +22,10 @@
  *   values (sizes, solve statistics) synchronise that stream.
  * - Every call returns an sgp_status; on failure sgp_last_error(ctx) holds a
  *   one-line reason.  No call aborts the process.
+ * - A context is used by one host thread at a time.  A handle may be read by
+ *   calls on several contexts, but not while calls that write it, or that
+ *   use its workspace (sgp_tree_apply uses the factor's), overlap on the GPU;
+ *   the solvers' workspace belongs to the context.
  */
 #ifndef SGP_H
 #define SGP_H
