@@ -25,7 +25,9 @@
  * - A context is used by one host thread at a time.  A handle may be read by
  *   calls on several contexts, but not while calls that write it, or that
  *   use its workspace (sgp_tree_apply uses the factor's), overlap on the GPU;
- *   the solvers' workspace belongs to the context.
+ *   the block-Jacobi inverses are written into the matrix by its first
+ *   block-Jacobi solve or warm start.  The solvers' workspace belongs to the
+ *   context.
  */
 #ifndef SGP_H
 #define SGP_H
