@@ -242,7 +242,7 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *matrix, const s
 /* ---- learned warm start (no counterpart in the paper) -----------------------
  * A message-passing network over the collision graph predicts the initial
  * guess v0 of the PCG of Section 1.1; the solver's own iteration count
- * judges the prediction.  Width 64, three message-passing layers, BF16
+ * measures the prediction.  Width 64, three message-passing layers, BF16
  * weights (round-to-nearest-even copies of FP32 master weights), FP32
  * activations and accumulation:
  *   basis  b0 = D^-1 F (block Jacobi), b1 = P^-1 F (spanning-forest factor),

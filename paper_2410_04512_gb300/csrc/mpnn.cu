@@ -1,6 +1,6 @@
 // mpnn.cu -- learned warm start: a message-passing network over the
 // collision graph that predicts the PCG initial guess v0 (the paper has no
-// learned component; the solver's own iterations judge the prediction).
+// learned component; the solver's own iterations measure the prediction).
 //
 // Network (width 64, 3 message-passing layers, BF16 weights, FP32
 // activations and accumulation):

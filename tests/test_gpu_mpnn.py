@@ -1,7 +1,7 @@
 """Parity of the warm-start network's CUDA kernels (called through the C ABI)
 with the CPU oracle: forward pass, loss and gradients for both losses, Adam,
 the minimal-residual scaling and the acceptance test; then online training
-on a short time-stepping sequence, judged by the solver itself.
+on a short time-stepping sequence, evaluated by the solver itself.
 
 Tolerances.  Both sides use the same BF16 weights (round-to-nearest-even of
 the same FP32 values).  The GPU keeps activations in FP32 with FP32
@@ -233,7 +233,7 @@ def test_bad_arguments_are_rejected(ctx):
 def _sequence(ctx, n=4000, train_steps=16, test_steps=6, epochs=8, lr=2e-3):
     """Time stepping x <- x + v dt with overlap springs and fresh active
     noise; the network is trained on the solver's solutions of the first
-    steps and judged on the rest by the iterations of PCG to 1e-8."""
+    steps and evaluated on the rest by the iterations of PCG to 1e-8."""
     c = workloads.ball(n=n, seed=2100, gamma0=1e-3)
     pos = dev_tensor(c.pos)
     radii = dev_tensor(c.radii)
