@@ -146,3 +146,27 @@ def test_batched_rejects_edges_between_instances(ctx):
     with pytest.raises(sgp.SgpError) as e:
         ctx.pcg_solve_batched(M, None, off, dev_tensor(np.ones((int(off[-1]), 3))), precond=sgp.PRECOND_NONE)
     assert e.value.code == sgp.ERR_INVALID_ARG
+
+
+def test_batched_rejects_a_cell_order_that_mixes_instances(ctx):
+    """Two instances far apart (no edge between them) assembled on a graph of
+    the whole union: the graph's grid-cell order interleaves them, which the
+    batched solver cannot use, so it must refuse rather than mix them; the
+    same union solved as one system is fine."""
+    cells, off, pos, radii = make_batch([700, 900])
+    pos = pos.copy()
+    lo = int(off[1])
+    pos[lo:, 2] += 1000.0     # far away along the grid's fastest axis: their cells interleave
+    pos_d, radii_d = dev_tensor(pos), dev_tensor(radii)
+    g = ctx.collision_graph(pos_d, radii_d)
+    ij = g.edges()
+    assert not ((ij[:, 0] < lo) & (ij[:, 1] >= lo)).any()
+    t = dev_tensor(workloads.gamma_table(0.1, 10.0))
+    gp, gq = workloads.pair_gamma_torch(SEED, ij, t, t)
+    M = ctx.friction_assemble(g, pos_d, gp.contiguous(), gq.contiguous(), 1e-2)
+    F = dev_tensor(np.ones((int(off[-1]), 3)))
+    with pytest.raises(sgp.SgpError) as e:
+        ctx.pcg_solve_batched(M, None, off, F, precond=sgp.PRECOND_NONE)
+    assert e.value.code == sgp.ERR_INVALID_ARG
+    v, info = ctx.pcg_solve(M, None, F, tol=1e-10, precond=sgp.PRECOND_NONE)
+    assert info.status == 0 and info.true_rel_residual <= 1e-10
