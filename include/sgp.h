@@ -206,6 +206,13 @@ sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *factor, const double *
  * (vertex, level) of the forward substitution.  Any pointer may be NULL. */
 sgp_status sgp_factor_info(const sgp_factor *factor, int32_t *rounds, int32_t *levels,
                            int64_t *l_blocks, int64_t *receiver_entries);
+/* Layout of the factor's binned solve: number of bins, vertices of the top
+ * part (solved by one thread block), the subtree bound, and whether the FP32
+ * and FP64 applications use it (1) or run one launch per contraction level
+ * (0: the layout is off or does not fit in shared memory).  Any pointer may
+ * be NULL. */
+sgp_status sgp_factor_layout(const sgp_factor *factor, int32_t *bins, int32_t *top, int32_t *bin_cap,
+                             int32_t *fp32, int32_t *fp64);
 void sgp_factor_destroy(sgp_factor *factor);
 
 /* ---- Section 1.1: preconditioned conjugate gradients ------------------------
@@ -330,7 +337,11 @@ typedef struct {
                             when it starts before the one-block tail and fits;
                             0 (none, default) or 256..16777216; read when a
                             factor is built */
-    int32_t reserved;
+    int32_t bin_cap;     /* the tree solve's thread-block bins: contraction subtrees
+                            of at most bin_cap vertices are solved by one thread
+                            block each (three launches per application); 0 =
+                            default (1024), -1 = off (one launch per contraction
+                            level), else 64..8192; read when a factor is built */
     double ms_per_iteration; /* sgp_autotune: the winning objective (ms per PCG
                                 iteration, or per factor build + solve); 0 from
                                 sgp_get_tuning */

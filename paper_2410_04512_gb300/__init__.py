@@ -46,10 +46,10 @@ class SolveOpts(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("spmv_lpr", ctypes.c_int32), ("tail_cap", ctypes.c_int32), ("batch_chunk", ctypes.c_int32),
                 ("comp_size", ctypes.c_int32), ("coop_cap", ctypes.c_int32), ("spmv_ilp", ctypes.c_int32),
-                ("ctail_cap", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
+                ("ctail_cap", ctypes.c_int32), ("bin_cap", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SolveInfo(ctypes.Structure):
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "sgp_set_kernel_timing": ([P, I32], I32),
         "sgp_kernel_time": ([P, I32, ctypes.POINTER(D), ctypes.POINTER(I64), I32], I32),
         "sgp_launch_count": ([P, ctypes.POINTER(I64), I32], I32),
+        "sgp_factor_layout": ([P] + [ctypes.POINTER(I32)] * 5, I32),
         "sgp_get_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "sgp_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "sgp_autotune": ([P, P, P, PP, I64, P, P, ctypes.POINTER(SolveOpts), I32, ctypes.POINTER(Tuning)], I32),
@@ -220,6 +221,13 @@ class Factor(_Handle):
         self.ctx._ok(_lib.sgp_factor_info(self.ptr, ctypes.byref(r), ctypes.byref(l), ctypes.byref(nb),
                                           ctypes.byref(nr)))
         return r.value, l.value, nb.value, nr.value
+
+    def layout(self) -> dict:
+        """The binned solve's layout: bins, top vertices, subtree bound, and
+        whether the FP32 / FP64 applications use it."""
+        v = [ctypes.c_int32() for _ in range(5)]
+        self.ctx._ok(_lib.sgp_factor_layout(self.ptr, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("bins", "top", "bin_cap", "fp32", "fp64"), (x.value for x in v)))
 
 
 class Mpnn(_Handle):
@@ -416,9 +424,9 @@ class Context:
         return t.as_dict()
 
     def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, comp_size: int = 0,
-                   coop_cap: int = 0, spmv_ilp: int = 0, ctail_cap: int = 0):
+                   coop_cap: int = 0, spmv_ilp: int = 0, ctail_cap: int = 0, bin_cap: int = 0):
         """Set the launch-shape knobs (the defaults are the library's)."""
-        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, coop_cap, spmv_ilp, ctail_cap, 0, 0.0)
+        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, coop_cap, spmv_ilp, ctail_cap, bin_cap, 0.0)
         self._ok(_lib.sgp_set_tuning(self.ptr, ctypes.byref(t)))
 
     def autotune(self, M: Matrix, T: Tree | None, Fh: Factor | None, F: torch.Tensor, offsets=None,

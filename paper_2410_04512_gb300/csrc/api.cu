@@ -470,6 +470,10 @@ sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
     ctx->use_pdl = (np && np[0] == '1') ? 0 : 1;
     const char *tc = getenv("SGP_TAIL_CAP");
     if (tc) ctx->tail_cap = atoi(tc);
+    const char *bc = getenv("SGP_BIN_CAP");
+    if (bc) ctx->bin_cap = atoi(bc);
+    const char *nf = getenv("SGP_NO_FUSE");
+    if (nf && atoi(nf)) ctx->fused = 0;
     if (scratch_ensure(ctx, 1 << 20) != SGP_OK || cudaMalloc(&ctx->d_flags, 4096) != cudaSuccess ||
         cudaMemset(ctx->d_flags, 0, 4096) != cudaSuccess) {
         cudaGetLastError();

@@ -1724,6 +1724,7 @@ static Tail tail_of(const sgp_factor *F)
 template <typename T>
 sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done)
 {
+    if (bins_usable<T>(F)) return bins_apply<T>(ctx, F, w, done);
     const bool f64 = sizeof(T) == 8;
     const T *L = reinterpret_cast<const T *>(f64 ? F->L.p : F->L32.p);
     const T *Lf = reinterpret_cast<const T *>(f64 ? F->Lf.p : F->Lf32.p);
@@ -2459,6 +2460,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     int herr = 0;
     SGP_TRY(read_back(ctx, &herr, err, sizeof(int)));
     if (herr) return sgp_fail(ctx, SGP_ERR_NOT_SPD, "tree_factor: a pivot block is not positive definite");
+    SGP_TRY(bins_build(ctx, F, M));
     return SGP_OK;
 }
 
@@ -2473,6 +2475,7 @@ sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *F, const double *b, do
     LAUNCH(ctx, k_to_internal<double>, grid_for(F->n, SGP_BLOCK), SGP_BLOCK, 0, F->n, orig_of, b, wi);
     SGP_TRY(tree_apply_inplace<double>(ctx, F, wi, nullptr));
     LAUNCH(ctx, k_to_caller<double>, grid_for(F->n, SGP_BLOCK), SGP_BLOCK, 0, F->n, orig_of, (const double *)wi, x);
+    if (bins_usable<double>(F)) SGP_TRY(bins_check(ctx, F));
     return SGP_OK;
 }
 
@@ -2484,6 +2487,18 @@ sgp_status sgp_factor_info(const sgp_factor *F, int32_t *rounds, int32_t *levels
     if (levels) *levels = F->levels;
     if (l_blocks) *l_blocks = F->npairs;
     if (receiver_entries) *receiver_entries = F->rl_ptr.empty() ? 0 : F->rl_ptr.back();
+    return SGP_OK;
+}
+
+sgp_status sgp_factor_layout(const sgp_factor *F, int32_t *bins, int32_t *top, int32_t *bin_cap, int32_t *fp32,
+                             int32_t *fp64)
+{
+    if (!F) return SGP_ERR_INVALID_ARG;
+    if (bins) *bins = F->bl.nb;
+    if (top) *top = F->bl.nt;
+    if (bin_cap) *bin_cap = F->bl.bmax;
+    if (fp32) *fp32 = F->bl.ok32;
+    if (fp64) *fp64 = F->bl.ok64;
     return SGP_OK;
 }
 
@@ -2505,6 +2520,19 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx, &F->comp_int, &F->orig_of, &F->small};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
+    BinLayout &B = F->bl;
+    DBuf *bb[] = {&B.hdr, &B.elev, &B.vlev, &B.gvert, &B.er, &B.ec, &B.cl, &B.kl, &B.ks, &B.pr, &B.pref, &B.zi,
+                  &B.tv, &B.tint, &B.c_src, &B.k_src, &B.p_src, &B.d_src, &B.t_src, &B.tD_src, &B.part, &B.err,
+                  &B.i_of_t, &B.t_of_i, &B.rpt, &B.ma32, &B.mb32, &B.m64, &B.mc64};
+    for (DBuf *b : bb)
+        if (b->p) cudaFree(b->p);
+    for (int k = 0; k < 2; ++k) {
+        DBuf *nb[] = {&B.cL[k], &B.kL[k], &B.pL[k], &B.D[k], &B.tL[k], &B.tD[k], &B.ly[k], &B.lsum[k], &B.tw[k]};
+        for (DBuf *b : nb)
+            if (b->p) cudaFree(b->p);
+    }
+    for (DBuf &b : B.scr)
+        if (b.p) cudaFree(b.p);
     delete F;
 }
 

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? (ILP == 1 ? 8 : 4) : (ILP
                 sc->done = 1;
             } else {
                 sc->alpha = sc->rho / pq;
+                sc->xpend = 1;
             }
         }
     }
@@ -392,6 +393,38 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 6 : 4) k_pupd(int64_t n, 
     for (int64_t k = np * K + g0; k < n3; k += gs) p[k] = fma(beta, p[k], w[k]);
 }
 
+// End of a fused PCG step (after the binned tree solve has set beta, or
+// stopped): x += alpha p, and p = z + beta p while the solve goes on.  Runs
+// once per step: the last block clears the pending flag that the product set.
+template <typename T>
+__global__ void __launch_bounds__(RB) k_pupd_x(int64_t n, T *x, T *p, const T *__restrict__ z, Scal *sc)
+{
+    if (!sc->xpend) return;
+    constexpr int K = Pack<T>::K;
+    const T a = (T)sc->alpha, beta = (T)sc->beta;
+    const bool live = !sc->done;
+    const int64_t n3 = 3 * n, np = n3 / K;
+    const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = g0; i < np; i += gs) {
+        Pack<T> xv = reinterpret_cast<const Pack<T> *>(x)[i];
+        Pack<T> pv = reinterpret_cast<const Pack<T> *>(p)[i];
+        Pack<T> zv = reinterpret_cast<const Pack<T> *>(z)[i];
+#pragma unroll
+        for (int e = 0; e < K; ++e) {
+            xv.v[e] = fma(a, pv.v[e], xv.v[e]);
+            pv.v[e] = fma(beta, pv.v[e], zv.v[e]);
+        }
+        reinterpret_cast<Pack<T> *>(x)[i] = xv;
+        if (live) reinterpret_cast<Pack<T> *>(p)[i] = pv;
+    }
+    for (int64_t k = np * K + g0; k < n3; k += gs) {
+        const T pk = p[k];
+        x[k] = fma(a, pk, x[k]);
+        if (live) p[k] = fma(beta, pk, z[k]);
+    }
+    if (last_block(&sc->cnt) && threadIdx.x == 0) sc->xpend = 0;
+}
+
 // FP64 residual r = F - Gamma x with |r|^2 and |F|^2 (exit check, outer loop)
 // ZX: the iterate is zero, so r = F without the product.
 template <bool ZX>
@@ -500,16 +533,29 @@ static unsigned red_grid(int64_t n)
 }
 
 
-// One PCG run in precision T on Gamma(T) x = F(T).  X is the type of the
-// iterate x.  Returns the device scalar block's final state in *hs.
-template <typename T, typename X>
-sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int precond,
-                   const T *F, X *x, int x_given, double tol, int64_t maxit, T *r, T *p, T *q, T *w,
-                   double *partials, Scal *sc, Scal *hs)
+// The factor's copy of the matrix rows in tree order.
+template <typename T>
+Blk<T> tree_blk(const sgp_factor *F);
+template <>
+inline Blk<double> tree_blk<double>(const sgp_factor *F)
 {
-    const int64_t n = M->n;
-    Blk<T> B = make_blk<T>(M);
-    const int32_t *row_ptr = bp<const int32_t>(M->row_ptr);
+    return Blk<double>{bp<const int32_t>(F->bl.mc64), bp<const double>(F->bl.m64)};
+}
+template <>
+inline Blk<float> tree_blk<float>(const sgp_factor *F)
+{
+    return Blk<float>{bp<const float4>(F->bl.ma32), bp<const float2>(F->bl.mb32)};
+}
+
+// One PCG run in precision T on Gamma(T) x = F(T) over n rows of the
+// product B/row_ptr.  X is the type of the iterate x.  `tree`: the vectors
+// are in the binned solve's tree order and every step is fused around it.
+// Returns the device scalar block's final state in *hs.
+template <typename T, typename X>
+sgp_status pcg_core(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int precond, Blk<T> B,
+                    const int32_t *row_ptr, int64_t n, bool tree, const T *F, X *x, int x_given, double tol,
+                    int64_t maxit, T *r, T *p, T *q, T *w, double *partials, Scal *sc, Scal *hs)
+{
     const T g0 = (T)M->gamma0;
     const T *jac = nullptr;
     if (precond == SGP_PRECOND_BLOCK_JACOBI) {
@@ -538,7 +584,8 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
     if (hs->done) return SGP_OK;
     if (precond == SGP_PRECOND_TREE) {
         SGP_TRY(kt_begin(ctx, SGP_KT_TREE_SOLVE, &ev));
-        SGP_TRY(tree_apply_inplace<T>(ctx, Fac, w, &sc->done));
+        if (tree) SGP_TRY(bins_apply_tree<T>(ctx, Fac, w, w, &sc->done));
+        else SGP_TRY(tree_apply_inplace<T>(ctx, Fac, w, &sc->done));
         SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
     }
     LAUNCH(ctx, k_rz_init<T>, G, RB, 0, n, (const T *)r, (const T *)w, p, partials, sc);
@@ -549,8 +596,26 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
     SGP_TRY(resident_grid(ctx, (const void *)k_update_v<T, 0>, RB,
                           (3 * n / Pack<T>::K + RB - 1) / RB, &Gv));
     // One PCG iteration per call; kernels return at once after convergence.
+    // With the binned tree solve the step is five launches: the product, the
+    // three launches of the solve carrying r -= alpha q, the stopping test
+    // and r^T z, and the x / p update.
+    const bool fused = tree;
     auto iterate = [&](int count) -> sgp_status {
         cudaEvent_t ev;
+        if (fused) {
+            for (int it = 0; it < count; ++it) {
+                SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
+                SGP_TRY(launch_spmv_pq<T>(ctx, B, row_ptr, g0, n, (const T *)p, q, partials, sc));
+                SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
+                SGP_TRY(kt_begin(ctx, SGP_KT_TREE_SOLVE, &ev));
+                SGP_TRY(bins_pcg_step<T>(ctx, Fac, r, (const T *)q, w, sc));
+                SGP_TRY(kt_end(ctx, SGP_KT_TREE_SOLVE, ev));
+                SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+                LAUNCH(ctx, k_pupd_x<T>, Gv, RB, 0, n, xt, p, (const T *)w, sc);
+                SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
+            }
+            return SGP_OK;
+        }
         for (int it = 0; it < count; ++it) {
             SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
             SGP_TRY(launch_spmv_pq<T>(ctx, B, row_ptr, g0, n, (const T *)p, q, partials, sc));
@@ -598,7 +663,7 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
                                  (uint64_t)(uintptr_t)r, (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q,
                                  (uint64_t)(uintptr_t)w, (uint64_t)(uintptr_t)partials, (uint64_t)(uintptr_t)sc,
                                  (uint64_t)(uintptr_t)jac, (uint64_t)wchunk, (uint64_t)ctx->spmv_lpr,
-                                 (uint64_t)ctx->spmv_ilp};
+                                 (uint64_t)ctx->spmv_ilp, (uint64_t)fused};
         GraphEntry *we = nullptr;
         SGP_TRY(graph_lookup(ctx, wkey, sizeof(wkey) / sizeof(wkey[0]), &we));
         if (!we->exec &&
@@ -625,7 +690,7 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
                             (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)q, (uint64_t)(uintptr_t)w,
                             (uint64_t)(uintptr_t)partials, (uint64_t)(uintptr_t)sc,
                             (uint64_t)(uintptr_t)jac, (uint64_t)ctx->timing, (uint64_t)chunk,
-                            (uint64_t)ctx->spmv_lpr, (uint64_t)ctx->spmv_ilp};
+                            (uint64_t)ctx->spmv_lpr, (uint64_t)ctx->spmv_ilp, (uint64_t)fused};
     GraphEntry *ge = nullptr;
     SGP_TRY(graph_lookup(ctx, key, sizeof(key) / sizeof(key[0]), &ge));
     if (!ge->exec) SGP_TRY(graph_capture(ctx, ge, [&]() { return iterate(chunk); }));
@@ -637,6 +702,27 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
         if (hs->done) break;
     }
     return SGP_OK;
+}
+
+// One PCG run on Gamma x = F in the matrix's internal order.  With the
+// tree preconditioner and a binned factor built from this assembly, the run
+// takes F (and x) to the factor's tree order, solves there with the fused
+// steps, and brings x back; Ft and xt are tree-order workspaces (NT cells).
+template <typename T, typename X>
+sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int precond, const T *F, X *x,
+                   int x_given, double tol, int64_t maxit, T *r, T *p, T *q, T *w, T *Ft, T *xt,
+                   double *partials, Scal *sc, Scal *hs)
+{
+    static_assert(sizeof(X) == sizeof(T), "iterate and vectors share one precision");
+    const bool tree = precond == SGP_PRECOND_TREE && ctx->fused && Ft && xt && bins_tree_ready<T>(Fac, M);
+    if (!tree)
+        return pcg_core<T, X>(ctx, M, Fac, precond, make_blk<T>(M), bp<const int32_t>(M->row_ptr), M->n, false, F,
+                              x, x_given, tol, maxit, r, p, q, w, partials, sc, hs);
+    SGP_TRY(bins_to_tree<T>(ctx, Fac, F, Ft));
+    if (x_given) SGP_TRY(bins_to_tree<T>(ctx, Fac, reinterpret_cast<const T *>(x), xt));
+    SGP_TRY((pcg_core<T, T>(ctx, M, Fac, precond, tree_blk<T>(Fac), bp<const int32_t>(Fac->bl.rpt), Fac->bl.NT,
+                            true, Ft, xt, x_given, tol, maxit, r, p, q, w, partials, sc, hs)));
+    return bins_from_tree<T>(ctx, Fac, xt, reinterpret_cast<T *>(x));
 }
 
 }  // namespace
@@ -721,10 +807,13 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         if (info) *info = inf;
         return SGP_OK;
     }
-    // workspace: FP64 r, p, q, w (4 x 3n), FP32 rhs, r, p, q, w, d (6 x 3n),
-    // partials, scalars
-    const size_t v64 = sizeof(double) * 3 * n, v32 = sizeof(float) * 3 * n;
-    size_t need = 6 * v64 + (mixed ? 6 * v32 : 0) + sizeof(double) * 2 * MAXP + 2 * sizeof(Scal) + 4096;
+    // workspace: FP64 r, p, q, w and the tree-order F and x (6 x 3nv), F and
+    // v in the internal order (2 x 3n), FP32 rhs, r, p, q, w, d and the
+    // tree-order pair (8 x 3nv), partials, scalars; nv covers the binned
+    // solve's tree order (a little longer than n: padding)
+    const int64_t nv = (opts->precond == SGP_PRECOND_TREE && Fac && Fac->bl.NT > n) ? Fac->bl.NT : n;
+    const size_t v64 = sizeof(double) * 3 * nv, v32 = sizeof(float) * 3 * nv;
+    size_t need = 8 * v64 + (mixed ? 8 * v32 : 0) + sizeof(double) * 2 * MAXP + 2 * sizeof(Scal) + 8192;
     SGP_TRY(scratch_ensure(ctx, need + 4096));
     char *base = reinterpret_cast<char *>(ctx->d_scratch) + 256;
     auto take = [&](size_t b) {
@@ -739,6 +828,8 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     double *p = reinterpret_cast<double *>(take(v64));
     double *q = reinterpret_cast<double *>(take(v64));
     double *w = reinterpret_cast<double *>(take(v64));
+    double *Ft64 = reinterpret_cast<double *>(take(v64));
+    double *xt64 = reinterpret_cast<double *>(take(v64));
     // the solve runs in the matrix's internal cell order
     const double *F_user = F;
     double *v_user = v;
@@ -761,7 +852,7 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     double hres[2] = {0, 0};
     if (!mixed) {
         SGP_TRY(pcg_run<double, double>(ctx, M, Fac, opts->precond, F, v, opts->x0_given, opts->tol,
-                                        opts->maxit, r, p, q, w, partials, sc, &hs));
+                                        opts->maxit, r, p, q, w, Ft64, xt64, partials, sc, &hs));
         inf.iterations = hs.it;
         inf.status = hs.status;
         inf.rel_residual = hs.FF > 0 ? std::sqrt(hs.rr / hs.FF) : 0.0;
@@ -773,6 +864,8 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         float *q32 = reinterpret_cast<float *>(take(v32));
         float *w32 = reinterpret_cast<float *>(take(v32));
         float *d32 = reinterpret_cast<float *>(take(v32));
+        float *Ft32 = reinterpret_cast<float *>(take(v32));
+        float *xt32 = reinterpret_cast<float *>(take(v32));
         const int max_outer = opts->max_outer > 0 ? opts->max_outer : 30;
         const double itol = opts->inner_tol > 0 ? opts->inner_tol : 1e-3;
         if (!opts->x0_given) SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
@@ -806,11 +899,12 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
             const double need = 0.5 * opts->tol * std::sqrt(ff) / nr;
             const double itol_k = std::max(itol, std::min(need, 0.5));
             SGP_TRY(pcg_run<float, float>(ctx, M, Fac, opts->precond, (const float *)r32, d32, 0, itol_k,
-                                          opts->maxit - total, s32, p32, q32, w32, partials, sc, &hs));
+                                          opts->maxit - total, s32, p32, q32, w32, Ft32, xt32, partials, sc,
+                                          &hs));
             total += hs.it;
             ++outer;
-            if (hs.status == SGP_ERR_NOT_SPD) {
-                inf.status = SGP_ERR_NOT_SPD;
+            if (hs.status == SGP_ERR_NOT_SPD || hs.status == SGP_ERR_TIMEOUT) {
+                inf.status = hs.status;
                 break;
             }
             LAUNCH(ctx, k_accumulate, grid_for(3 * n, SGP_BLOCK), SGP_BLOCK, 0, 3 * n, (const float *)d32,
@@ -830,7 +924,10 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     inf.true_rel_residual = hres[1] > 0 ? std::sqrt(hres[0] / hres[1]) : 0.0;
     LAUNCH(ctx, k_to_caller<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v, v_user);
     if (info) *info = inf;
-    if (inf.status == SGP_ERR_NOT_SPD)
+    if (opts->precond == SGP_PRECOND_TREE) SGP_TRY(bins_check(ctx, Fac));
+    if (inf.status == SGP_ERR_TIMEOUT)
+        rc = sgp_fail(ctx, SGP_ERR_TIMEOUT, "pcg: a bounded device wait gave up");
+    else if (inf.status == SGP_ERR_NOT_SPD)
         rc = sgp_fail(ctx, SGP_ERR_NOT_SPD, "pcg: breakdown (p^T Gamma p or r^T z not positive)");
     else if (inf.status == SGP_ERR_NO_CONVERGENCE)
         rc = sgp_fail(ctx, SGP_ERR_NO_CONVERGENCE, "pcg: no convergence after %lld iterations",

@@ -67,6 +67,8 @@ struct sgp_ctx {
     int coop_cap = 0;       // vertices left when one cooperative kernel takes over the levels (0: none)
     int ctail_cap = 0;      // vertices left when the thread-block-cluster tail takes over (0: none)
     int ctail_R = 0;        // cluster size of that tail on this device (0: not probed, -1: none)
+    int bin_cap = 1024;     // largest contraction subtree solved by one thread block (0: level kernels only)
+    int fused = 1;          // PCG step fused around the binned tree solve
     int use_pdl = 1;        // programmatic dependent launch of the level kernels
     int batch_chunk = 0;    // rows per work item of the batched solver
     int num_sms = 0;
@@ -188,6 +190,36 @@ sgp_status scan_exclusive_i32(sgp_ctx *ctx, const int32_t *in, int32_t *out, int
 template <typename T>
 sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
 
+// The binned tree solve (bins.cu).  bins_build runs at the end of a factor
+// build; bins_usable tells whether precision T has a layout that fits;
+// bins_apply is z = P^-1 w in place; bins_pcg_step is one PCG step around
+// the solve (r -= alpha q, |r|^2 and the stopping test, z = P^-1 r, r^T z and
+// beta) with the scalars in `scal` (the solver's device scalar block);
+// bins_check reports a bounded device wait that gave up.
+// The fused solve runs in the layout's own cell order (tree order,
+// BinLayout::NT cells, padding zero): bins_tree_ready tells whether the
+// factor holds the matrix's rows in that order for this assembly;
+// bins_to_tree / bins_from_tree move vectors between the orders;
+// bins_apply_tree is z = P^-1 w on tree-order vectors.
+struct sgp_factor;
+struct sgp_matrix;
+sgp_status bins_build(sgp_ctx *ctx, sgp_factor *F, const sgp_matrix *M);
+template <typename T>
+bool bins_usable(const sgp_factor *F);
+template <typename T>
+bool bins_tree_ready(const sgp_factor *F, const sgp_matrix *M);
+template <typename T>
+sgp_status bins_apply(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done);
+template <typename T>
+sgp_status bins_apply_tree(sgp_ctx *ctx, const sgp_factor *F, T *w, T *z, const int *done);
+template <typename T>
+sgp_status bins_to_tree(sgp_ctx *ctx, const sgp_factor *F, const T *src, T *dst);
+template <typename T>
+sgp_status bins_from_tree(sgp_ctx *ctx, const sgp_factor *F, const T *src, T *dst);
+template <typename T>
+sgp_status bins_pcg_step(sgp_ctx *ctx, const sgp_factor *F, T *r, const T *q, T *z, void *scal);
+sgp_status bins_check(sgp_ctx *ctx, const sgp_factor *F);
+
 // Kernel timing hooks (no-ops unless enabled on the context).
 sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev);
 sgp_status kt_end(sgp_ctx *ctx, int kclass, cudaEvent_t ev);
@@ -236,6 +268,34 @@ struct sgp_tree {
     DBuf edges;   // nt int32 tree edge ids, ascending
     DBuf comp;    // n int32 component label
     DBuf bestw, beste, hook, intree, flag, idx;
+};
+
+// The binned layout of the tree solve (bins.cu): the contraction tree cut
+// into bins of subtrees with at most bmax vertices and the top part above
+// them.  Per-bin arrays are padded to 4 entries so that every segment starts
+// on a 16-byte boundary (bulk copies).  Index [0] of the numeric arrays is
+// FP32, [1] FP64.
+struct BinLayout {
+    int ok32 = 0, ok64 = 0;
+    int32_t nb = 0, nt = 0, LV = 0, LVP = 0, bmax = 0;
+    int32_t G = 0, E = 0, Cc = 0, K = 0, Pp = 0, Z = 0;
+    int32_t ntt = 0, nte = 0, ntp = 0, nly = 0, tints = 0;
+    int32_t toff[9] = {0};
+    int32_t NT = 0;                    // length of a tree-order vector (cells)
+    size_t smA[2] = {0, 0}, smT[2] = {0, 0}, smC[2] = {0, 0};   // fused PCG step
+    size_t smA0[2] = {0, 0}, smC0[2] = {0, 0};                  // plain solve
+    size_t smTnd[2] = {0, 0};                                   // top without staged pivots
+    DBuf hdr, elev, vlev, gvert, er, ec, cl, kl, ks, pr, pref, zi, tv, tint;
+    DBuf c_src, k_src, p_src, d_src, t_src, tD_src;
+    DBuf cL[2], kL[2], pL[2], D[2], tL[2], tD[2];
+    DBuf ly[2], lsum[2], tw[2], part, err;
+    // tree order <-> the matrix's internal order, and the matrix's rows in
+    // tree order (FP32 eq. (1) records for MIXED, FP64 blocks and columns
+    // for F64) from the assembly of generation mgen
+    DBuf i_of_t, t_of_i, rpt, ma32, mb32, m64, mc64;
+    uint64_t mgen = 0;
+    int mat32 = 0, mat64 = 0;
+    DBuf scr[64];
 };
 
 struct sgp_factor {
@@ -289,6 +349,7 @@ struct sgp_factor {
     DBuf bm_Lf, bm_Lf32, bm_Lb, bm_Lb32, bm_D, bm_D32;
     int32_t bm_maxv[4] = {0, 0, 0, 0};      // largest per-block count of each kind
     DBuf et_succ, et_dist, et_succ2, et_dist2, et_tid, et_size, et_flag, pinned, comp_int;  // Euler tour scratch
+    BinLayout bl;
     // structure-simulation scratch
     DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,
         acc, fill, sbuf, tmp, rflag, cnt;

@@ -16,6 +16,7 @@ struct Scal {
     int done, status;
     unsigned cnt;
     int pad;
+    int xpend;   // the step's x += alpha p is still to be applied
 };
 
 // The end of a step's r^T z reduction: beta = rz / rho, rho = rz, or a

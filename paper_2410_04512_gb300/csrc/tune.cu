@@ -67,7 +67,7 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *t)
     t->coop_cap = ctx->coop_cap;
     t->spmv_ilp = ctx->spmv_ilp;
     t->ctail_cap = ctx->ctail_cap;
-    t->reserved = 0;
+    t->bin_cap = ctx->bin_cap > 0 ? ctx->bin_cap : -1;
     t->ms_per_iteration = 0.0;
     return SGP_OK;
 }
@@ -89,7 +89,10 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     if (!(t->comp_size == 0 || (t->comp_size >= 64 && t->comp_size <= 8192 &&
                                 (t->comp_size & (t->comp_size - 1)) == 0)))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: comp_size must be 0 or a power of two in [64, 8192]");
+    if (!(t->bin_cap == 0 || t->bin_cap == -1 || (t->bin_cap >= 64 && t->bin_cap <= 8192)))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: bin_cap must be 0, -1 or in [64, 8192]");
     ctx->spmv_lpr = t->spmv_lpr;
+    ctx->bin_cap = t->bin_cap == 0 ? 1024 : t->bin_cap;
     ctx->tail_cap = t->tail_cap;
     ctx->comp_size = t->comp_size;
     ctx->coop_cap = t->coop_cap;

@@ -23,10 +23,18 @@ def test_set_tuning_validates(ctx):
                 dict(coop_cap=1 << 25), dict(spmv_ilp=3), dict(ctail_cap=100)):
         with pytest.raises(sgp.SgpError):
             ctx.set_tuning(**bad)
+    for bad in (dict(bin_cap=32), dict(bin_cap=-2), dict(bin_cap=9000)):
+        with pytest.raises(sgp.SgpError):
+            ctx.set_tuning(**bad)
     ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096, spmv_ilp=2,
-                   ctail_cap=8192)
+                   ctail_cap=8192, bin_cap=512)
     assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "comp_size": 256,
-                                "coop_cap": 4096, "spmv_ilp": 2, "ctail_cap": 8192, "ms_per_iteration": 0.0}
+                                "coop_cap": 4096, "spmv_ilp": 2, "ctail_cap": 8192, "bin_cap": 512,
+                                "ms_per_iteration": 0.0}
+    ctx.set_tuning(bin_cap=-1)
+    assert ctx.get_tuning()["bin_cap"] == -1
+    ctx.set_tuning()
+    assert ctx.get_tuning()["bin_cap"] == 1024
 
 
 @pytest.mark.parametrize("cap,cs,coop,ct", [(0, 0, 0, 0), (64, 1024, 0, 0), (256, 64, 2048, 0), (-1, 256, 0, 0),
