@@ -420,7 +420,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, n, run_seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args, forms.get("plain_fp64_mst", {}).get("iterations"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -652,33 +652,102 @@ def run_warm(args):
 # ---------------------------------------------------------------------------
 # the CPU oracle: cpu_baseline leg and the reference arm
 # ---------------------------------------------------------------------------
-def oracle_sample(n_sample: int, seed: int, tol: float):
-    """One oracle pass over a ball of n_sample cells of the default law:
-    brute-force contacts, eq. (1) blocks, Prim, TreeLDLT, PCG."""
-    import oracle
-    c = workloads.ball(n=n_sample, seed=seed, gamma0=1e-3)
-    F = c.forces()
-    t = time.perf_counter()
-    s = oracle.build_system(c.pos, c.radii, c.gammas_np, c.gamma0)
-    res, _ = oracle.solve_system(s, F, tol=tol)
-    return time.perf_counter() - t, res.iters
+def oracle_iterations(workload: str, fallback=None):
+    """The oracle's own PCG iteration count to the tolerance on a benchmark
+    workload (oracle/calibration.json, written by ``python -m
+    oracle.calibrate``), else `fallback` (the FP64 GPU solve's count of the
+    same system, which the parity tests keep within 2 of the oracle's)."""
+    p = os.path.join(ROOT, "oracle", "calibration.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            cal = json.load(f)
+        if workload in cal:
+            return int(cal[workload]["iterations"]), "the oracle's own count, oracle/calibration.json"
+    if fallback is not None:
+        return int(fallback), "FP64 GPU solve of the same system"
+    return None, None
 
 
-def cpu_baseline(args, n_full: int, run_seconds: float = 15.0):
-    n_s = args.cpu_sample_cells
-    times, its = [], []
-    t0 = time.perf_counter()
-    while True:
-        dt, it = oracle_sample(n_s, 2000, args.tol)
-        times.append(dt)
-        its.append(it)
-        if time.perf_counter() - t0 > run_seconds or len(times) >= 20:
-            break
-    per = float(np.median(times)) * (n_full / n_s)
-    return {"value": round(1.0 / per, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} oracle passes on a {n_s}-cell ball of the same law (brute-force "
-                      f"contacts, Prim, TreeLDLT, PCG to {args.tol:g}; {int(np.median(its))} iterations), "
-                      f"median {np.median(times):.3f} s, scaled by N ({n_full}/{n_s}) to the full workload"}
+class OracleSystem:
+    """The full workload of rank 0's replica on the CPU: k-d tree contact
+    search (the oracle's contact rule), eq. (1) blocks; then the solve
+    phase the paper times (Section 5): Prim, TreeLDLT, PCG."""
+
+    def __init__(self, workload: str):
+        import oracle
+        self.oracle = oracle
+        self.cells = WORKLOADS[workload]["make"](replica_seed(0))
+        c = self.cells
+        self.F = c.forces()
+        t = time.perf_counter()
+        ij = oracle.contacts_kdtree(c.pos, c.radii)
+        self.contacts_s = time.perf_counter() - t
+        t = time.perf_counter()
+        self.sys = oracle.build_system(c.pos, c.radii, c.gammas_np, c.gamma0, ij=ij)
+        self.blocks_s = time.perf_counter() - t
+
+    def factor(self):
+        o, s = self.oracle, self.sys
+        t = time.perf_counter()
+        forest = o.prim_msf(s.n, s.ij, s.w)
+        t1 = time.perf_counter()
+        fac = o.tree_ldlt(forest, s.blocks, s.gamma0)
+        t2 = time.perf_counter()
+        return fac, t1 - t, t2 - t1
+
+    def pcg_iter_s(self, fac, k: int, parallel: bool) -> float:
+        """Seconds per PCG iteration at full size, from k timed iterations."""
+        o, s = self.oracle, self.sys
+        t = time.perf_counter()
+        if parallel:
+            o.pcg_parallel(s.n, s.ij, s.blocks, s.gamma0, self.F, fac, tol=1e-300, maxit=k)
+        else:
+            o.pcg(s.n, s.ij, s.blocks, s.gamma0, self.F, o.PRECOND_TREE, fac, fixed_iters=k)
+        return (time.perf_counter() - t) / k
+
+    def contact_scan(self, n_sample: int = 20000):
+        """The oracle's brute-force contact test over all pairs of a sample
+        of cells: pair tests per second, and the full scan's time at that
+        rate (extrapolated)."""
+        c = self.cells
+        ns = min(n_sample, c.n)
+        t = time.perf_counter()
+        self.oracle.contacts(c.pos[:ns], c.radii[:ns])
+        dt = time.perf_counter() - t
+        rate = ns * (ns - 1) / 2 / dt
+        return {"sample_cells": ns, "pair_tests_per_s": round(rate, 1),
+                "full_scan_s": round(c.n * (c.n - 1) / 2 / rate, 1), "extrapolated": True}
+
+
+def cpu_baseline(args, gpu_fp64_iters=None, k_iters: int = 20):
+    """The oracle on the host cores, on the full workload: Prim and TreeLDLT
+    timed in full, PCG timed for k_iters iterations at full size (one core,
+    as the oracle stands; and all cores: the same PCG with the product and
+    the vector operations over OpenMP threads, the tree solve sequential),
+    each scaled to the oracle's own iteration count to the tolerance."""
+    osys = OracleSystem(args.workload)
+    iters, src = oracle_iterations(args.workload, gpu_fp64_iters)
+    if iters is None:
+        return {"unavailable": "no oracle iteration count for this workload (python -m oracle.calibrate)"}
+    fac, prim_s, ldlt_s = osys.factor()
+    it1 = osys.pcg_iter_s(fac, k_iters, parallel=False)
+    itn = osys.pcg_iter_s(fac, k_iters, parallel=True)
+    threads = osys.oracle.parallel_threads()
+    one = prim_s + ldlt_s + it1 * iters
+    alln = prim_s + ldlt_s + itn * iters
+    n = osys.cells.n
+    return {"value": round(1.0 / one, 6), "unit": "solves/s", "cores": 1, "kind": "oracle", "extrapolated": True,
+            "sample": f"full {n}-cell workload: Prim {prim_s:.2f} s and TreeLDLT {ldlt_s:.2f} s timed in full, "
+                      f"PCG timed for {k_iters} iterations at full size ({it1 * 1e3:.1f} ms each) and scaled "
+                      f"to {iters} iterations to {args.tol:g} ({src})",
+            "solve_s": round(one, 3),
+            "all_cores": {"value": round(1.0 / alln, 6), "unit": "solves/s", "cores": threads,
+                          "nproc": os.cpu_count(), "solve_s": round(alln, 3),
+                          "pcg_iteration_ms": round(itn * 1e3, 2),
+                          "note": "product and vector operations over OpenMP threads, tree solve sequential"},
+            "setup_not_in_value": {"contacts_kdtree_s": round(osys.contacts_s, 3),
+                                   "friction_blocks_s": round(osys.blocks_s, 3)},
+            "contact_scan_bruteforce": osys.contact_scan()}
 
 
 def run_reference(args):
@@ -686,27 +755,38 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_full = {"ball1m": 1_000_000, "cube1k": 1000, "hex4m": 4_000_000}[args.workload]
-    n_s = min(args.cpu_sample_cells, n_full)
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": f"no CPU reference for workload {args.workload}"}))
+        return
+    iters, src = oracle_iterations(args.workload)
+    if iters is None:
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "no oracle iteration count for this workload (python -m oracle.calibrate)"}))
+        return
+    osys = OracleSystem(args.workload)
+    k_iters = 10
+
+    def step():
+        fac, prim_s, ldlt_s = osys.factor()
+        return prim_s + ldlt_s + osys.pcg_iter_s(fac, k_iters, parallel=False) * iters
+
     for _ in range(args.warmup):
-        oracle_sample(n_s, 2000, args.tol)
-    times, its = [], []
-    for _ in range(args.steps):
-        dt, it = oracle_sample(n_s, 2000, args.tol)
-        times.append(dt)
-        its.append(it)
-    total = float(np.sum(times)) * (n_full / n_s)
+        step()
+    times = [step() for _ in range(args.steps)]
+    total = float(np.sum(times))
     value = args.steps / total
+    n = osys.cells.n
+    sample = (f"each step: Prim and TreeLDLT on the full {n}-cell workload timed in full, PCG timed for "
+              f"{k_iters} iterations at full size and scaled to {iters} iterations to {args.tol:g} ({src})")
     line = {"metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "n_cells": n_full, "tol": args.tol,
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "n_cells": n, "tol": args.tol,
                        "precond": "tree", "precision": "fp64"},
             "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one oracle pass on a {n_s}-cell ball of the same law, "
-                                       f"time scaled by N ({n_full}/{n_s})"},
+                             "extrapolated": True, "sample": sample},
             "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -725,8 +805,6 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--cpu-baseline", dest="cpu_baseline", type=int, default=1)
     ap.add_argument("--compare", type=int, default=1, help="also time plain FP64 and block-Jacobi")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--cpu-sample-cells", type=int, default=20000)
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the launch shapes with the library's autotuner before timing "
                          "(whole solves plus factor builds per candidate); 0: built-in defaults")

@@ -47,6 +47,66 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_PAR_SRC = os.path.join(_HERE, "cpu_parallel.c")
+_PAR_LIB = os.path.join(_HERE, "_sgp_parallel.so")
+_par = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the all-cores CPU baseline (cpu_parallel.c together with the
+    oracle's sources, OpenMP when the compiler has it).  Baseline
+    infrastructure: only the benchmark's CPU leg and the tests use it."""
+    srcs = [_SRC, _PAR_SRC]
+    if force or not os.path.exists(_PAR_LIB) or any(os.path.getmtime(_PAR_LIB) < os.path.getmtime(f) for f in srcs):
+        tmp = _PAR_LIB + f".{os.getpid()}.tmp"
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+        try:
+            subprocess.check_call(base + ["-fopenmp"] + srcs + ["-o", tmp, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + srcs + ["-o", tmp, "-lm"])
+        os.replace(tmp, _PAR_LIB)
+    return _PAR_LIB
+
+
+def _get_parallel():
+    global _par
+    with _lock:
+        if _par is None:
+            lib = ctypes.CDLL(build_parallel())
+            P, I64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+            lib.orc_omp_threads.argtypes = []
+            lib.orc_omp_threads.restype = ctypes.c_int
+            lib.orc_omp_pcg_tree.argtypes = [I64, I64, P, P, D, P, P, P, P, P, P, D, I64,
+                                             ctypes.POINTER(I64), ctypes.POINTER(D)]
+            lib.orc_omp_pcg_tree.restype = ctypes.c_int
+            _par = lib
+    return _par
+
+
+def parallel_threads() -> int:
+    """Threads the all-cores baseline runs with (1 without OpenMP)."""
+    return int(_get_parallel().orc_omp_threads())
+
+
+def pcg_parallel(n: int, ij, blocks, gamma0: float, F, factor: "TreeFactor", tol: float = 1e-8,
+                 maxit: int = 100000) -> "PcgResult":
+    """The same PCG with the tree preconditioner (Section 1.1), the Appendix
+    B.2 product row by row and the vector operations over all cores, the
+    tree solve (Appendix B.1) sequential.  Baseline timing only: the oracle
+    proper is ``pcg``."""
+    ij, blocks, F = _i32(ij), _f64(blocks), _f64(F)
+    x = np.zeros((n, 3))
+    it = ctypes.c_int64(0)
+    rel = ctypes.c_double(0.0)
+    f = factor.forest
+    rc = _get_parallel().orc_omp_pcg_tree(n, ij.shape[0], _p(ij), _p(blocks), gamma0, _p(f.order),
+                                          _p(f.parent), _p(factor.L), _p(factor.Dinv), _p(F), _p(x), tol,
+                                          maxit, ctypes.byref(it), ctypes.byref(rel))
+    if rc not in (OK, ERR_NO_CONVERGENCE):
+        raise OracleError(rc, "pcg_parallel")
+    return PcgResult(x, int(it.value), float(rel.value), rc)
+
+
 def _get():
     global _lib
     with _lock:

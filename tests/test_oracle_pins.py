@@ -453,3 +453,22 @@ def test_mst_beats_jacobi_and_identity_iterations():
         assert r.status == oracle.OK
         its[p] = r.iters
     assert its[oracle.PRECOND_TREE] < its[oracle.PRECOND_JACOBI] <= its[oracle.PRECOND_NONE]
+
+
+def test_all_cores_baseline_solves_the_same_system():
+    """The all-cores CPU baseline (row-wise product and vector operations on
+    OpenMP threads, the oracle's sequential tree solve) is the same PCG: on a
+    1000-cell cube it takes the oracle's iterations and reaches its solution
+    to rounding, and after a fixed number of steps it reports them."""
+    c = workloads.cube(n=1000, side=8.886, seed=1000)
+    o = oracle.build_system(c.pos, c.radii, c.gammas_np, c.gamma0)
+    F = c.forces()
+    f = oracle.prim_msf(c.n, o.ij, o.w)
+    fac = oracle.tree_ldlt(f, o.blocks, c.gamma0)
+    r1 = oracle.pcg(c.n, o.ij, o.blocks, c.gamma0, F, oracle.PRECOND_TREE, fac, tol=1e-10)
+    r2 = oracle.pcg_parallel(c.n, o.ij, o.blocks, c.gamma0, F, fac, tol=1e-10)
+    assert abs(r1.iters - r2.iters) <= 1
+    assert np.linalg.norm(r1.x - r2.x) <= 1e-9 * np.linalg.norm(r1.x)
+    r3 = oracle.pcg_parallel(c.n, o.ij, o.blocks, c.gamma0, F, fac, tol=1e-300, maxit=7)
+    assert r3.iters == 7 and r3.status == oracle.ERR_NO_CONVERGENCE
+    assert oracle.parallel_threads() >= 1
