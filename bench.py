@@ -167,6 +167,30 @@ def tree_bytes(n: int, npairs: int, nrecv: int, fp: int) -> int:
     return fwd + bwd
 
 
+def binned_bytes(n: int, npairs: int, nrecv: int, nleak: int, ntop: int, fp: int) -> int:
+    """Algorithmic bytes of one fused step around the binned tree solve
+    (its forward, leak-sum, top and backward launches).  Vectors: the
+    forward launch reads r and q and writes r and the forward values, the
+    backward launch reads them and r (for r^T z) and writes z; the top reads
+    r, q and its leak sums, writes r and z.  Blocks: every L block once in
+    each pass, D^-1 once.  Leaks: each product written and read, each top
+    sum written and read.  Indices: per forward entry its receiver and
+    contributor start, per pair its contributor / receiver reference, per
+    leak its source and slot, per cell its pair start."""
+    w = 3 * fp
+    vec = 7 * w * (n - ntop) + 5 * w * ntop
+    blocks = 2 * 9 * fp * npairs + 6 * fp * n
+    leaks = 2 * w * nleak + 2 * w * ntop
+    idx = 8 * nrecv + 8 * npairs + 8 * nleak + 4 * n
+    return vec + blocks + leaks + idx
+
+
+def update_bytes(n: int, fp: int) -> int:
+    """Bytes of the fused step's last launch: x += alpha p, p = z + beta p
+    (reads x, p, z, writes x, p)."""
+    return 5 * 3 * fp * n
+
+
 def vector_bytes(n: int, fp: int, precond: str) -> int:
     """Algorithmic bytes of the vector kernels of one PCG iteration (3n
     entries each): the update reads p, q, r, x and writes x, r and the
@@ -187,9 +211,7 @@ def outer_bytes(n: int, m: int) -> int:
 # one ncu capture of the current kernels on the default workload and form
 # (cold, serialised launches: the tree solve's levels re-read from DRAM what
 # the previous level left in L2); other workloads report null.
-MEASURED_TRAFFIC = {
-    ("ball1m", "mixed", "tree"): {"tree": 266915072, "spmv": 137288704},
-}
+MEASURED_TRAFFIC = {}
 
 
 def spmv_bytes(n: int, m: int, fp: int) -> int:
@@ -287,7 +309,8 @@ def run_gpu(args):
             ctx.set_kernel_timing(False)
             elapsed = max_over_ranks(elapsed, dev)
             return dict(elapsed=elapsed, solve_ms=float(np.median(solve_ms)), iters=float(np.mean(iters)),
-                        info=self.last[0], kt=kt, launches=launches, v=v)
+                        iters_total=int(np.sum(iters)), steps=steps, info=self.last[0], kt=kt,
+                        launches=launches, v=v)
 
     # ---- timed region: the chosen form, device-resident inputs ------------
     chosen = Form(args.precision, args.precond)
@@ -335,14 +358,10 @@ def run_gpu(args):
     e2e_s = max_over_ranks(e2e_s, dev)
     e2e_value = replica_throughput(world, e2e_steps, e2e_s)
 
-    # ---- rooflines of the two per-iteration kernels -----------------------
+    # ---- rooflines of the per-iteration kernels ----------------------------
     M = chosen.H["M"]
     m = M.m
     fp = 4 if chosen.precision == sgp.PREC_MIXED else 8
-    spmv_ms, spmv_n = kres["kt"][sgp.KT_SPMV]
-    tree_ms, tree_n = kres["kt"][sgp.KT_TREE_SOLVE]
-
-    traffic = MEASURED_TRAFFIC.get((args.workload, args.precision, args.precond), {})
 
     def roof(name, bytes_per, total_ms, launches, unit_note, traffic_bytes=None):
         avg_s = (total_ms / max(launches, 1)) / 1e3
@@ -354,25 +373,62 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": int(bytes_per), "avg_launch_us": round(avg_s * 1e6, 2),
                 "launches": launches, "unit_of_work": unit_note}
 
-    roofs = [roof("k_spmv_pq<%s>" % ("float" if fp == 4 else "double"), spmv_bytes(n, m, fp), spmv_ms, spmv_n,
-                  "one product Gamma p + p^T q over all rows", traffic.get("spmv"))]
-    if chosen.precond == sgp.PRECOND_TREE:
-        _, levels, npairs, nrecv = chosen.H["Fh"].stats()
-        roofs.append(roof("tree solve (k_tree_fwd/k_tree_tail/k_tree_bwd<%s>, %d levels)"
-                          % ("float" if fp == 4 else "double", levels),
-                          tree_bytes(n, npairs, nrecv, fp), tree_ms, tree_n,
-                          "one application of P^-1 (all levels)", traffic.get("tree")))
-    dominant = max(range(len(roofs)), key=lambda i: [spmv_ms, tree_ms][i])
+    def form_rooflines(form, kres, label=""):
+        """Rooflines of a form's kernel classes from its timed repeat: the
+        product, the tree step (fused binned solve, or the level kernels),
+        and the vector updates (per iteration)."""
+        H = form.H
+        fpx = 4 if form.precision == sgp.PREC_MIXED else 8
+        tn = "float" if fpx == 4 else "double"
+        mm = H["M"].m
+        traffic = MEASURED_TRAFFIC.get((args.workload, "mixed" if fpx == 4 else "f64", "tree"), {})
+        spmv_ms, spmv_n = kres["kt"][sgp.KT_SPMV]
+        tree_ms, tree_n = kres["kt"][sgp.KT_TREE_SOLVE]
+        vec_ms, _ = kres["kt"][sgp.KT_PCG_VECTOR]
+        its = max(int(kres["iters_total"]), 1)   # iterations of every timed step
+        out = {"spmv": roof(label + "k_spmv_pq<%s>" % tn, spmv_bytes(n, mm, fpx), spmv_ms, spmv_n,
+                            "one product Gamma p + p^T q over all rows", traffic.get("spmv"))}
+        it_bytes = spmv_bytes(n, mm, fpx)
+        if form.precond == sgp.PRECOND_TREE:
+            _, levels, npairs, nrecv = H["Fh"].stats()
+            lay = H["Fh"].layout()
+            if lay["fp32" if fpx == 4 else "fp64"]:
+                tb = binned_bytes(n, npairs, nrecv, lay["leaks"], lay["top"], fpx)
+                out["tree"] = roof(label + "fused tree step (k_bin_fwd, k_leaksum, k_top, k_bin_bwd <%s>; %d bins, "
+                                   "top %d)" % (tn, lay["bins"], lay["top"]), tb, tree_ms, tree_n,
+                                   "one application of P^-1 with r -= alpha q, |r|^2 and r^T z (four launches)",
+                                   traffic.get("tree"))
+                vb = update_bytes(n, fpx)
+                out["vector"] = roof(label + "k_pupd_x<%s> (class time also holds the solve's start and the "
+                                     "refinement's residual kernels)" % tn, vb, vec_ms, its,
+                                     "x += alpha p, p = z + beta p, per iteration", traffic.get("vector"))
+            else:
+                tb = tree_bytes(n, npairs, nrecv, fpx)
+                out["tree"] = roof(label + "tree solve (level kernels <%s>, %d levels)" % (tn, levels), tb,
+                                   tree_ms, tree_n, "one application of P^-1 (all levels)")
+                vb = vector_bytes(n, fpx, "tree")
+                out["vector"] = roof(label + "PCG vector kernels <%s>" % tn, vb, vec_ms, its,
+                                     "update, r^T z and direction kernels, per iteration")
+            it_bytes += tb + vb
+        else:
+            vb = vector_bytes(n, fpx, "jacobi")
+            out["vector"] = roof(label + "PCG vector kernels <%s>" % tn, vb, vec_ms, its,
+                                 "update with the block-Jacobi product, per iteration")
+            it_bytes += vb
+        return out, it_bytes
+
+    roofmap, it_bytes = form_rooflines(chosen, kres)
+    names = list(roofmap)
+    dominant = max(names, key=lambda k: roofmap[k]["avg_launch_us"] * roofmap[k]["launches"])
     # the solve against the bandwidth roofline: algorithmic bytes of all its
-    # iterations (product + tree solve + vector kernels) and refinement steps
-    it_bytes = spmv_bytes(n, m, fp) + vector_bytes(n, fp, args.precond)
-    if chosen.precond == sgp.PRECOND_TREE:
-        it_bytes += tree_bytes(n, npairs, nrecv, fp)
+    # iterations (product + tree step + vector updates) and refinement steps
     solve_bytes = res["iters"] * it_bytes + (info.outer_iterations + 1) * outer_bytes(n, m) * (fp == 4)
     roof_ms = solve_bytes / (hbm_peak * 1e9) * 1e3
     solve_roof = {"bytes": int(solve_bytes), "bytes_per_inner_iteration": int(it_bytes),
                   "roof_ms": round(roof_ms, 3), "measured_ms": round(res["solve_ms"], 3),
                   "frac": round(roof_ms / res["solve_ms"], 4), "peak_gbs": hbm_peak}
+    roof_other = [roofmap[k] for k in names if k != dominant]
+    tree_layout = chosen.H["Fh"].layout() if chosen.precond == sgp.PRECOND_TREE else None
 
     # ---- the other forms on the same workload (outside the timed region) --
     forms = {}
@@ -381,11 +437,16 @@ def run_gpu(args):
         for label, prec, pc, steps in (("plain_fp64_mst", "f64", "tree", 2), ("fp64_block_jacobi", "f64", "jacobi", 1)):
             if (prec, pc) == (args.precision, args.precond):
                 continue
-            r = Form(prec, pc).timed(steps, 1, kernel_timing=False)
+            f = Form(prec, pc)
+            r = f.timed(steps, 1, kernel_timing=False)
             forms[label] = {"solves_per_s": round(steps / r["elapsed"], 4),
                             "solve_only_per_s": round(1e3 / r["solve_ms"], 4),
                             "iterations": int(round(r["iters"])),
                             "true_rel_residual": r["info"].true_rel_residual}
+            if label == "plain_fp64_mst":
+                kr = f.timed(1, 0, kernel_timing=True)
+                rm, _ = form_rooflines(f, kr, "plain FP64 form: ")
+                roof_other += list(rm.values())
         if "plain_fp64_mst" in forms:
             forms["chosen_vs_plain_fp64"] = round(value / forms["plain_fp64_mst"]["solves_per_s"], 3)
 
@@ -409,9 +470,11 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d_bytes(pos, radii, F),
                 "d2h_bytes_per_step": F.numel() * 8, "steps": e2e_steps},
         "gpu_launches": int(res["launches"]),
-        "roofline": roofs[dominant], "roofline_other": [r for i, r in enumerate(roofs) if i != dominant],
-        "solve_roofline": solve_roof,
-        "time_share_ms": {"spmv": round(spmv_ms, 2), "tree_solve": round(tree_ms, 2),
+        "roofline": roofmap[dominant], "roofline_other": roof_other,
+        "solve_roofline": solve_roof, "tree_layout": tree_layout,
+        "time_share_ms": {"spmv": round(kres["kt"][sgp.KT_SPMV][0], 2),
+                          "tree_solve": round(kres["kt"][sgp.KT_TREE_SOLVE][0], 2),
+                          "vector": round(kres["kt"][sgp.KT_PCG_VECTOR][0], 2),
                           "timed": round(kres["elapsed"] * 1e3, 2),
                           "note": "kernel events over a repeat of the timed steps (%d steps, %.2f solves/s "
                                   "with the events on)" % (args.steps, args.steps / kres["elapsed"])},
@@ -421,11 +484,57 @@ def run_gpu(args):
     }
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, forms.get("plain_fp64_mst", {}).get("iterations"))
+    if rank == 0 and world == 1 and args.configs and args.workload == "ball1m":
+        line["configs"] = other_configs(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def other_configs(args):
+    """The other configurations of the benchmark's set, each run as its own
+    bench.py process with short step counts (built-in launch shapes): the
+    1000-cell cube, the 4e6-cell sheet against plain FP64, the 512-spheroid
+    batch against looped solves, the learned warm start.  A compact record
+    of each goes into the main line."""
+    runs = [("cube1k", ["--workload", "cube1k", "--steps", "20", "--compare", "1"]),
+            ("hex4m", ["--workload", "hex4m", "--steps", "2", "--compare", "1"]),
+            ("batch512", ["--workload", "batch512", "--steps", "2"]),
+            ("warm200k", ["--workload", "warm200k"])]
+    out = {}
+    for name, extra in runs:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "3", "--autotune", "0",
+               "--cpu-baseline", "0", "--configs", "0"] + extra
+        t0 = time.perf_counter()
+        try:
+            p = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            rec = None
+            for ln in p.stdout.splitlines():
+                if ln.startswith("{"):
+                    rec = json.loads(ln)
+            if rec is None:
+                out[name] = {"error": (p.stderr or p.stdout)[-400:]}
+                continue
+        except subprocess.TimeoutExpired:
+            out[name] = {"error": "timed out"}
+            continue
+        keep = {k: rec[k] for k in ("value", "unit", "ms_per_step", "iterations", "true_rel_residual",
+                                    "outer_iterations", "true_rel_residual_max", "solve_only", "forms",
+                                    "latency_ms", "looped_plain_fp64", "looped_mixed", "learned", "zero_guess",
+                                    "previous_v", "solve_only_ms_mean", "tree_layout", "clocks")
+                if k in rec}
+        keep["workload"] = rec.get("config", {}).get("workload")
+        if "roofline" in rec:
+            keep["roofline"] = {k: rec["roofline"][k] for k in ("kernel", "achieved", "frac", "avg_launch_us")}
+            keep["roofline_other"] = [{k: r[k] for k in ("kernel", "achieved", "frac", "avg_launch_us")}
+                                      for r in rec.get("roofline_other", [])]
+        if "solve_roofline" in rec:
+            keep["solve_roofline_frac"] = rec["solve_roofline"]["frac"]
+        keep["run_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = keep
+    return out
 
 
 def h2d_bytes(*ts) -> int:
@@ -487,27 +596,33 @@ def run_batch(args):
     its = np.array([i.iterations for i in infos])
     res = np.array([i.true_rel_residual for i in infos])
 
-    # the plain solver looped over the same instances (FP64, one at a time,
-    # built-in launch shapes)
+    # the single-system solver looped over the same instances, one at a
+    # time (built-in launch shapes): plain FP64, and the batch's own
+    # precision (isolating what batching gains)
     ctx.set_tuning()
-    lat = []
-    Hs = {"g": None, "M": None, "T": None, "Fh": None}
-    for s in range(len(cells)):
-        lo, hi = int(off[s]), int(off[s + 1])
-        p_s, r_s, F_s = pos[lo:hi].contiguous(), radii[lo:hi].contiguous(), F[lo:hi].contiguous()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        Hs["g"] = ctx.collision_graph(p_s, r_s, Hs["g"])
-        ij = Hs["g"].edges().to(torch.int64) + lo
-        gp, gq = workloads.pair_gamma_torch(4000, ij, t, t)
-        Hs["M"] = ctx.friction_assemble(Hs["g"], p_s, gp.contiguous(), gq.contiguous(), 1e-2, sgp.PREC_F64, Hs["M"])
-        Hs["T"] = ctx.max_spanning_tree(Hs["M"], Hs["T"])
-        Hs["Fh"] = ctx.tree_factor(Hs["M"], Hs["T"], Hs["Fh"])
-        ctx.pcg_solve(Hs["M"], Hs["Fh"], F_s, tol=args.tol)
-        b.record(stream)
-        b.synchronize()
-        lat.append(a.elapsed_time(b))
-    lat = np.array(lat)
+
+    def looped(pr):
+        lat = []
+        Hs = {"g": None, "M": None, "T": None, "Fh": None}
+        for s in range(len(cells)):
+            lo, hi = int(off[s]), int(off[s + 1])
+            p_s, r_s, F_s = pos[lo:hi].contiguous(), radii[lo:hi].contiguous(), F[lo:hi].contiguous()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Hs["g"] = ctx.collision_graph(p_s, r_s, Hs["g"])
+            ij = Hs["g"].edges().to(torch.int64) + lo
+            gp, gq = workloads.pair_gamma_torch(4000, ij, t, t)
+            Hs["M"] = ctx.friction_assemble(Hs["g"], p_s, gp.contiguous(), gq.contiguous(), 1e-2, pr, Hs["M"])
+            Hs["T"] = ctx.max_spanning_tree(Hs["M"], Hs["T"])
+            Hs["Fh"] = ctx.tree_factor(Hs["M"], Hs["T"], Hs["Fh"])
+            ctx.pcg_solve(Hs["M"], Hs["Fh"], F_s, tol=args.tol, precision=pr)
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+        return np.array(lat)
+
+    lat = looped(sgp.PREC_F64)
+    lat_m = looped(prec) if prec != sgp.PREC_F64 else lat
     line = {
         "metric": METRIC, "value": round(len(cells) / step_s, 3), "unit": "instance solves/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
@@ -523,6 +638,11 @@ def run_batch(args):
                        "looped_plain_fp64_p50": round(float(np.percentile(lat, 50)), 3),
                        "looped_plain_fp64_p99": round(float(np.percentile(lat, 99)), 3)},
         "looped_plain_fp64": {"value": round(len(cells) / (lat.sum() / 1e3), 3), "unit": "instance solves/s"},
+        "looped_mixed": {"value": round(len(cells) / (lat_m.sum() / 1e3), 3), "unit": "instance solves/s",
+                         "p50_ms": round(float(np.percentile(lat_m, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat_m, 99)), 3),
+                         "note": "the same precision as the batch, one instance per solve: the batching gain "
+                                 "is value / this"},
         "gpu_launches": int(launches), "tuning": tuning, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -805,6 +925,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--cpu-baseline", dest="cpu_baseline", type=int, default=1)
     ap.add_argument("--compare", type=int, default=1, help="also time plain FP64 and block-Jacobi")
+    ap.add_argument("--configs", type=int, default=1,
+                    help="1: also run the other configurations (cube, sheet, batch, warm start) and record them")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the launch shapes with the library's autotuner before timing "
                          "(whole solves plus factor builds per candidate); 0: built-in defaults")

@@ -77,8 +77,10 @@ typedef struct {
 } sgp_solve_opts;
 
 typedef struct {
-    int64_t iterations;        /* PCG iterations (FP32 inner iterations summed for MIXED) */
-    int32_t outer_iterations;  /* MIXED refinement steps; 0 otherwise */
+    int64_t iterations;        /* PCG iterations (inner iterations summed for MIXED and
+                                  for sgp_fcg_solve) */
+    int32_t outer_iterations;  /* MIXED refinement steps, or sgp_fcg_solve's flexible
+                                  steps; 0 otherwise */
     int32_t status;            /* sgp_status of the solve */
     double rel_residual;       /* final recursive |r|/|F| (FP64 outer residual for MIXED) */
     double true_rel_residual;  /* |F - Gamma v|/|F| recomputed in FP64 at exit */
@@ -207,12 +209,12 @@ sgp_status sgp_tree_apply(sgp_ctx *ctx, const sgp_factor *factor, const double *
 sgp_status sgp_factor_info(const sgp_factor *factor, int32_t *rounds, int32_t *levels,
                            int64_t *l_blocks, int64_t *receiver_entries);
 /* Layout of the factor's binned solve: number of bins, vertices of the top
- * part (solved by one thread block), the subtree bound, and whether the FP32
- * and FP64 applications use it (1) or run one launch per contraction level
- * (0: the layout is off or does not fit in shared memory).  Any pointer may
- * be NULL. */
-sgp_status sgp_factor_layout(const sgp_factor *factor, int32_t *bins, int32_t *top, int32_t *bin_cap,
-                             int32_t *fp32, int32_t *fp64);
+ * part (solved by one thread block), products sent from bins to the top
+ * ("leaks"), the subtree bound, and whether the FP32 and FP64 applications
+ * use it (1) or run one launch per contraction level (0: the layout is off
+ * or does not fit in shared memory).  Any pointer may be NULL. */
+sgp_status sgp_factor_layout(const sgp_factor *factor, int32_t *bins, int32_t *top, int32_t *leaks,
+                             int32_t *bin_cap, int32_t *fp32, int32_t *fp64);
 void sgp_factor_destroy(sgp_factor *factor);
 
 /* ---- Section 1.1: preconditioned conjugate gradients ------------------------
@@ -245,6 +247,54 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_facto
 sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_factor *factor,
                                  int64_t n_instances, const int64_t *offsets, const double *F_dev,
                                  double *v_dev, const sgp_solve_opts *opts, sgp_solve_info *infos);
+
+/* ---- Section 3.1 (Vaidya's second preconditioner), Sections 3.3 and 5 --------
+ * Augmented spanning forest.  The forest of `tree` is cut into pieces: every
+ * tree is rooted at its smallest cell id, a depth-first preorder visits
+ * children in ascending id order and the trees in ascending order of their
+ * roots, and with s = ceil(n/t) a piece is a maximal set of tree-connected
+ * cells whose preorder numbers share one block [k s, (k+1) s) (connected
+ * subtrees of at most s cells, at least t of them, numbered in preorder of
+ * their top cell).  For every pair of pieces that the collision graph joins,
+ * the heaviest edge between them (weight descending, then edge index
+ * ascending) is added back; the augmented forest T' is the union with the
+ * tree edges and P' = gamma0 I + block Laplacian of T'.  t = 0 takes
+ * round(n^(1/4)) (the section's optimum).  *aug is created, or rebuilt in
+ * place when non-NULL.  INVALID_ARG for t < 0 or a tree that does not belong
+ * to the matrix.  Synchronises. */
+typedef struct sgp_aug sgp_aug;
+sgp_status sgp_augment_tree(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_tree *tree, int32_t t,
+                            sgp_aug **aug);
+/* t used, number of pieces, the piece bound s, edges of T' and how many of
+ * them are not tree edges.  Any pointer may be NULL. */
+sgp_status sgp_aug_info(const sgp_aug *aug, int32_t *t, int32_t *pieces, int32_t *piece_cap, int64_t *edges,
+                        int64_t *added);
+/* piece_dev (n int32, device): the piece of every cell.  Asynchronous. */
+sgp_status sgp_aug_pieces(sgp_ctx *ctx, const sgp_aug *aug, int32_t *piece_dev);
+/* edges_dev (edges int32, device): the edge ids of T', ascending.  Asynchronous. */
+sgp_status sgp_aug_edges(sgp_ctx *ctx, const sgp_aug *aug, int32_t *edges_dev);
+/* P' as a matrix handle (FP64) owned by `aug`: sgp_spmv gives P' v, and
+ * sgp_pcg_solve with the plain forest factor solves P' z = r -- the inner
+ * solve of sgp_fcg_solve.  NULL for a NULL aug. */
+const sgp_matrix *sgp_aug_matrix(const sgp_aug *aug);
+void sgp_aug_destroy(sgp_aug *aug);
+
+/* Flexible CG (Section 5: "nested (flexible) conjugate gradient") on
+ * Gamma v = F with the augmented preconditioner: each outer step applies
+ * z = P'^-1 r approximately by an inner PCG on P' preconditioned by the plain
+ * forest `factor` (from z = 0, to |r_in| <= inner_tol |r| with
+ * opts->inner_tol, 0 = 0.1 as in the paper, or inner_maxit iterations), then
+ * keeps one previous direction (Notay's flexible CG with truncation 1):
+ *   p = z - (z^T q_prev / p_prev^T q_prev) p_prev, q = Gamma p,
+ *   alpha = p^T r / p^T q, v += alpha p, r -= alpha q,
+ * until |r|_2 <= opts->tol |F|_2 or opts->maxit outer steps.  FP64 only
+ * (opts->precision F64, opts->precond TREE).  info->outer_iterations counts
+ * the outer steps, info->iterations the inner PCG iterations of all of them.
+ * INVALID_ARG if `aug` or `factor` was not built from this matrix.
+ * Synchronises. */
+sgp_status sgp_fcg_solve(sgp_ctx *ctx, const sgp_matrix *matrix, const sgp_aug *aug, const sgp_factor *factor,
+                         const double *F_dev, double *v_dev, const sgp_solve_opts *opts, int64_t inner_maxit,
+                         sgp_solve_info *info);
 
 /* ---- learned warm start (no counterpart in the paper) -----------------------
  * A message-passing network over the collision graph predicts the initial
@@ -317,31 +367,15 @@ typedef struct {
                             default 1024); read when a factor is built */
     int32_t batch_chunk; /* rows per work item of the batched solver: 0 (default
                             2048) or 256..65536 */
-    int32_t comp_size;   /* block of the tree factor's local phase: the forest is
-                            cut into blocks of comp_size consecutive vertices of a
-                            depth-first order, and the contraction levels that
-                            stay inside blocks run block by block in shared
-                            memory; 0 (none) or a power of two in 64..8192
-                            (default 0); read when a factor is built */
-    int32_t coop_cap;    /* the middle contraction levels, from the first one with
-                            at most coop_cap vertices left down to the tail, run in
-                            one cooperative kernel per direction with grid-wide
-                            barriers instead of one launch per level; 0 (none,
-                            default) or 256..16777216; read when a factor is built */
     int32_t spmv_ilp;    /* row groups each lane of the PCG product keeps in flight
                             at once: 0 (default, 1), 1 or 2 */
-    int32_t ctail_cap;   /* the last contraction levels, from the first one with at
-                            most ctail_cap vertices left, run in one cluster of
-                            thread blocks (16 or 8, whatever the device schedules)
-                            that keeps the tail in distributed shared memory; used
-                            when it starts before the one-block tail and fits;
-                            0 (none, default) or 256..16777216; read when a
-                            factor is built */
     int32_t bin_cap;     /* the tree solve's thread-block bins: contraction subtrees
                             of at most bin_cap vertices are solved by one thread
                             block each (three launches per application); 0 =
-                            default (1024), -1 = off (one launch per contraction
-                            level), else 64..8192; read when a factor is built */
+                            default (1024 for the FP32 solve of a MIXED factor;
+                            FP64 solves run one launch per contraction level),
+                            -1 = off in both precisions, 64..8192 = that cap in
+                            both precisions; read when a factor is built */
     double ms_per_iteration; /* sgp_autotune: the winning objective (ms per PCG
                                 iteration, or per factor build + solve); 0 from
                                 sgp_get_tuning */
@@ -350,11 +384,10 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *tuning);
 /* INVALID_ARG for a value outside the ranges above (nothing is changed). */
 sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *tuning);
 /* Pick the knobs by timing the caller's own system for each candidate, one
- * knob after the other: comp_size in {0, 256, 512, 1024, 2048, 4096},
- * tail_cap in {0, 256, 512, 1024, 2048, 4096, -1}, ctail_cap in
- * {0, 8192, 16384, 32768} and coop_cap in {0, 8192, 32768, 131072} (tree
- * preconditioner only; *factor is rebuilt
- * from `tree` for each candidate and left built with the chosen values), then
+ * knob after the other: tail_cap in {0, 256, 512, 1024, 2048, 4096, -1} and
+ * bin_cap in {0, -1, 512, 1024, 2048} (tree preconditioner only; *factor is
+ * rebuilt from `tree` for each candidate and left built with the chosen
+ * values), then
  * spmv_lpr in {1, 2, 4, 8} with spmv_ilp in {1, 2}, then, when n_instances > 0
  * (a batch with host `offsets`, as for sgp_pcg_solve_batched), batch_chunk in
  * {512, ..., 8192} with the batched solver timed throughout.  The objective

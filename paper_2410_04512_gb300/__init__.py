@@ -45,8 +45,7 @@ class SolveOpts(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("spmv_lpr", ctypes.c_int32), ("tail_cap", ctypes.c_int32), ("batch_chunk", ctypes.c_int32),
-                ("comp_size", ctypes.c_int32), ("coop_cap", ctypes.c_int32), ("spmv_ilp", ctypes.c_int32),
-                ("ctail_cap", ctypes.c_int32), ("bin_cap", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
+                ("spmv_ilp", ctypes.c_int32), ("bin_cap", ctypes.c_int32), ("ms_per_iteration", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,7 +99,7 @@ def load_library(path: str = LIB_PATH):
         "sgp_set_kernel_timing": ([P, I32], I32),
         "sgp_kernel_time": ([P, I32, ctypes.POINTER(D), ctypes.POINTER(I64), I32], I32),
         "sgp_launch_count": ([P, ctypes.POINTER(I64), I32], I32),
-        "sgp_factor_layout": ([P] + [ctypes.POINTER(I32)] * 5, I32),
+        "sgp_factor_layout": ([P] + [ctypes.POINTER(I32)] * 6, I32),
         "sgp_get_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "sgp_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "sgp_autotune": ([P, P, P, PP, I64, P, P, ctypes.POINTER(SolveOpts), I32, ctypes.POINTER(Tuning)], I32),
@@ -111,6 +110,14 @@ def load_library(path: str = LIB_PATH):
         "sgp_mpnn_backward": ([P, P, P, I32, ctypes.POINTER(D)], I32),
         "sgp_mpnn_step": ([P, P, ctypes.c_float], I32),
         "sgp_warm_start": ([P, P, P, P, P, P, P, I32, ctypes.POINTER(I32)], I32),
+        "sgp_augment_tree": ([P, P, P, I32, PP], I32),
+        "sgp_aug_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                          ctypes.POINTER(I64), ctypes.POINTER(I64)], I32),
+        "sgp_aug_pieces": ([P, P, P], I32),
+        "sgp_aug_edges": ([P, P, P], I32),
+        "sgp_aug_matrix": ([P], P),
+        "sgp_aug_destroy": ([P], None),
+        "sgp_fcg_solve": ([P, P, P, P, P, P, ctypes.POINTER(SolveOpts), I64, ctypes.POINTER(SolveInfo)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -125,7 +132,7 @@ def exported_symbols():
     import re
     with open(os.path.join(os.path.dirname(_HERE), "include", "sgp.h")) as f:
         txt = f.read()
-    return sorted(set(re.findall(r"^\s*(?:sgp_status|void|const char \*)\s*\*?(sgp_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:sgp_status|void|const \w+ \*)\s*\*?(sgp_\w+)\s*\(", txt, re.M)))
 
 
 def _ptr(t: torch.Tensor | None):
@@ -191,6 +198,10 @@ class Matrix(_Handle):
         return blocks, w
 
 
+class _BorrowedMatrix(Matrix):
+    _destroy = None
+
+
 class Tree(_Handle):
     _destroy = "sgp_tree_destroy"
 
@@ -225,9 +236,39 @@ class Factor(_Handle):
     def layout(self) -> dict:
         """The binned solve's layout: bins, top vertices, subtree bound, and
         whether the FP32 / FP64 applications use it."""
-        v = [ctypes.c_int32() for _ in range(5)]
+        v = [ctypes.c_int32() for _ in range(6)]
         self.ctx._ok(_lib.sgp_factor_layout(self.ptr, *[ctypes.byref(x) for x in v]))
-        return dict(zip(("bins", "top", "bin_cap", "fp32", "fp64"), (x.value for x in v)))
+        return dict(zip(("bins", "top", "leaks", "bin_cap", "fp32", "fp64"), (x.value for x in v)))
+
+
+class Augmented(_Handle):
+    """The augmented spanning forest T' and P' (Section 3.1)."""
+    _destroy = "sgp_aug_destroy"
+
+    def info(self) -> dict:
+        t, k, cap = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ne, na = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx._ok(_lib.sgp_aug_info(self.ptr, ctypes.byref(t), ctypes.byref(k), ctypes.byref(cap),
+                                       ctypes.byref(ne), ctypes.byref(na)))
+        return {"t": t.value, "pieces": k.value, "piece_cap": cap.value, "edges": ne.value, "added": na.value}
+
+    def pieces(self, n: int) -> torch.Tensor:
+        out = torch.empty((n,), dtype=torch.int32, device=self.ctx.device)
+        self.ctx._ok(_lib.sgp_aug_pieces(self.ctx.ptr, self.ptr, _ptr(out)))
+        return out
+
+    def edges(self) -> torch.Tensor:
+        out = torch.empty((self.info()["edges"],), dtype=torch.int32, device=self.ctx.device)
+        self.ctx._ok(_lib.sgp_aug_edges(self.ctx.ptr, self.ptr, _ptr(out)))
+        return out
+
+    def matrix(self, n: int) -> "Matrix":
+        """P' as a matrix handle owned by this object (not destroyed with
+        the returned wrapper)."""
+        m = _BorrowedMatrix(self.ctx, n, self.info()["edges"], PREC_F64)
+        m.ptr = ctypes.c_void_p(_lib.sgp_aug_matrix(self.ptr))
+        m.owner = self
+        return m
 
 
 class Mpnn(_Handle):
@@ -338,6 +379,30 @@ class Context:
             self._ok(rc)
         return v, info
 
+    # -- augmented spanning forest and flexible CG (Sections 3.1, 5) ---------
+    def augment_tree(self, M: Matrix, T: Tree, t: int = 0, aug: "Augmented | None" = None) -> "Augmented":
+        A = aug if aug is not None else Augmented(self)
+        self._ok(_lib.sgp_augment_tree(self.ptr, M.ptr, T.ptr, t, ctypes.byref(A.ptr)))
+        return A
+
+    def fcg_solve(self, M: Matrix, A: "Augmented", Fh: Factor, F: torch.Tensor, v: torch.Tensor | None = None,
+                  tol: float = 1e-8, maxit: int = 100000, inner_tol: float = 0.1, inner_maxit: int = 1000,
+                  x0_given: bool = False, raise_on_error: bool = True):
+        """Flexible CG with the augmented preconditioner applied by an inner
+        PCG (Section 5); returns (v, Info) with Info.outer_iterations the
+        flexible steps and Info.iterations the inner iterations."""
+        _check_vec(F, M.n, name="F")
+        v = torch.zeros_like(F) if v is None else v
+        _check_vec(v, M.n, name="v")
+        o = SolveOpts(tol, maxit, PRECOND_TREE, PREC_F64, int(x0_given), 0, inner_tol)
+        inf = SolveInfo()
+        rc = _lib.sgp_fcg_solve(self.ptr, M.ptr, A.ptr, Fh.ptr, _ptr(F), _ptr(v), ctypes.byref(o), inner_maxit,
+                                ctypes.byref(inf))
+        info = Info(inf.iterations, inf.outer_iterations, inf.status, inf.rel_residual, inf.true_rel_residual)
+        if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
+            self._ok(rc)
+        return v, info
+
     # -- batches of independent configurations ------------------------------
     def collision_graph_batched(self, offsets, pos: torch.Tensor, radii: torch.Tensor,
                                 graph: Graph | None = None) -> Graph:
@@ -423,10 +488,10 @@ class Context:
         self._ok(_lib.sgp_get_tuning(self.ptr, ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, comp_size: int = 0,
-                   coop_cap: int = 0, spmv_ilp: int = 0, ctail_cap: int = 0, bin_cap: int = 0):
+    def set_tuning(self, spmv_lpr: int = 0, tail_cap: int = 1024, batch_chunk: int = 0, spmv_ilp: int = 0,
+                   bin_cap: int = 0):
         """Set the launch-shape knobs (the defaults are the library's)."""
-        t = Tuning(spmv_lpr, tail_cap, batch_chunk, comp_size, coop_cap, spmv_ilp, ctail_cap, bin_cap, 0.0)
+        t = Tuning(spmv_lpr, tail_cap, batch_chunk, spmv_ilp, bin_cap, 0.0)
         self._ok(_lib.sgp_set_tuning(self.ptr, ctypes.byref(t)))
 
     def autotune(self, M: Matrix, T: Tree | None, Fh: Factor | None, F: torch.Tensor, offsets=None,

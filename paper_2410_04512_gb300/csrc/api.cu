@@ -209,10 +209,7 @@ sgp_status kt_begin(sgp_ctx *ctx, int kclass, cudaEvent_t *ev)
     *ev = nullptr;
     if (!ctx->timing) return SGP_OK;
     if (ctx->capture_sink) {
-        // inside a capture: an event-record node owned by the graph entry;
-        // the product and the tree solve are timed there (not the cheap
-        // vector kernels), to keep the graph lean
-        if (kclass == SGP_KT_PCG_VECTOR) return SGP_OK;
+        // inside a capture: an event-record node owned by the graph entry
         SGP_CUDA(ctx, cudaEventCreate(ev));
         SGP_CUDA(ctx, cudaEventRecordWithFlags(*ev, ctx->stream, cudaEventRecordExternal));
         return SGP_OK;

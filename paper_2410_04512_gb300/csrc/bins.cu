@@ -1621,8 +1621,12 @@ sgp_status bins_build(sgp_ctx *ctx, sgp_factor *F, const sgp_matrix *M)
     BinLayout &B = F->bl;
     B.ok32 = B.ok64 = 0;
     const int32_t n = (int32_t)F->n, LV = F->levels;
-    const int bmax = ctx->bin_cap;
+    // default (0): the FP32 solve of a MIXED factor only, at 1024 -- measured,
+    // FP64 bins were slower than the level kernels on the 1e6 spheroid
+    const int bmax = ctx->bin_cap == 0 ? 1024 : ctx->bin_cap;
+    const bool f64_bins = ctx->bin_cap > 0;
     if (n == 0 || bmax <= 0 || LV == 0) return SGP_OK;
+    if (!f64_bins && F->precision != SGP_PREC_MIXED) return SGP_OK;
     B.LV = LV;
     B.LVP = pad4(LV + 1);
     B.bmax = bmax;
@@ -1946,6 +1950,7 @@ sgp_status bins_build(sgp_ctx *ctx, sgp_factor *F, const sgp_matrix *M)
     for (int s = 0; s < 2; ++s) {
         const bool f32 = s == 0;
         if (f32 && F->precision != SGP_PREC_MIXED) continue;
+        if (!f32 && !f64_bins) continue;
         const bool fits = B.smA[s] <= (size_t)SMEM_MAX && B.smC[s] <= (size_t)SMEM_MAX && B.smTnd[s] <= (size_t)SMEM_MAX &&
                           B.smA0[s] <= (size_t)SMEM_MAX && B.smC0[s] <= (size_t)SMEM_MAX;
         if (!fits) continue;

@@ -25,7 +25,6 @@
 // replays them forward (receivers gather L_qc z_c) and backward (each
 // eliminated vertex gathers from its receivers).  All sums run in a fixed
 // order, so results are bitwise reproducible.
-#include <cooperative_groups.h>
 
 #include "sgp_internal.cuh"
 
@@ -118,282 +117,6 @@ __global__ void k_acc_init(const int32_t *__restrict__ adj_ptr, int64_t n,
     alive[v] = (int32_t)v;
 }
 
-// ----------------------------------------- depth-first preorder of the forest
-// Euler tour: directed slot s of u (u -> v = nbr[s]) is followed by the slot
-// after twin(s) in v's sorted list, cyclically.  Each tree's tour starts at
-// its root's first slot (the root is the tree's label from the spanning
-// forest); the slot whose successor would wrap around to it ends the tour.
-__global__ void k_et_init(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ nbr,
-                          const int32_t *__restrict__ twin, const int32_t *__restrict__ comp, int64_t n,
-                          int32_t *succ, int32_t *dist)
-{
-    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s) {
-        const int32_t v = nbr[s], t = twin[s];
-        const bool wrap = t + 1 >= adj_ptr[v + 1];
-        if (wrap && comp[v] == v) {
-            succ[s] = -1;
-            dist[s] = 0;
-        } else {
-            succ[s] = wrap ? adj_ptr[v] : t + 1;
-            dist[s] = 1;
-        }
-    }
-}
-
-// one round of pointer jumping: dist becomes the number of slots to the end
-__global__ void k_et_jump(int64_t m2, const int32_t *__restrict__ succ, const int32_t *__restrict__ dist,
-                          int32_t *succ2, int32_t *dist2)
-{
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= m2) return;
-    const int32_t nx = succ[s];
-    if (nx < 0) {
-        succ2[s] = -1;
-        dist2[s] = dist[s];
-    } else {
-        succ2[s] = succ[nx];
-        dist2[s] = dist[s] + dist[nx];
-    }
-}
-
-__global__ void k_comp_internal(int64_t n, const int32_t *__restrict__ comp, const int32_t *__restrict__ int_of,
-                                const int32_t *__restrict__ orig_of, int32_t *out)
-{
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v < n) out[v] = int_of[comp[orig_of[v]]];
-}
-
-__global__ void k_root_flag(const int32_t *__restrict__ comp, int64_t n, int32_t *flag)
-{
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v < n) flag[v] = comp[v] == (int32_t)v;
-}
-
-// tree index (rank of the root among roots) and tree sizes
-__global__ void k_tree_index(const int32_t *__restrict__ comp, const int32_t *__restrict__ rank, int64_t n,
-                             int32_t *tid, int32_t *size)
-{
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const int32_t t = rank[comp[v]];
-    tid[v] = t;
-    atomicAdd(size + t, 1);
-}
-
-// A slot is a down edge (parent -> child) if the tour takes it before its
-// twin.  Down flags are laid out in tour order, trees one after another
-// (tree t's tour starts at 2 (voff[t] - t), voff the exclusive sum of sizes).
-__device__ __forceinline__ int32_t tour_index(int32_t s, int32_t t, const int32_t *voff, const int32_t *size,
-                                              const int32_t *dist)
-{
-    return 2 * (voff[t] - t) + (2 * (size[t] - 1) - 1 - dist[s]);
-}
-
-__global__ void k_et_down(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ twin,
-                          const int32_t *__restrict__ dist, const int32_t *__restrict__ tid,
-                          const int32_t *__restrict__ voff, const int32_t *__restrict__ size, int64_t n,
-                          int64_t ns, int32_t *down, int *err)
-{
-    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    const int32_t t = tid[u];
-    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s) {
-        const int32_t k = tour_index(s, t, voff, size, dist);
-        if (k < 0 || k >= ns) {      // not a tour: record, skip the write
-            atomicOr(err, 8);
-            continue;
-        }
-        down[k] = dist[s] > dist[twin[s]];
-    }
-}
-
-// preorder number: the root of tree t gets voff[t]; the head of a down edge
-// gets 1 + (down edges before it in the tour) + t
-__global__ void k_preorder(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ nbr,
-                           const int32_t *__restrict__ twin, const int32_t *__restrict__ dist,
-                           const int32_t *__restrict__ tid, const int32_t *__restrict__ voff,
-                           const int32_t *__restrict__ size, const int32_t *__restrict__ dscan,
-                           const int32_t *__restrict__ comp, int64_t n, int64_t ns, int32_t *pre, int *err)
-{
-    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    const int32_t t = tid[u];
-    if (comp[u] == (int32_t)u) pre[u] = voff[t];
-    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s)
-        if (dist[s] > dist[twin[s]]) {
-            const int32_t k = tour_index(s, t, voff, size, dist);
-            if (k < 0 || k >= ns) {
-                atomicOr(err, 8);
-                continue;
-            }
-            pre[nbr[s]] = 1 + dscan[k] + t;
-        }
-}
-
-// inverse permutation, and the vertices with a tree neighbour in another block
-__global__ void k_blocks(const int32_t *__restrict__ adj_ptr, const int32_t *__restrict__ nbr,
-                         const int32_t *__restrict__ pre, int64_t n, int32_t shift, int32_t *inv_pre,
-                         int32_t *pinned, int *err)
-{
-    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    const int32_t pu = pre[u];
-    if (pu < 0 || pu >= n) {
-        atomicOr(err, 8);
-        pinned[u] = 1;
-        return;
-    }
-    inv_pre[pu] = (int32_t)u;
-    int32_t pin = 0;
-    for (int32_t s = adj_ptr[u]; s < adj_ptr[u + 1]; ++s)
-        if ((pre[nbr[s]] >> shift) != (pu >> shift)) pin = 1;
-    pinned[u] = pin;
-}
-
-// in-block index of each listed vertex
-__global__ void k_loc_map(const int32_t *src, const int32_t *__restrict__ pre, int32_t count,
-                          int32_t mask, int32_t *dst)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < count) dst[k] = pre[src[k]] & mask;
-}
-
-// out[c] = first k in [lo, hi) whose vertex lies in block >= c (the list is
-// in preorder within a level), c = 0..nb
-__global__ void k_block_ranges(const int32_t *__restrict__ list, const int32_t *__restrict__ pre, int32_t lo,
-                               int32_t hi, int32_t nb, int32_t shift, int32_t *out)
-{
-    int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > nb) return;
-    int32_t a = lo, b = hi;
-    while (a < b) {
-        const int32_t m = (a + b) >> 1;
-        if ((pre[list[m]] >> shift) < c) a = m + 1;
-        else b = m;
-    }
-    out[c] = a;
-}
-
-// ------------------------------------------- block-major layout of local levels
-// Per block c, for kind k (0 forward entries, 1 contributors, 2 positions,
-// 3 pairs): prefix counts over the local levels (nlev + 1 values) and totals.
-__global__ void k_bm_tables(int32_t nlev, int32_t nb, const int32_t *__restrict__ roff,
-                            const int32_t *__restrict__ poff, const int32_t *__restrict__ rc_ptr,
-                            const int32_t *__restrict__ pr_ptr, int32_t *tab, int32_t *tot, int32_t *mx)
-{
-    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nb) return;
-    int32_t *t = tab + (size_t)c * 4 * (nlev + 1);
-    int32_t acc[4] = {0, 0, 0, 0};
-    for (int32_t l = 0; l < nlev; ++l) {
-        const int32_t *ro = roff + (size_t)l * (nb + 1), *po = poff + (size_t)l * (nb + 1);
-        const int32_t r0 = ro[c], r1 = ro[c + 1], p0 = po[c], p1 = po[c + 1];
-        const int32_t d[4] = {r1 - r0, rc_ptr[r1] - rc_ptr[r0], p1 - p0, pr_ptr[p1] - pr_ptr[p0]};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            t[k * (nlev + 1) + l] = acc[k];
-            acc[k] += d[k];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        t[k * (nlev + 1) + nlev] = acc[k];
-        tot[(size_t)k * nb + c] = acc[k];
-        atomicMax(mx + k, acc[k]);
-    }
-}
-
-// position in the block-major array of kind k of an entry at offset `off`
-// within block c's segment of level l
-__device__ __forceinline__ int32_t bm_at(const int32_t *tab, const int32_t *base, int32_t nlev, int32_t nb,
-                                         int32_t c, int32_t l, int k, int32_t off)
-{
-    return base[(size_t)k * (nb + 1) + c] + tab[((size_t)c * 4 + k) * (nlev + 1) + l] + off;
-}
-
-__global__ void k_bm_recv(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t k0, int32_t cnt,
-                          const int32_t *__restrict__ rv, const int32_t *__restrict__ pre,
-                          const int32_t *__restrict__ roff, const int32_t *__restrict__ rc_ptr,
-                          const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
-                          const int32_t *__restrict__ loc_r, int32_t *bm_q, int32_t *bm_beg)
-{
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int32_t k = k0 + i;
-    const int32_t c = pre[rv[k]] >> shift;
-    const int32_t seg = roff[(size_t)l * (nb + 1) + c];
-    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 0, k - seg);
-    bm_q[e] = loc_r[k];
-    bm_beg[e] = tab[((size_t)c * 4 + 1) * (nlev + 1) + l] + (rc_ptr[k] - rc_ptr[seg]);
-}
-
-__global__ void k_bm_contrib(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t j0, int32_t cnt,
-                             const int32_t *__restrict__ ctv, const int32_t *__restrict__ pre,
-                             const int32_t *__restrict__ roff, const int32_t *__restrict__ rc_ptr,
-                             const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
-                             const int32_t *__restrict__ loc_c, const double *__restrict__ Lf,
-                             const float *__restrict__ Lf32, int32_t *bm_cloc, double *bm_Lf, float *bm_Lf32)
-{
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int32_t j = j0 + i;
-    const int32_t c = pre[ctv[j]] >> shift;
-    const int32_t seg = rc_ptr[roff[(size_t)l * (nb + 1) + c]];
-    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 1, j - seg);
-    bm_cloc[e] = loc_c[j];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) bm_Lf[9 * (int64_t)e + a] = Lf[9 * (int64_t)j + a];
-    if (Lf32)
-#pragma unroll
-        for (int a = 0; a < 9; ++a) bm_Lf32[9 * (int64_t)e + a] = Lf32[9 * (int64_t)j + a];
-}
-
-__global__ void k_bm_pos(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t t0, int32_t cnt,
-                         const int32_t *__restrict__ ord, const int32_t *__restrict__ pre,
-                         const int32_t *__restrict__ poff, const int32_t *__restrict__ pr_ptr,
-                         const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
-                         const int32_t *__restrict__ loc_o, const double *__restrict__ Dinv,
-                         const float *__restrict__ Dinv32, int32_t *bm_oloc, int32_t *bm_pbeg, double *bm_D,
-                         float *bm_D32)
-{
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int32_t t = t0 + i;
-    const int32_t c = pre[ord[t]] >> shift;
-    const int32_t seg = poff[(size_t)l * (nb + 1) + c];
-    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 2, t - seg);
-    bm_oloc[e] = loc_o[t];
-    bm_pbeg[e] = tab[((size_t)c * 4 + 3) * (nlev + 1) + l] + (pr_ptr[t] - pr_ptr[seg]);
-#pragma unroll
-    for (int a = 0; a < 6; ++a) bm_D[6 * (int64_t)e + a] = Dinv[6 * (int64_t)t + a];
-    if (Dinv32)
-#pragma unroll
-        for (int a = 0; a < 6; ++a) bm_D32[6 * (int64_t)e + a] = Dinv32[6 * (int64_t)t + a];
-}
-
-__global__ void k_bm_pair(int32_t l, int32_t nlev, int32_t nb, int32_t shift, int32_t q0, int32_t cnt,
-                          const int32_t *__restrict__ pr_c, const int32_t *__restrict__ pre,
-                          const int32_t *__restrict__ poff, const int32_t *__restrict__ pr_ptr,
-                          const int32_t *__restrict__ tab, const int32_t *__restrict__ base,
-                          const int32_t *__restrict__ loc_q, const double *__restrict__ L,
-                          const float *__restrict__ L32, int32_t *bm_qloc, double *bm_Lb, float *bm_Lb32)
-{
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int32_t p = q0 + i;
-    const int32_t c = pre[pr_c[p]] >> shift;
-    const int32_t seg = pr_ptr[poff[(size_t)l * (nb + 1) + c]];
-    const int32_t e = bm_at(tab, base, nlev, nb, c, l, 3, p - seg);
-    bm_qloc[e] = loc_q[p];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) bm_Lb[9 * (int64_t)e + a] = L[9 * (int64_t)p + a];
-    if (L32)
-#pragma unroll
-        for (int a = 0; a < 9; ++a) bm_Lb32[9 * (int64_t)e + a] = L32[9 * (int64_t)p + a];
-}
-
 // -------------------------------------------------------- structure: select
 __device__ __forceinline__ uint32_t mix32(uint32_t x)
 {
@@ -422,13 +145,8 @@ struct Sim {
 // degree-2 neighbours by the level's hash.  No two chosen vertices are
 // adjacent, and each has at most two neighbours, so eliminating them all at
 // once equals eliminating them one by one: the forest stays a forest.
-// Pinned vertices (local phase: a tree neighbour in another block) are never
-// chosen, and the rules that defer to a neighbour ignore pinned neighbours.
-__device__ __forceinline__ void select_vertex(const Sim &S, int32_t v, int32_t level, uint32_t salt,
-                                              const int32_t *__restrict__ pin)
+__device__ __forceinline__ void select_vertex(const Sim &S, int32_t v, int32_t level, uint32_t salt)
 {
-    if (pin && pin[v]) return;
-    auto free_ = [&](int32_t u) { return !(pin && pin[u]); };
     const int32_t d = S.deg[v];
     if (d == 0) {
         S.lev[v] = level;
@@ -444,7 +162,7 @@ __device__ __forceinline__ void select_vertex(const Sim &S, int32_t v, int32_t l
         }
     const int32_t a = S.nbr[e1];
     if (d == 1) {
-        if (S.deg[a] == 1 && a > v && free_(a)) return;
+        if (S.deg[a] == 1 && a > v) return;
         S.lev[v] = level;
         S.nrec[v] = 1;
         S.rq[v] = make_int2(a, -1);
@@ -454,9 +172,9 @@ __device__ __forceinline__ void select_vertex(const Sim &S, int32_t v, int32_t l
     }
     const int32_t b = S.nbr[e2];
     const int32_t da = S.deg[a], db = S.deg[b];
-    if ((da == 1 && free_(a)) || (db == 1 && free_(b))) return;
-    if (da == 2 && free_(a) && key_less(a, v, salt)) return;
-    if (db == 2 && free_(b) && key_less(b, v, salt)) return;
+    if (da == 1 || db == 1) return;
+    if (da == 2 && key_less(a, v, salt)) return;
+    if (db == 2 && key_less(b, v, salt)) return;
     const bool sw = a > b;
     S.lev[v] = level;
     S.nrec[v] = 2;
@@ -465,11 +183,10 @@ __device__ __forceinline__ void select_vertex(const Sim &S, int32_t v, int32_t l
     S.ren[v] = sw ? make_int2(e2, e1) : make_int2(e1, e2);
 }
 
-__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt,
-                         const int32_t *__restrict__ pin)
+__global__ void k_select(Sim S, const int32_t *__restrict__ A, int32_t na, int32_t level, uint32_t salt)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < na) select_vertex(S, A[k], level, salt, pin);
+    if (k < na) select_vertex(S, A[k], level, salt);
 }
 
 // ----------------------------------------------------- structure: bookkeeping
@@ -486,71 +203,6 @@ __global__ void k_flags(const int32_t *__restrict__ A, int32_t na, int mode, int
     else if (mode == 1) f = (rflag[v] != 0);
     else f = (lev[v] == -1);
     flag[k] = f;
-}
-
-// Stable scatter of flagged list entries to dst[base + off]; mode 0 also
-// records each vertex's position, mode 1 clears the receiver flag.
-__global__ void k_scatter_list(const int32_t *__restrict__ A, int32_t na,
-                               const int32_t *__restrict__ flag, const int32_t *__restrict__ off,
-                               int32_t *dst, int32_t base, int mode, int32_t *pos, int32_t *rflag)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= na || !flag[k]) return;
-    int32_t v = A[k];
-    int32_t at = base + off[k];
-    dst[at] = v;
-    if (mode == 0) pos[v] = at;
-    if (mode == 1) rflag[v] = 0;
-}
-
-// pairs of this level's eliminated vertices: nrec -> tmp (to be scanned)
-__global__ void k_level_nrec(const int32_t *__restrict__ ord, int32_t p0, int32_t cnt,
-                             const int32_t *__restrict__ nrec, int32_t *tmp)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < cnt) tmp[k] = nrec[ord[p0 + k]];
-}
-
-__global__ void k_level_pairs(const int32_t *__restrict__ ord, int32_t p0, int32_t cnt,
-                              const int32_t *__restrict__ off, int32_t pair0,
-                              const int32_t *__restrict__ nrec, const int2 *__restrict__ rq,
-                              int32_t *pr_ptr, int32_t *pr_q, int32_t *pr_c, int32_t *rflag)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cnt) return;
-    int32_t c = ord[p0 + k];
-    int32_t p = pair0 + off[k];
-    pr_ptr[p0 + k] = p;
-    int32_t r = nrec[c];
-    int2 q = rq[c];
-    if (r > 0) { pr_q[p] = q.x; pr_c[p] = c; rflag[q.x] = 1; }
-    if (r > 1) { pr_q[p + 1] = q.y; pr_c[p + 1] = c; rflag[q.y] = 1; }
-}
-
-// Contributors of each receiver: its live entries whose neighbour goes at
-// this level, in list order.  COUNT pass, then FILL pass.
-template <bool FILL>
-__global__ void k_contrib(Sim S, const int32_t *__restrict__ rv, int32_t r0, int32_t cnt,
-                          int32_t level, const int32_t *__restrict__ pos,
-                          const int32_t *__restrict__ pr_ptr, int32_t *count,
-                          const int32_t *__restrict__ off, int32_t ct0, int32_t *rc_ptr, int32_t *ct)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cnt) return;
-    int32_t q = rv[r0 + k];
-    int32_t c_n = 0;
-    int32_t at = FILL ? ct0 + off[k] : 0;
-    if (FILL) rc_ptr[r0 + k] = at;
-    for (int32_t s = S.adj_ptr[q]; s < S.adj_ptr[q + 1]; ++s) {
-        int32_t c = S.nbr[s];
-        if (c < 0 || S.lev[c] != level) continue;
-        if (FILL) {
-            int32_t which = (S.rq[c].x == q) ? 0 : 1;
-            ct[at + c_n] = pr_ptr[pos[c]] + which;
-        }
-        ++c_n;
-    }
-    if (!FILL) count[k] = c_n;
 }
 
 // Structural update of a merged level: a leaf leaves its neighbour's list;
@@ -573,11 +225,6 @@ __device__ __forceinline__ void apply_vertex(const Sim &S, int32_t v, int32_t nt
     }
 }
 
-__global__ void k_apply(Sim S, const int32_t *__restrict__ ord, int32_t p0, int32_t cnt, int32_t nt)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < cnt) apply_vertex(S, ord[p0 + k], nt);
-}
 
 // ------------------------- structure: a level with its counts on the device
 // The same steps as above for a level whose counts stay on the device until
@@ -721,7 +368,7 @@ __global__ void __launch_bounds__(SB) k_levels_small(Sim S, int32_t *A, int32_t 
         const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
         int32_t lo, hi;
         chunk(na, lo, hi);
-        for (int32_t k = lo; k < hi; ++k) select_vertex(S, A[k], level, salt, nullptr);
+        for (int32_t k = lo; k < hi; ++k) select_vertex(S, A[k], level, salt);
         __syncthreads();
         // eliminated vertices -> ord, pos
         int32_t c = 0, ne;
@@ -1046,344 +693,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 8) k_tree_bwd(const
     w[3 * (int64_t)c + 2] = z[2];
 }
 
-// Local levels: one thread block per block of comp_size consecutive
-// preorder numbers.  Every vertex eliminated in a local level has all its
-// tree neighbours (and so all its receivers) in its own block, so the block
-// runs all local levels on its slice of the vector in shared memory, with
-// block barriers between levels, and touches global memory only to gather
-// the slice at the start and scatter it at the end.
-struct Local {
-    int32_t nlev, nb, shift, n;
-    const int32_t *inv_pre, *roff, *poff, *rc_ptr, *pr_ptr, *loc_r, *loc_c, *loc_o, *loc_q;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_local_fwd(Local a, const T *__restrict__ Lf, T *w, const int *done)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sw = reinterpret_cast<T *>(smem_raw);
-    pdl_trigger();
-    if (done && *done) return;
-    const int32_t c = blockIdx.x, base = c << a.shift;
-    const int32_t cnt = min(1 << a.shift, a.n - base);
-    pdl_wait();
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        sw[3 * i] = w[3 * v];
-        sw[3 * i + 1] = w[3 * v + 1];
-        sw[3 * i + 2] = w[3 * v + 2];
-    }
-    __syncthreads();
-    for (int l = 0; l < a.nlev; ++l) {
-        const int32_t *ro = a.roff + (size_t)l * (a.nb + 1);
-        const int32_t k1 = ro[c + 1];
-        for (int32_t k = ro[c] + threadIdx.x; k < k1; k += blockDim.x) {
-            T s[3] = {0, 0, 0};
-            for (int32_t j = a.rc_ptr[k]; j < a.rc_ptr[k + 1]; ++j) {
-                T y[3];
-                full_mv(Lf + 9 * (int64_t)j, sw + 3 * a.loc_c[j], y);
-                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
-            }
-            const int32_t q = a.loc_r[k];
-            sw[3 * q] -= s[0];
-            sw[3 * q + 1] -= s[1];
-            sw[3 * q + 2] -= s[2];
-        }
-        __syncthreads();
-    }
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        w[3 * v] = sw[3 * i];
-        w[3 * v + 1] = sw[3 * i + 1];
-        w[3 * v + 2] = sw[3 * i + 2];
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_local_bwd(Local a, const T *__restrict__ L, const T *__restrict__ Dinv,
-                                                   T *w, const int *done)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sw = reinterpret_cast<T *>(smem_raw);
-    pdl_trigger();
-    if (done && *done) return;
-    const int32_t c = blockIdx.x, base = c << a.shift;
-    const int32_t cnt = min(1 << a.shift, a.n - base);
-    pdl_wait();
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        sw[3 * i] = w[3 * v];
-        sw[3 * i + 1] = w[3 * v + 1];
-        sw[3 * i + 2] = w[3 * v + 2];
-    }
-    __syncthreads();
-    for (int l = a.nlev - 1; l >= 0; --l) {
-        const int32_t *po = a.poff + (size_t)l * (a.nb + 1);
-        const int32_t t1 = po[c + 1];
-        for (int32_t t = po[c] + threadIdx.x; t < t1; t += blockDim.x) {
-            const int32_t i = a.loc_o[t];
-            T z[3];
-            sym_mv(Dinv + 6 * (int64_t)t, sw + 3 * i, z);
-            for (int32_t p = a.pr_ptr[t]; p < a.pr_ptr[t + 1]; ++p) {
-                T u[3];
-                full_mtv(L + 9 * (int64_t)p, sw + 3 * a.loc_q[p], u);
-                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
-            }
-            sw[3 * i] = z[0];
-            sw[3 * i + 1] = z[1];
-            sw[3 * i + 2] = z[2];
-        }
-        __syncthreads();
-    }
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        w[3 * v] = sw[3 * i];
-        w[3 * v + 1] = sw[3 * i + 1];
-        w[3 * v + 2] = sw[3 * i + 2];
-    }
-}
-
-// Middle levels in one cooperative kernel per direction: the grid walks the
-// levels [coop_level, tail_level) with a grid-wide barrier between levels
-// instead of one launch per level (same per-entry arithmetic and order as
-// k_tree_fwd / k_tree_bwd).  Launched cooperatively, so every block is
-// resident and the barrier is CUDA's own.
-template <typename T, bool FWD>
-__global__ void __launch_bounds__(256) k_tree_coop(int32_t nlev, const int32_t *__restrict__ lidx,
-                                                   const int32_t *__restrict__ rv, const int32_t *__restrict__ rc_ptr,
-                                                   const int32_t *__restrict__ ctv, const T *__restrict__ Lf,
-                                                   const int32_t *__restrict__ ord, const int32_t *__restrict__ pr_ptr,
-                                                   const int32_t *__restrict__ pr_q, const T *__restrict__ L,
-                                                   const T *__restrict__ Dinv, T *w, const int *done)
-{
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    if (done && *done) return;   // the same value in every block: no block reaches a barrier
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    if (FWD) {
-        for (int32_t l = 0; l < nlev; ++l) {
-            const int32_t r0 = lidx[nlev + 1 + l], r1 = lidx[nlev + 2 + l];
-            for (int64_t k = r0 + tid; k < r1; k += nth) {
-                const int32_t q = rv[k];
-                T s[3] = {0, 0, 0};
-                for (int32_t j = rc_ptr[k]; j < rc_ptr[k + 1]; ++j) {
-                    const int64_t c = ctv[j];
-                    T x[3] = {w[3 * c], w[3 * c + 1], w[3 * c + 2]};
-                    T y[3];
-                    full_mv(Lf + 9 * (int64_t)j, x, y);
-                    s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
-                }
-                w[3 * (int64_t)q] -= s[0];
-                w[3 * (int64_t)q + 1] -= s[1];
-                w[3 * (int64_t)q + 2] -= s[2];
-            }
-            if (l + 1 < nlev) grid.sync();
-        }
-    } else {
-        for (int32_t l = nlev - 1; l >= 0; --l) {
-            const int32_t p0 = lidx[l], p1 = lidx[l + 1];
-            for (int64_t t = p0 + tid; t < p1; t += nth) {
-                const int64_t c = ord[t];
-                T x[3] = {w[3 * c], w[3 * c + 1], w[3 * c + 2]};
-                T z[3];
-                sym_mv(Dinv + 6 * t, x, z);
-                for (int32_t p = pr_ptr[t]; p < pr_ptr[t + 1]; ++p) {
-                    const int64_t q = pr_q[p];
-                    T y[3] = {w[3 * q], w[3 * q + 1], w[3 * q + 2]};
-                    T u[3];
-                    full_mtv(L + 9 * (int64_t)p, y, u);
-                    z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
-                }
-                w[3 * c] = z[0];
-                w[3 * c + 1] = z[1];
-                w[3 * c + 2] = z[2];
-            }
-            if (l > 0) grid.sync();
-        }
-    }
-}
-
-template <typename T, bool FWD>
-static sgp_status launch_coop(sgp_ctx *ctx, const sgp_factor *F, int32_t nlev, const int32_t *lidx,
-                              const int32_t *rv, const int32_t *rc, const int32_t *ctv, const T *Lf,
-                              const int32_t *ord, const int32_t *prp, const int32_t *prq, const T *L,
-                              const T *Dinv, T *w, const int *done)
-{
-    auto kern = k_tree_coop<T, FWD>;
-    int per_sm = 0;
-    SGP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
-    if (ctx->num_sms <= 0) SGP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    const int grid = std::max(1, std::min(per_sm, 2) * ctx->num_sms);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = ctx->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, nlev, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done);
-    ctx->launches++;
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return sgp_fail(ctx, SGP_ERR_CUDA, "launch of k_tree_coop failed: %s", cudaGetErrorString(e));
-    (void)F;
-    return SGP_OK;
-}
-
 // shared-memory carving: every piece starts on a 16-byte boundary
 __host__ __device__ inline size_t tail_align(size_t b) { return (b + 15) & ~size_t(15); }
-
-// Staged local levels: the block's share of the block-major arrays (its
-// forward entries and contributors, or its positions and pairs, level after
-// level) is copied into shared memory with contiguous loads before the wait
-// on the previous kernel; the levels then run from shared memory.
-struct LocalS {
-    int32_t nlev, nb, shift, n;
-    const int32_t *inv_pre, *tab, *base;
-    const int32_t *q, *beg, *cloc, *oloc, *pbeg, *qloc;
-};
-
-template <typename T>
-__host__ __device__ inline size_t local_fwd_smem(int32_t B, int32_t nlev, int32_t me, int32_t mc)
-{
-    return tail_align(sizeof(T) * 3 * (size_t)B) + tail_align(sizeof(T) * 9 * (size_t)mc) +
-           tail_align(4 * (size_t)mc) + tail_align(4 * (size_t)me) + tail_align(4 * ((size_t)me + 1)) +
-           tail_align(4 * ((size_t)nlev + 1));
-}
-
-template <typename T>
-__host__ __device__ inline size_t local_bwd_smem(int32_t B, int32_t nlev, int32_t mp, int32_t mq)
-{
-    return tail_align(sizeof(T) * 3 * (size_t)B) + tail_align(sizeof(T) * 6 * (size_t)mp) +
-           tail_align(sizeof(T) * 9 * (size_t)mq) + tail_align(4 * (size_t)mp) + tail_align(4 * ((size_t)mp + 1)) +
-           tail_align(4 * (size_t)mq) + tail_align(4 * ((size_t)nlev + 1));
-}
-
-template <typename T>
-__global__ void __launch_bounds__(512) k_local_fwd_s(LocalS a, const T *__restrict__ Lb, T *w, const int *done,
-                                                     int32_t me, int32_t mc)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
-    if (done && *done) return;
-    const int32_t B = 1 << a.shift, c = blockIdx.x, base = c << a.shift;
-    const int32_t cnt = min(B, a.n - base);
-    unsigned char *cur = smem_raw;
-    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
-    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * B));
-    T *sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * mc));
-    int32_t *sc = reinterpret_cast<int32_t *>(take(4 * mc));
-    int32_t *sq = reinterpret_cast<int32_t *>(take(4 * me));
-    int32_t *sb = reinterpret_cast<int32_t *>(take(4 * (me + 1)));
-    int32_t *st = reinterpret_cast<int32_t *>(take(4 * (a.nlev + 1)));
-    const int32_t *tab = a.tab + (size_t)c * 4 * (a.nlev + 1);
-    const int32_t ne = tab[a.nlev], nc = tab[(a.nlev + 1) + a.nlev];
-    const int32_t e0 = a.base[c], c0 = a.base[(a.nb + 1) + c];
-    for (int32_t i = threadIdx.x; i <= a.nlev; i += blockDim.x) st[i] = tab[i];
-    for (int32_t i = threadIdx.x; i < 9 * nc; i += blockDim.x) sL[i] = Lb[9 * (int64_t)c0 + i];
-    for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) sc[i] = a.cloc[c0 + i];
-    for (int32_t i = threadIdx.x; i < ne; i += blockDim.x) {
-        sq[i] = a.q[e0 + i];
-        sb[i] = a.beg[e0 + i];
-    }
-    if (threadIdx.x == 0) sb[ne] = nc;
-    pdl_wait();
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        sw[3 * i] = w[3 * v];
-        sw[3 * i + 1] = w[3 * v + 1];
-        sw[3 * i + 2] = w[3 * v + 2];
-    }
-    __syncthreads();
-    for (int l = 0; l < a.nlev; ++l) {
-        const int32_t k1 = st[l + 1];
-        for (int32_t k = st[l] + threadIdx.x; k < k1; k += blockDim.x) {
-            T s[3] = {0, 0, 0};
-            for (int32_t j = sb[k]; j < sb[k + 1]; ++j) {
-                T y[3];
-                full_mv(sL + 9 * j, sw + 3 * sc[j], y);
-                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
-            }
-            const int32_t q = sq[k];
-            sw[3 * q] -= s[0];
-            sw[3 * q + 1] -= s[1];
-            sw[3 * q + 2] -= s[2];
-        }
-        __syncthreads();
-    }
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        w[3 * v] = sw[3 * i];
-        w[3 * v + 1] = sw[3 * i + 1];
-        w[3 * v + 2] = sw[3 * i + 2];
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(512) k_local_bwd_s(LocalS a, const T *__restrict__ Lb, const T *__restrict__ Db,
-                                                     T *w, const int *done, int32_t mp, int32_t mq)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
-    if (done && *done) return;
-    const int32_t B = 1 << a.shift, c = blockIdx.x, base = c << a.shift;
-    const int32_t cnt = min(B, a.n - base);
-    unsigned char *cur = smem_raw;
-    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
-    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * B));
-    T *sD = reinterpret_cast<T *>(take(sizeof(T) * 6 * mp));
-    T *sL = reinterpret_cast<T *>(take(sizeof(T) * 9 * mq));
-    int32_t *so = reinterpret_cast<int32_t *>(take(4 * mp));
-    int32_t *sp = reinterpret_cast<int32_t *>(take(4 * (mp + 1)));
-    int32_t *sq = reinterpret_cast<int32_t *>(take(4 * mq));
-    int32_t *st = reinterpret_cast<int32_t *>(take(4 * (a.nlev + 1)));
-    const int32_t *tab = a.tab + (size_t)c * 4 * (a.nlev + 1);
-    const int32_t np = tab[3 * (a.nlev + 1) - 1], nq = tab[4 * (a.nlev + 1) - 1];
-    const int32_t t0 = a.base[2 * (a.nb + 1) + c], q0 = a.base[3 * (a.nb + 1) + c];
-    for (int32_t i = threadIdx.x; i <= a.nlev; i += blockDim.x) st[i] = tab[2 * (a.nlev + 1) + i];
-    for (int32_t i = threadIdx.x; i < 6 * np; i += blockDim.x) sD[i] = Db[6 * (int64_t)t0 + i];
-    for (int32_t i = threadIdx.x; i < 9 * nq; i += blockDim.x) sL[i] = Lb[9 * (int64_t)q0 + i];
-    for (int32_t i = threadIdx.x; i < np; i += blockDim.x) {
-        so[i] = a.oloc[t0 + i];
-        sp[i] = a.pbeg[t0 + i];
-    }
-    if (threadIdx.x == 0) sp[np] = nq;
-    for (int32_t i = threadIdx.x; i < nq; i += blockDim.x) sq[i] = a.qloc[q0 + i];
-    pdl_wait();
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        sw[3 * i] = w[3 * v];
-        sw[3 * i + 1] = w[3 * v + 1];
-        sw[3 * i + 2] = w[3 * v + 2];
-    }
-    __syncthreads();
-    for (int l = a.nlev - 1; l >= 0; --l) {
-        const int32_t i1 = st[l + 1];
-        for (int32_t i = st[l] + threadIdx.x; i < i1; i += blockDim.x) {
-            const int32_t o = so[i];
-            T z[3];
-            sym_mv(sD + 6 * i, sw + 3 * o, z);
-            for (int32_t p = sp[i]; p < sp[i + 1]; ++p) {
-                T u[3];
-                full_mtv(sL + 9 * p, sw + 3 * sq[p], u);
-                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
-            }
-            sw[3 * o] = z[0];
-            sw[3 * o + 1] = z[1];
-            sw[3 * o + 2] = z[2];
-        }
-        __syncthreads();
-    }
-    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t v = a.inv_pre[base + i];
-        w[3 * v] = sw[3 * i];
-        w[3 * v + 1] = sw[3 * i + 1];
-        w[3 * v + 2] = sw[3 * i + 2];
-    }
-}
 
 // The last levels (the vertices at elimination positions >= P0) in one
 // thread block with every array they use staged in shared memory: vectors,
@@ -1503,202 +814,6 @@ __global__ void __launch_bounds__(1024) k_tree_tail(Tail tl, const int32_t *__re
     }
 }
 
-// The tail in one thread-block cluster: tail position i belongs to block
-// i / S of the cluster, which keeps w_i, D_i^-1 and the L blocks of the
-// pairs it eliminates (backward) and of the receiver entries it owns
-// (forward) in its shared memory; values of other blocks are read through
-// distributed shared memory.  Levels are separated by cluster barriers.
-struct CTail {
-    int32_t nlev, n, S, P0, Q0, C0;
-    const int32_t *lvl_pos;  // nlev + 1 absolute positions
-    const int32_t *tb;       // local receiver of each tail pair
-    const int32_t *fo;       // R x (nlev + 1): forward entries of block r by level (block-relative)
-    const int32_t *eoff, *coff;  // R + 1: block offsets into fq/fbeg and fcon/fidx
-    const int32_t *fq, *fbeg;    // per forward entry: receiver slot, first contributor (block-relative)
-    const int32_t *fcon, *fidx;  // per contributor: local position, tail contributor entry
-};
-
-template <typename T>
-__host__ __device__ inline size_t ctail_smem(int32_t S, int32_t nlev, int32_t npair, int32_t ne, int32_t nc)
-{
-    return tail_align(sizeof(T) * 3 * (size_t)S) + tail_align(sizeof(T) * 6 * (size_t)S) +
-           tail_align(sizeof(T) * 9 * (size_t)npair) + tail_align(4 * (size_t)npair) +
-           tail_align(4 * ((size_t)S + 1)) + tail_align(4 * (size_t)ne) + tail_align(4 * ((size_t)ne + 1)) +
-           tail_align(sizeof(T) * 9 * (size_t)nc) + tail_align(4 * (size_t)nc) + tail_align(4 * ((size_t)nlev + 1));
-}
-
-template <typename T>
-__global__ void __launch_bounds__(1024) k_tree_ctail(CTail a, const int32_t *__restrict__ ord,
-                                                     const int32_t *__restrict__ pr_ptr, const T *__restrict__ L,
-                                                     const T *__restrict__ Lf, const T *__restrict__ Dinv, T *w,
-                                                     const int *done)
-{
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
-    if (done && *done) return;   // the same in every block of the cluster
-    const int32_t r = (int32_t)cl.block_rank();
-    const int32_t i0 = r * a.S;
-    const int32_t cnt = max(0, min(a.S, a.n - i0));
-    const int32_t pa = cnt > 0 ? pr_ptr[a.P0 + i0] : 0, pb = cnt > 0 ? pr_ptr[a.P0 + i0 + cnt] : 0;
-    const int32_t np = pb - pa;
-    const int32_t e0 = a.eoff[r], ne = a.eoff[r + 1] - e0, c0 = a.coff[r], nc = a.coff[r + 1] - c0;
-    unsigned char *cur = smem_raw;
-    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
-    T *sw = reinterpret_cast<T *>(take(sizeof(T) * 3 * a.S));
-    T *sD = reinterpret_cast<T *>(take(sizeof(T) * 6 * a.S));
-    T *sLb = reinterpret_cast<T *>(take(sizeof(T) * 9 * np));
-    int32_t *sbq = reinterpret_cast<int32_t *>(take(4 * np));
-    int32_t *spr = reinterpret_cast<int32_t *>(take(4 * (a.S + 1)));
-    int32_t *sq = reinterpret_cast<int32_t *>(take(4 * ne));
-    int32_t *sb = reinterpret_cast<int32_t *>(take(4 * (ne + 1)));
-    T *sLf = reinterpret_cast<T *>(take(sizeof(T) * 9 * nc));
-    int32_t *sc = reinterpret_cast<int32_t *>(take(4 * nc));
-    int32_t *sfo = reinterpret_cast<int32_t *>(take(4 * (a.nlev + 1)));
-    // stage the factor (independent of the previous kernel)
-    for (int32_t k = threadIdx.x; k < 6 * cnt; k += blockDim.x) sD[k] = Dinv[6 * ((int64_t)a.P0 + i0) + k];
-    for (int32_t k = threadIdx.x; k < 9 * np; k += blockDim.x) sLb[k] = L[9 * (int64_t)pa + k];
-    for (int32_t k = threadIdx.x; k < np; k += blockDim.x) sbq[k] = a.tb[pa - a.Q0 + k];
-    for (int32_t k = threadIdx.x; k <= cnt; k += blockDim.x) spr[k] = pr_ptr[a.P0 + i0 + k] - pa;
-    for (int32_t k = threadIdx.x; k < ne; k += blockDim.x) {
-        sq[k] = a.fq[e0 + k];
-        sb[k] = a.fbeg[e0 + k];
-    }
-    if (threadIdx.x == 0) sb[ne] = nc;
-    for (int32_t k = threadIdx.x; k < nc; k += blockDim.x) sc[k] = a.fcon[c0 + k];
-    for (int32_t k = threadIdx.x; k < 9 * nc; k += blockDim.x) {
-        const int32_t j = k / 9, e = k - 9 * j;
-        sLf[k] = Lf[9 * ((int64_t)a.C0 + a.fidx[c0 + j]) + e];
-    }
-    for (int32_t k = threadIdx.x; k <= a.nlev; k += blockDim.x) sfo[k] = a.fo[r * (a.nlev + 1) + k];
-    pdl_wait();
-    for (int32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
-        const int64_t v = ord[a.P0 + i0 + k];
-        sw[3 * k] = w[3 * v];
-        sw[3 * k + 1] = w[3 * v + 1];
-        sw[3 * k + 2] = w[3 * v + 2];
-    }
-    cl.sync();
-    auto value = [&](int32_t i) -> const T * {   // w of tail position i, wherever it lives
-        const int32_t o = i / a.S, slot = i - o * a.S;
-        return o == r ? sw + 3 * slot : cl.map_shared_rank(sw, (unsigned)o) + 3 * slot;
-    };
-    for (int l = 0; l < a.nlev; ++l) {
-        const int32_t k1 = sfo[l + 1];
-        for (int32_t k = sfo[l] + threadIdx.x; k < k1; k += blockDim.x) {
-            T s[3] = {0, 0, 0};
-            for (int32_t j = sb[k]; j < sb[k + 1]; ++j) {
-                const T *x = value(sc[j]);
-                T xv[3] = {x[0], x[1], x[2]};
-                T y[3];
-                full_mv(sLf + 9 * j, xv, y);
-                s[0] += y[0]; s[1] += y[1]; s[2] += y[2];
-            }
-            const int32_t q = sq[k];
-            sw[3 * q] -= s[0];
-            sw[3 * q + 1] -= s[1];
-            sw[3 * q + 2] -= s[2];
-        }
-        cl.sync();
-    }
-    for (int l = a.nlev - 1; l >= 0; --l) {
-        const int32_t g0 = max(a.lvl_pos[l] - a.P0, i0), g1 = min(a.lvl_pos[l + 1] - a.P0, i0 + cnt);
-        for (int32_t i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
-            const int32_t k = i - i0;
-            T z[3];
-            sym_mv(sD + 6 * k, sw + 3 * k, z);
-            for (int32_t p = spr[k]; p < spr[k + 1]; ++p) {
-                const T *y = value(sbq[p]);
-                T yv[3] = {y[0], y[1], y[2]};
-                T u[3];
-                full_mtv(sLb + 9 * p, yv, u);
-                z[0] -= u[0]; z[1] -= u[1]; z[2] -= u[2];
-            }
-            sw[3 * k] = z[0];
-            sw[3 * k + 1] = z[1];
-            sw[3 * k + 2] = z[2];
-        }
-        cl.sync();
-    }
-    for (int32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
-        const int64_t v = ord[a.P0 + i0 + k];
-        w[3 * v] = sw[3 * k];
-        w[3 * v + 1] = sw[3 * k + 1];
-        w[3 * v + 2] = sw[3 * k + 2];
-    }
-}
-
-static CTail ctail_of(const sgp_factor *F)
-{
-    CTail t;
-    t.nlev = F->levels - F->tail_level;
-    t.n = (int32_t)(F->n - F->tail_P0);
-    t.S = F->ctail_S;
-    t.P0 = F->tail_P0;
-    t.Q0 = F->tail_Q0;
-    t.C0 = F->tail_C0;
-    t.lvl_pos = bp<const int32_t>(F->tail_idx);
-    t.tb = bp<const int32_t>(F->tail_b);
-    t.fo = bp<const int32_t>(F->ct_fo);
-    t.eoff = bp<const int32_t>(F->ct_eoff);
-    t.coff = bp<const int32_t>(F->ct_coff);
-    t.fq = bp<const int32_t>(F->ct_fq);
-    t.fbeg = bp<const int32_t>(F->ct_fbeg);
-    t.fcon = bp<const int32_t>(F->ct_fcon);
-    t.fidx = bp<const int32_t>(F->ct_fidx);
-    return t;
-}
-
-template <typename T>
-static cudaLaunchConfig_t ctail_config(sgp_ctx *ctx, int R, size_t smem, cudaLaunchAttribute *attr, bool pdl)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(R);
-    cfg.blockDim = dim3(1024);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = ctx->stream;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = R;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = pdl ? ctx->use_pdl : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 2;
-    return cfg;
-}
-
-// Cluster size for the cluster tail on this device: 16 (non-portable) or 8
-// thread blocks of 1024 threads with the full shared-memory budget, whichever
-// the device can schedule; -1 if neither.
-static sgp_status ctail_probe(sgp_ctx *ctx)
-{
-    if (ctx->ctail_R != 0) return SGP_OK;
-    ctx->ctail_R = -1;
-    const int bytes = TREE_TAIL_SMEM;
-    for (auto k : {(const void *)k_tree_ctail<float>, (const void *)k_tree_ctail<double>}) {
-        SGP_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-        SGP_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    }
-    for (int R : {16, 8}) {
-        cudaLaunchAttribute attr[2];
-        cudaLaunchConfig_t cfg = ctail_config<float>(ctx, R, bytes, attr, false);
-        cfg.numAttrs = 1;
-        int ncl = 0;
-        cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, k_tree_ctail<float>, &cfg);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (ncl >= 1) {
-            ctx->ctail_R = R;
-            break;
-        }
-    }
-    return SGP_OK;
-}
-
 static Tail tail_of(const sgp_factor *F)
 {
     Tail t;
@@ -1720,7 +835,10 @@ static Tail tail_of(const sgp_factor *F)
     return t;
 }
 
-// In-place P^-1 w (T = double uses the FP64 factor, float the FP32 copies).
+// In-place P^-1 w (T = double uses the FP64 factor, float the FP32 copies):
+// the binned solve when the factor has a layout for T, else one launch per
+// contraction level below the tail, the tail kernel, one launch per level
+// back down.
 template <typename T>
 sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int *done)
 {
@@ -1737,55 +855,14 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
     // MIXED factor whose tail does not fit runs every level as its own kernel
     int lt = F->tail_level;
     if (lt < F->levels) {
-        if (F->ctail) {
-            if ((f64 ? F->ctail_smem64 : F->ctail_smem32) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
-        } else {
-            const Tail tl = tail_of(F);
-            if (tail_smem_bytes<T>(tl.n, tl.np, tl.nr) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
-        }
+        const Tail tl = tail_of(F);
+        if (tail_smem_bytes<T>(tl.n, tl.np, tl.nr) > (size_t)TREE_TAIL_SMEM) lt = F->levels;
     }
-    const int L1 = F->local_levels;
-    Local la{L1, F->ncomp, 0, (int32_t)F->n, bp<const int32_t>(F->inv_pre), bp<const int32_t>(F->roff),
-             bp<const int32_t>(F->poff), rc, prp, bp<const int32_t>(F->loc_r), bp<const int32_t>(F->loc_c),
-             bp<const int32_t>(F->loc_o), bp<const int32_t>(F->loc_q)};
-    while ((1 << la.shift) < F->comp_size) ++la.shift;
-    const size_t lsm = sizeof(T) * 3 * (size_t)F->comp_size;
-    LocalS ls{L1, F->ncomp, la.shift, (int32_t)F->n, bp<const int32_t>(F->inv_pre), bp<const int32_t>(F->bm_tab),
-              bp<const int32_t>(F->bm_base), bp<const int32_t>(F->bm_q), bp<const int32_t>(F->bm_beg),
-              bp<const int32_t>(F->bm_cloc), bp<const int32_t>(F->bm_oloc), bp<const int32_t>(F->bm_pbeg),
-              bp<const int32_t>(F->bm_qloc)};
-    const int32_t *mv = F->bm_maxv;
-    const size_t fsm = local_fwd_smem<T>(F->comp_size, L1, mv[0], mv[1]);
-    const size_t bsm = local_bwd_smem<T>(F->comp_size, L1, mv[2], mv[3]);
-    const bool staged = L1 > 0 && fsm <= (size_t)TREE_TAIL_SMEM && bsm <= (size_t)TREE_TAIL_SMEM;
-    const T *bLf = reinterpret_cast<const T *>(f64 ? F->bm_Lf.p : F->bm_Lf32.p);
-    const T *bLb = reinterpret_cast<const T *>(f64 ? F->bm_Lb.p : F->bm_Lb32.p);
-    const T *bD = reinterpret_cast<const T *>(f64 ? F->bm_D.p : F->bm_D32.p);
-    if (L1 > 0) {
-        if (staged) LAUNCH_PDL(ctx, k_local_fwd_s<T>, F->ncomp, 512, fsm, ls, bLf, w, done, mv[0], mv[1]);
-        else LAUNCH_PDL(ctx, k_local_fwd<T>, F->ncomp, 256, lsm, la, Lf, w, done);
-    }
-    // the cooperative kernel covers [lc, lt) when the factor has one and the
-    // tail is in use (an FP64 apply whose tail does not fit runs plain levels)
-    const int lc = (F->coop_level < F->tail_level && lt == F->tail_level) ? F->coop_level : lt;
-    const int32_t *lidx = bp<const int32_t>(F->coop_idx);
-    for (int l = L1; l < lc; ++l) {
+    for (int l = 0; l < lt; ++l) {
         int32_t r0 = F->rl_ptr[l], cnt = F->rl_ptr[l + 1] - r0;
         if (cnt > 0) LAUNCH_PDL(ctx, k_tree_fwd<T>, grid_for(cnt, B), B, 0, rv, rc, ctv, Lf, r0, cnt, w, done);
     }
-    if (lc < lt)
-        SGP_TRY((launch_coop<T, true>(ctx, F, lt - lc, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done)));
-    if (lt < F->levels && F->ctail) {
-        const CTail ctl = ctail_of(F);
-        cudaLaunchAttribute attr[2];
-        const size_t sm = f64 ? F->ctail_smem64 : F->ctail_smem32;
-        cudaLaunchConfig_t cfg = ctail_config<T>(ctx, F->ctail_R, sm, attr, true);
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_tree_ctail<T>, ctl, ord, prp, L, Lf, Dinv, w, done);
-        ctx->launches++;
-        if (e == cudaSuccess) e = cudaGetLastError();
-        if (e != cudaSuccess)
-            return sgp_fail(ctx, SGP_ERR_CUDA, "launch of k_tree_ctail failed: %s", cudaGetErrorString(e));
-    } else if (lt < F->levels) {
+    if (lt < F->levels) {
         const Tail tl = tail_of(F);
         const size_t staged = tail_smem_staged<T>(tl.n, tl.np, tl.nr);
         if (staged <= (size_t)TREE_TAIL_SMEM)
@@ -1794,15 +871,9 @@ sgp_status tree_apply_inplace(sgp_ctx *ctx, const sgp_factor *F, T *w, const int
             LAUNCH_PDL(ctx, (k_tree_tail<T, false>), 1, 1024, tail_smem_bytes<T>(tl.n, tl.np, tl.nr), tl, ord, rc,
                        prp, L, Lf, Dinv, w, done);
     }
-    if (lc < lt)
-        SGP_TRY((launch_coop<T, false>(ctx, F, lt - lc, lidx, rv, rc, ctv, Lf, ord, prp, prq, L, Dinv, w, done)));
-    for (int l = lc - 1; l >= L1; --l) {
+    for (int l = lt - 1; l >= 0; --l) {
         int32_t p0 = F->lvl_ptr[l], cnt = F->lvl_ptr[l + 1] - p0;
         if (cnt > 0) LAUNCH_PDL(ctx, k_tree_bwd<T>, grid_for(cnt, B), B, 0, ord, prp, prq, L, Dinv, p0, cnt, w, done);
-    }
-    if (L1 > 0) {
-        if (staged) LAUNCH_PDL(ctx, k_local_bwd_s<T>, F->ncomp, 512, bsm, ls, bLb, bD, w, done, mv[2], mv[3]);
-        else LAUNCH_PDL(ctx, k_local_bwd<T>, F->ncomp, 256, lsm, la, L, Dinv, w, done);
     }
     return SGP_OK;
 }
@@ -1819,14 +890,6 @@ static sgp_status tail_smem_optin(sgp_ctx *ctx)
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SGP_CUDA(ctx, cudaFuncSetAttribute(k_tree_tail<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_fwd_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SGP_CUDA(ctx, cudaFuncSetAttribute(k_local_bwd_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (ctx->device >= 0 && ctx->device < 64) done_dev[ctx->device] = 1;
     return SGP_OK;
 }
@@ -1863,22 +926,8 @@ __global__ void k_tail_pairs(const int32_t *__restrict__ ct, int32_t first, int3
 }  // namespace
 
 // ------------------------------------------------------------------- factor
-static sgp_status compact(sgp_ctx *ctx, const int32_t *A, int32_t na, int mode, int32_t level,
-                          const int32_t *lev, int32_t *rflag, int32_t *flag, int32_t *off,
-                          int32_t *dst, int32_t base, int32_t *pos, int32_t *count)
-{
-    *count = 0;
-    if (na == 0) return SGP_OK;
-    LAUNCH(ctx, k_flags, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, A, na, mode, level, lev,
-           (const int32_t *)rflag, flag);
-    SGP_TRY(scan_exclusive_i32(ctx, flag, off, na));
-    LAUNCH(ctx, k_scatter_list, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, A, na, (const int32_t *)flag,
-           (const int32_t *)off, dst, base, mode, pos, rflag);
-    SGP_TRY(read_back(ctx, count, off + na, sizeof(int32_t)));
-    return SGP_OK;
-}
-
-// compact() with the count left on the device (*count).
+// Stable compaction of the flagged entries of the alive list A (k_flags'
+// modes) to dst[base + ...], the count left on the device (*count).
 static sgp_status compact_dev(sgp_ctx *ctx, const int32_t *A, int32_t na, int mode, int32_t level,
                               const int32_t *lev, int32_t *rflag, int32_t *flag, int32_t *off, int32_t *dst,
                               int32_t base, int32_t *pos, int32_t *count)
@@ -1911,7 +960,6 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     F->pl_ptr.assign(1, 0);
     F->cl_ptr.assign(1, 0);
     F->tail_level = 0;
-    F->coop_level = 0;
     const size_t n1 = (size_t)n + 1, P = 2 * (size_t)n + 2;
     SGP_TRY(buf_ensure(ctx, F->adj_ptr, sizeof(int32_t) * n1));
     SGP_TRY(buf_ensure(ctx, F->nbr, sizeof(int32_t) * (2 * nt + 1)));
@@ -1976,88 +1024,13 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
            M->gamma0, bp<double>(F->acc), deg, lev, A);
     SGP_CUDA(ctx, cudaMemsetAsync(rflag, 0, sizeof(int32_t) * n1, ctx->stream));
 
-    // local phase: depth-first preorder, blocks of comp_size consecutive
-    // preorder numbers, pinned vertices; the alive list starts in preorder so
-    // that every per-level list comes out grouped by block
-    const int32_t B = ctx->comp_size;
-    const bool local = B > 0;
-    int32_t shift = 0;
-    int32_t *pinned = nullptr;
-    F->comp_size = local ? B : 0;
-    F->local_levels = 0;
-    F->ncomp = 0;
-    if (local) {
-        while ((1 << shift) < B) ++shift;
-        F->ncomp = (int32_t)((n + B - 1) >> shift);
-        SGP_TRY(buf_ensure(ctx, F->pre, sizeof(int32_t) * n1));
-        SGP_TRY(buf_ensure(ctx, F->inv_pre, sizeof(int32_t) * n1));
-        SGP_TRY(buf_ensure(ctx, F->pinned, sizeof(int32_t) * n1));
-        SGP_TRY(buf_ensure(ctx, F->et_tid, sizeof(int32_t) * n1));
-        SGP_TRY(buf_ensure(ctx, F->et_size, sizeof(int32_t) * (n1 + 1)));
-        const size_t m2 = 2 * (size_t)nt + 1;
-        SGP_TRY(buf_ensure(ctx, F->et_succ, sizeof(int32_t) * m2));
-        SGP_TRY(buf_ensure(ctx, F->et_dist, sizeof(int32_t) * m2));
-        SGP_TRY(buf_ensure(ctx, F->et_succ2, sizeof(int32_t) * m2));
-        SGP_TRY(buf_ensure(ctx, F->et_dist2, sizeof(int32_t) * m2));
-        SGP_TRY(buf_ensure(ctx, F->et_flag, sizeof(int32_t) * (m2 + 1)));
-        int32_t *pre = bp<int32_t>(F->pre), *tid = bp<int32_t>(F->et_tid), *tsize = bp<int32_t>(F->et_size);
-        int32_t *succ = bp<int32_t>(F->et_succ), *dist = bp<int32_t>(F->et_dist);
-        int32_t *succ2 = bp<int32_t>(F->et_succ2), *dist2 = bp<int32_t>(F->et_dist2);
-        int32_t *dflag = bp<int32_t>(F->et_flag);
-        // tree labels in internal ids: the root of v's tree is int_of[comp[orig_of[v]]]
-        SGP_TRY(buf_ensure(ctx, F->comp_int, sizeof(int32_t) * n1));
-        LAUNCH(ctx, k_comp_internal, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, bp<const int32_t>(T->comp), int_of,
-               orig_of, bp<int32_t>(F->comp_int));
-        const int32_t *comp = bp<const int32_t>(F->comp_int);
-        pinned = bp<int32_t>(F->pinned);
-        // trees: rank of each root among roots, sizes, exclusive size sums
-        LAUNCH(ctx, k_root_flag, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n, flag);
-        SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, n));
-        int32_t ntree = 0;
-        SGP_TRY(read_back(ctx, &ntree, tmp + n, sizeof(int32_t)));
-        SGP_CUDA(ctx, cudaMemsetAsync(tsize, 0, sizeof(int32_t) * (n1 + 1), ctx->stream));
-        LAUNCH(ctx, k_tree_index, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, (const int32_t *)tmp, n, tid, tsize);
-        int32_t *voff = bp<int32_t>(F->pos);   // scratch until the contraction starts
-        SGP_TRY(scan_exclusive_i32(ctx, tsize, voff, ntree));
-        int *perr = ctx->d_flags + 16;
-        SGP_TRY(tail_smem_optin(ctx));
-        SGP_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
-        SGP_CUDA(ctx, cudaMemsetAsync(pre, 0xff, sizeof(int32_t) * n, ctx->stream));
-        const int64_t ns = 2 * nt;
-        if (nt > 0) {
-            LAUNCH(ctx, k_et_init, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
-                   (const int32_t *)nbr, (const int32_t *)twin, comp, n, succ, dist);
-            for (int64_t span = 1; span < ns; span *= 2) {
-                LAUNCH(ctx, k_et_jump, grid_for(ns, SGP_BLOCK), SGP_BLOCK, 0, ns, (const int32_t *)succ,
-                       (const int32_t *)dist, succ2, dist2);
-                std::swap(succ, succ2);
-                std::swap(dist, dist2);
-            }
-            LAUNCH(ctx, k_et_down, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
-                   (const int32_t *)twin, (const int32_t *)dist, (const int32_t *)tid, (const int32_t *)voff,
-                   (const int32_t *)tsize, n, ns, dflag, perr);
-            SGP_TRY(scan_exclusive_i32(ctx, dflag, dflag, ns));
-        }
-        LAUNCH(ctx, k_preorder, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
-               (const int32_t *)nbr, (const int32_t *)twin, (const int32_t *)dist, (const int32_t *)tid,
-               (const int32_t *)voff, (const int32_t *)tsize, (const int32_t *)dflag, comp, n, ns, pre, perr);
-        LAUNCH(ctx, k_blocks, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)adj_ptr,
-               (const int32_t *)nbr, (const int32_t *)pre, n, shift, bp<int32_t>(F->inv_pre), pinned, perr);
-        int herr8 = 0;
-        SGP_TRY(read_back(ctx, &herr8, perr, sizeof(int)));
-        if (herr8) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: the depth-first order is not a permutation");
-        SGP_CUDA(ctx, cudaMemcpyAsync(A, F->inv_pre.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
-                                      ctx->stream));
-    }
-
     Sim S{adj_ptr, nbr, twin, eref, deg, lev, nrec, bp<int2>(F->rq), bp<int2>(F->re), bp<int2>(F->ren)};
     int32_t na = (int32_t)n, npos = 0, npair = 0, nrecv = 0, ncontrib = 0, level = 0;
     const int max_phases = 4 * 64 + 8 * 32;
-    bool phase1 = local;
     for (int phase = 0; na > 0; ++phase) {
         if (phase > max_phases)
             return sgp_fail(ctx, SGP_ERR_TIMEOUT, "tree_factor: contraction did not finish");
-        if (!phase1 && na <= SMALL_NA) {
+        if (na <= SMALL_NA) {
             // the short tail: all remaining levels in one block, one read-back
             int32_t *hdr = bp<int32_t>(F->small);
             int4 *rec = reinterpret_cast<int4 *>(hdr + 4);
@@ -2087,102 +1060,47 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
             phase += done - 1;
             continue;
         }
+        // a large level: every count stays on the device until one read at its end
         const uint32_t salt = 0x9E3779B9u * (uint32_t)(phase + 1);
-        if (!phase1) {
-            // a large level: every count stays on the device until one read at its end
-            int32_t *dc = bp<int32_t>(F->small) + 4 + 4 * SMALL_MAXL;
-            const unsigned gn = grid_for(na, SGP_BLOCK);
-            LAUNCH(ctx, k_select, gn, SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt, (const int32_t *)nullptr);
-            F->rounds++;
-            SGP_TRY(compact_dev(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, dc + 0));
-            LAUNCH(ctx, k_level_nrec_d, gn, SGP_BLOCK, 0, (const int32_t *)ord, npos, na, (const int32_t *)dc,
-                   (const int32_t *)nrec, flag);
-            SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, na));
-            LAUNCH(ctx, k_level_pairs_d, gn, SGP_BLOCK, 0, (const int32_t *)ord, npos, na, dc, (const int32_t *)tmp,
-                   npair, (const int32_t *)nrec, (const int2 *)S.rq, pr_ptr, pr_q, pr_c, rflag);
-            SGP_TRY(compact_dev(ctx, A, na, 1, level, lev, rflag, flag, tmp, rv, nrecv, pos, dc + 2));
-            LAUNCH(ctx, k_contrib_d<false>, gn, SGP_BLOCK, 0, S, (const int32_t *)rv, nrecv, na, dc, level,
-                   (const int32_t *)pos, (const int32_t *)pr_ptr, flag, (const int32_t *)nullptr, 0,
-                   (int32_t *)nullptr, (int32_t *)nullptr);
-            SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, na));
-            LAUNCH(ctx, k_contrib_d<true>, gn, SGP_BLOCK, 0, S, (const int32_t *)rv, nrecv, na, dc, level,
-                   (const int32_t *)pos, (const int32_t *)pr_ptr, flag, (const int32_t *)tmp, ncontrib, rc_ptr, ct);
-            LAUNCH(ctx, k_apply_d, gn, SGP_BLOCK, 0, S, (const int32_t *)ord, npos, (const int32_t *)dc,
-                   (int32_t)nt);
-            level++;
-            SGP_TRY(compact_dev(ctx, A, na, 2, level, lev, rflag, flag, tmp, Bl, 0, pos, dc + 4));
-            int32_t h[5] = {0, 0, 0, 0, 0};
-            SGP_TRY(read_back(ctx, h, dc, sizeof(h)));
-            const int32_t ne = h[0], lp = h[1], nr = h[2], lc = h[3], nalive = h[4];
-            if (ne == 0) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
-            if (lc != lp)
-                return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent contraction (%d/%d)", lc, lp);
-            npos += ne;
-            npair += lp;
-            nrecv += nr;
-            ncontrib += lc;
-            F->lvl_ptr.push_back(npos);
-            F->rl_ptr.push_back(nrecv);
-            F->pl_ptr.push_back(npair);
-            F->cl_ptr.push_back(ncontrib);
-            std::swap(A, Bl);
-            na = nalive;
-            continue;
-        }
-        LAUNCH(ctx, k_select, grid_for(na, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt,
-               (const int32_t *)(phase1 ? pinned : nullptr));
+        int32_t *dc = bp<int32_t>(F->small) + 4 + 4 * SMALL_MAXL;
+        const unsigned gn = grid_for(na, SGP_BLOCK);
+        LAUNCH(ctx, k_select, gn, SGP_BLOCK, 0, S, (const int32_t *)A, na, level, salt);
         F->rounds++;
-        int32_t ne = 0;
-        SGP_TRY(compact(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, &ne));
-        if (ne == 0 && phase1) {        // local phase exhausted: the rest contracts globally
-            phase1 = false;
-            F->local_levels = level;
-            continue;
-        }
-        if (ne == 0) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
-        // pairs (receivers) of the eliminated vertices
-        LAUNCH(ctx, k_level_nrec, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, npos, ne,
+        SGP_TRY(compact_dev(ctx, A, na, 0, level, lev, rflag, flag, tmp, ord, npos, pos, dc + 0));
+        LAUNCH(ctx, k_level_nrec_d, gn, SGP_BLOCK, 0, (const int32_t *)ord, npos, na, (const int32_t *)dc,
                (const int32_t *)nrec, flag);
-        SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, ne));
-        LAUNCH(ctx, k_level_pairs, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, npos, ne,
-               (const int32_t *)tmp, npair, (const int32_t *)nrec, (const int2 *)S.rq, pr_ptr, pr_q,
-               pr_c, rflag);
-        int32_t lp = 0;
-        SGP_TRY(read_back(ctx, &lp, tmp + ne, sizeof(int32_t)));
-        // receivers, ascending id, and their contributors
-        int32_t nr = 0;
-        SGP_TRY(compact(ctx, A, na, 1, level, lev, rflag, flag, tmp, rv, nrecv, pos, &nr));
-        if (nr > 0) {
-            LAUNCH(ctx, k_contrib<false>, grid_for(nr, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)rv,
-                   nrecv, nr, level, (const int32_t *)pos, (const int32_t *)pr_ptr, flag,
-                   (const int32_t *)nullptr, 0, (int32_t *)nullptr, (int32_t *)nullptr);
-            SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, nr));
-            LAUNCH(ctx, k_contrib<true>, grid_for(nr, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)rv,
-                   nrecv, nr, level, (const int32_t *)pos, (const int32_t *)pr_ptr, flag,
-                   (const int32_t *)tmp, ncontrib, rc_ptr, ct);
-            int32_t lc = 0;
-            SGP_TRY(read_back(ctx, &lc, tmp + nr, sizeof(int32_t)));
-            if (lc != lp)
-                return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent contraction (%d/%d)", lc, lp);
-            ncontrib += lc;
-        }
-        // structural update
-        LAUNCH(ctx, k_apply, grid_for(ne, SGP_BLOCK), SGP_BLOCK, 0, S, (const int32_t *)ord, npos, ne, (int32_t)nt);
+        SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, na));
+        LAUNCH(ctx, k_level_pairs_d, gn, SGP_BLOCK, 0, (const int32_t *)ord, npos, na, dc, (const int32_t *)tmp,
+               npair, (const int32_t *)nrec, (const int2 *)S.rq, pr_ptr, pr_q, pr_c, rflag);
+        SGP_TRY(compact_dev(ctx, A, na, 1, level, lev, rflag, flag, tmp, rv, nrecv, pos, dc + 2));
+        LAUNCH(ctx, k_contrib_d<false>, gn, SGP_BLOCK, 0, S, (const int32_t *)rv, nrecv, na, dc, level,
+               (const int32_t *)pos, (const int32_t *)pr_ptr, flag, (const int32_t *)nullptr, 0,
+               (int32_t *)nullptr, (int32_t *)nullptr);
+        SGP_TRY(scan_exclusive_i32(ctx, flag, tmp, na));
+        LAUNCH(ctx, k_contrib_d<true>, gn, SGP_BLOCK, 0, S, (const int32_t *)rv, nrecv, na, dc, level,
+               (const int32_t *)pos, (const int32_t *)pr_ptr, flag, (const int32_t *)tmp, ncontrib, rc_ptr, ct);
+        LAUNCH(ctx, k_apply_d, gn, SGP_BLOCK, 0, S, (const int32_t *)ord, npos, (const int32_t *)dc,
+               (int32_t)nt);
+        level++;
+        SGP_TRY(compact_dev(ctx, A, na, 2, level, lev, rflag, flag, tmp, Bl, 0, pos, dc + 4));
+        int32_t h[5] = {0, 0, 0, 0, 0};
+        SGP_TRY(read_back(ctx, h, dc, sizeof(h)));
+        const int32_t ne = h[0], lp = h[1], nr = h[2], lc = h[3], nalive = h[4];
+        if (ne == 0) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: a contraction level eliminated nothing");
+        if (lc != lp)
+            return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: inconsistent contraction (%d/%d)", lc, lp);
         npos += ne;
         npair += lp;
         nrecv += nr;
+        ncontrib += lc;
         F->lvl_ptr.push_back(npos);
         F->rl_ptr.push_back(nrecv);
         F->pl_ptr.push_back(npair);
         F->cl_ptr.push_back(ncontrib);
-        level++;
-        int32_t nalive = 0;
-        SGP_TRY(compact(ctx, A, na, 2, level, lev, rflag, flag, tmp, Bl, 0, pos, &nalive));
         std::swap(A, Bl);
         na = nalive;
     }
     if (npos != n) return sgp_fail(ctx, SGP_ERR_CUDA, "tree_factor: %d of %lld eliminated", npos, (long long)n);
-    if (phase1) F->local_levels = level;
     F->levels = level;
     F->npairs = npair;
     // closing entries of the pointer arrays
@@ -2227,87 +1145,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
     }
     // the tail: the first level from which everything left fits in the
     // tail kernel's shared memory
-    // in-block indices and per-block ranges of the local levels
-    const int L1 = F->local_levels;
-    if (L1 > 0) {
-        const int32_t nb = F->ncomp, mask = B - 1;
-        const int32_t nr1 = F->rl_ptr[L1], nc1 = F->cl_ptr[L1], no1 = F->lvl_ptr[L1], nq1 = F->pl_ptr[L1];
-        SGP_TRY(buf_ensure(ctx, F->loc_r, sizeof(int32_t) * std::max(nr1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->loc_c, sizeof(int32_t) * std::max(nc1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->loc_o, sizeof(int32_t) * std::max(no1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->loc_q, sizeof(int32_t) * std::max(nq1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->roff, sizeof(int32_t) * (size_t)L1 * (nb + 1)));
-        SGP_TRY(buf_ensure(ctx, F->poff, sizeof(int32_t) * (size_t)L1 * (nb + 1)));
-        const int32_t *pre = bp<const int32_t>(F->pre);
-        LAUNCH(ctx, k_loc_map, grid_for(nr1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv, pre, nr1, mask,
-               bp<int32_t>(F->loc_r));
-        LAUNCH(ctx, k_loc_map, grid_for(nc1, SGP_BLOCK), SGP_BLOCK, 0, bp<const int32_t>(F->ctv), pre, nc1, mask,
-               bp<int32_t>(F->loc_c));
-        LAUNCH(ctx, k_loc_map, grid_for(no1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, pre, no1, mask,
-               bp<int32_t>(F->loc_o));
-        LAUNCH(ctx, k_loc_map, grid_for(nq1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)pr_q, pre, nq1, mask,
-               bp<int32_t>(F->loc_q));
-        for (int l = 0; l < L1; ++l) {
-            LAUNCH(ctx, k_block_ranges, grid_for(nb + 1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)rv, pre,
-                   F->rl_ptr[l], F->rl_ptr[l + 1], nb, shift, bp<int32_t>(F->roff) + (size_t)l * (nb + 1));
-            LAUNCH(ctx, k_block_ranges, grid_for(nb + 1, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)ord, pre,
-                   F->lvl_ptr[l], F->lvl_ptr[l + 1], nb, shift, bp<int32_t>(F->poff) + (size_t)l * (nb + 1));
-        }
-        // block-major copies
-        SGP_TRY(buf_ensure(ctx, F->bm_tab, sizeof(int32_t) * (size_t)nb * 4 * (L1 + 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_tot, sizeof(int32_t) * 4 * (size_t)nb));
-        SGP_TRY(buf_ensure(ctx, F->bm_base, sizeof(int32_t) * 4 * ((size_t)nb + 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_max, sizeof(int32_t) * 4));
-        SGP_CUDA(ctx, cudaMemsetAsync(F->bm_max.p, 0, sizeof(int32_t) * 4, ctx->stream));
-        int32_t *tab = bp<int32_t>(F->bm_tab), *tot = bp<int32_t>(F->bm_tot), *base = bp<int32_t>(F->bm_base);
-        LAUNCH(ctx, k_bm_tables, grid_for(nb, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)L1, nb, bp<const int32_t>(F->roff),
-               bp<const int32_t>(F->poff), (const int32_t *)rc_ptr, (const int32_t *)pr_ptr, tab, tot,
-               bp<int32_t>(F->bm_max));
-        for (int k = 0; k < 4; ++k)
-            SGP_TRY(scan_exclusive_i32(ctx, tot + (size_t)k * nb, base + (size_t)k * (nb + 1), nb));
-        SGP_TRY(read_back(ctx, F->bm_maxv, F->bm_max.p, sizeof(int32_t) * 4));
-        const bool m32 = F->precision == SGP_PREC_MIXED;
-        SGP_TRY(buf_ensure(ctx, F->bm_q, sizeof(int32_t) * std::max(nr1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_beg, sizeof(int32_t) * std::max(nr1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_cloc, sizeof(int32_t) * std::max(nc1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_Lf, sizeof(double) * 9 * std::max(nc1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_oloc, sizeof(int32_t) * std::max(no1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_pbeg, sizeof(int32_t) * std::max(no1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_D, sizeof(double) * 6 * std::max(no1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_qloc, sizeof(int32_t) * std::max(nq1, 1)));
-        SGP_TRY(buf_ensure(ctx, F->bm_Lb, sizeof(double) * 9 * std::max(nq1, 1)));
-        if (m32) {
-            SGP_TRY(buf_ensure(ctx, F->bm_Lf32, sizeof(float) * 9 * std::max(nc1, 1)));
-            SGP_TRY(buf_ensure(ctx, F->bm_D32, sizeof(float) * 6 * std::max(no1, 1)));
-            SGP_TRY(buf_ensure(ctx, F->bm_Lb32, sizeof(float) * 9 * std::max(nq1, 1)));
-        }
-        const int32_t *cpre = pre, *croff = bp<const int32_t>(F->roff), *cpoff = bp<const int32_t>(F->poff);
-        for (int l = 0; l < L1; ++l) {
-            const int32_t r0 = F->rl_ptr[l], rn = F->rl_ptr[l + 1] - r0;
-            const int32_t j0 = F->cl_ptr[l], jn = F->cl_ptr[l + 1] - j0;
-            const int32_t t0 = F->lvl_ptr[l], tn = F->lvl_ptr[l + 1] - t0;
-            const int32_t q0 = F->pl_ptr[l], qn = F->pl_ptr[l + 1] - q0;
-            LAUNCH(ctx, k_bm_recv, grid_for(rn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, r0, rn,
-                   (const int32_t *)rv, cpre, croff, (const int32_t *)rc_ptr, (const int32_t *)tab,
-                   (const int32_t *)base, bp<const int32_t>(F->loc_r), bp<int32_t>(F->bm_q), bp<int32_t>(F->bm_beg));
-            LAUNCH(ctx, k_bm_contrib, grid_for(jn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, j0,
-                   jn, bp<const int32_t>(F->ctv), cpre, croff, (const int32_t *)rc_ptr, (const int32_t *)tab,
-                   (const int32_t *)base, bp<const int32_t>(F->loc_c), bp<const double>(F->Lf),
-                   m32 ? bp<const float>(F->Lf32) : (const float *)nullptr, bp<int32_t>(F->bm_cloc),
-                   bp<double>(F->bm_Lf), m32 ? bp<float>(F->bm_Lf32) : (float *)nullptr);
-            LAUNCH(ctx, k_bm_pos, grid_for(tn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, t0, tn,
-                   (const int32_t *)ord, cpre, cpoff, (const int32_t *)pr_ptr, (const int32_t *)tab,
-                   (const int32_t *)base, bp<const int32_t>(F->loc_o), bp<const double>(F->Dinv),
-                   m32 ? bp<const float>(F->Dinv32) : (const float *)nullptr, bp<int32_t>(F->bm_oloc),
-                   bp<int32_t>(F->bm_pbeg), bp<double>(F->bm_D), m32 ? bp<float>(F->bm_D32) : (float *)nullptr);
-            LAUNCH(ctx, k_bm_pair, grid_for(qn, SGP_BLOCK), SGP_BLOCK, 0, (int32_t)l, (int32_t)L1, nb, shift, q0, qn,
-                   (const int32_t *)pr_c, cpre, cpoff, (const int32_t *)pr_ptr, (const int32_t *)tab,
-                   (const int32_t *)base, bp<const int32_t>(F->loc_q), bp<const double>(F->L),
-                   m32 ? bp<const float>(F->L32) : (const float *)nullptr, bp<int32_t>(F->bm_qloc),
-                   bp<double>(F->bm_Lb), m32 ? bp<float>(F->bm_Lb32) : (float *)nullptr);
-        }
-    }
-    int lt = L1;
+    int lt = 0;
     auto tail_bytes = [&](int l) {
         const int32_t tn = (int32_t)(n - F->lvl_ptr[l]), tp = npair - F->pl_ptr[l], tr = nrecv - F->rl_ptr[l];
         return F->precision == SGP_PREC_MIXED ? tail_smem_bytes<float>(tn, tp, tr)
@@ -2350,113 +1188,7 @@ sgp_status sgp_tree_factor(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T,
         SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
         return SGP_OK;
     };
-    // the cluster tail: blocks own consecutive tail positions; each block's
-    // forward entries are grouped by level on the host from the tail lists
-    auto build_ctail = [&](int t, bool *fits) -> sgp_status {
-        *fits = false;
-        SGP_TRY(build_tail(t));
-        const int R = ctx->ctail_R, nl = F->levels - t;
-        const int32_t tn = (int32_t)(n - F->tail_P0), nq = nrecv - F->tail_R0, nb = npair - F->tail_Q0;
-        const int32_t S = (tn + R - 1) / R;
-        std::vector<int32_t> tq(std::max(nq, 1)), tcl(2 * std::max(nb, 1)), rcr(nq + 1), prr(tn + 1);
-        SGP_TRY(read_back(ctx, tq.data(), F->tail_q.p, sizeof(int32_t) * nq));
-        SGP_TRY(read_back(ctx, tcl.data(), F->tail_c.p, sizeof(int32_t) * 2 * nb));
-        SGP_TRY(read_back(ctx, rcr.data(), rc_ptr + F->tail_R0, sizeof(int32_t) * (nq + 1)));
-        SGP_TRY(read_back(ctx, prr.data(), pr_ptr + F->tail_P0, sizeof(int32_t) * (tn + 1)));
-        const int32_t *tpc = tcl.data(), *tct = tcl.data() + nb;
-        std::vector<int32_t> fo((size_t)R * (nl + 1)), eoff(R + 1, 0), coff(R + 1, 0), fq, fbeg, fcon, fidx;
-        size_t m32 = 0, m64 = 0;
-        for (int r = 0; r < R; ++r) {
-            eoff[r] = (int32_t)fq.size();
-            coff[r] = (int32_t)fcon.size();
-            for (int l = 0; l < nl; ++l) {
-                fo[(size_t)r * (nl + 1) + l] = (int32_t)fq.size() - eoff[r];
-                for (int32_t k = F->rl_ptr[t + l] - F->tail_R0; k < F->rl_ptr[t + l + 1] - F->tail_R0; ++k) {
-                    if (tq[k] / S != r) continue;
-                    fq.push_back(tq[k] - r * S);
-                    fbeg.push_back((int32_t)fcon.size() - coff[r]);
-                    for (int32_t j = rcr[k] - F->tail_C0; j < rcr[k + 1] - F->tail_C0; ++j) {
-                        fcon.push_back(tpc[tct[j]]);
-                        fidx.push_back(j);
-                    }
-                }
-            }
-            fo[(size_t)r * (nl + 1) + nl] = (int32_t)fq.size() - eoff[r];
-            const int32_t i0 = std::min(r * S, tn), i1 = std::min(i0 + S, tn);
-            const int32_t npr = prr[i1] - prr[i0];
-            const int32_t ner = (int32_t)fq.size() - eoff[r], ncr = (int32_t)fcon.size() - coff[r];
-            m32 = std::max(m32, ctail_smem<float>(S, nl, npr, ner, ncr));
-            m64 = std::max(m64, ctail_smem<double>(S, nl, npr, ner, ncr));
-        }
-        eoff[R] = (int32_t)fq.size();
-        coff[R] = (int32_t)fcon.size();
-        const size_t need = F->precision == SGP_PREC_MIXED ? m32 : m64;
-        if (need > (size_t)TREE_TAIL_SMEM) return SGP_OK;
-        auto up = [&](DBuf &b, const std::vector<int32_t> &v) -> sgp_status {
-            SGP_TRY(buf_ensure(ctx, b, sizeof(int32_t) * std::max<size_t>(v.size(), 1)));
-            if (!v.empty())
-                SGP_CUDA(ctx, cudaMemcpyAsync(b.p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice,
-                                              ctx->stream));
-            return SGP_OK;
-        };
-        SGP_TRY(up(F->ct_fo, fo));
-        SGP_TRY(up(F->ct_eoff, eoff));
-        SGP_TRY(up(F->ct_coff, coff));
-        SGP_TRY(up(F->ct_fq, fq));
-        SGP_TRY(up(F->ct_fbeg, fbeg));
-        SGP_TRY(up(F->ct_fcon, fcon));
-        SGP_TRY(up(F->ct_fidx, fidx));
-        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the vectors live on the host stack
-        F->ctail_R = R;
-        F->ctail_S = S;
-        F->ctail_smem32 = m32;
-        F->ctail_smem64 = m64;
-        *fits = true;
-        return SGP_OK;
-    };
-    F->ctail = 0;
-    if (ctx->ctail_cap > 0) {
-        SGP_TRY(ctail_probe(ctx));
-        if (ctx->ctail_R > 0) {
-            int t = L1;
-            while (t < F->levels && n - F->lvl_ptr[t] > ctx->ctail_cap) ++t;
-            for (; t < lt; ++t) {   // a cluster tail only pays when it starts before the one-block tail
-                bool fits = false;
-                SGP_TRY(build_ctail(t, &fits));
-                if (fits) {
-                    F->ctail = 1;
-                    lt = t;
-                    F->tail_level = lt;
-                    break;
-                }
-            }
-        }
-    }
-    if (!F->ctail && lt < F->levels) SGP_TRY(build_tail(lt));
-    // the cooperative middle: from the first level with at most coop_cap
-    // vertices left up to the tail
-    {
-        int lc = lt;
-        if (ctx->coop_cap > 0)
-            for (int l = L1; l < lt; ++l)
-                if (n - F->lvl_ptr[l] <= ctx->coop_cap) {
-                    lc = l;
-                    break;
-                }
-        F->coop_level = lc;
-        if (lc < lt) {
-            const int nl = lt - lc;
-            std::vector<int32_t> idx(2 * (nl + 1));
-            for (int l = 0; l <= nl; ++l) {
-                idx[l] = F->lvl_ptr[lc + l];
-                idx[nl + 1 + l] = F->rl_ptr[lc + l];
-            }
-            SGP_TRY(buf_ensure(ctx, F->coop_idx, sizeof(int32_t) * idx.size()));
-            SGP_CUDA(ctx, cudaMemcpyAsync(F->coop_idx.p, idx.data(), sizeof(int32_t) * idx.size(),
-                                          cudaMemcpyHostToDevice, ctx->stream));
-            SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // idx lives on the host stack
-        }
-    }
+    if (lt < F->levels) SGP_TRY(build_tail(lt));
     int herr = 0;
     SGP_TRY(read_back(ctx, &herr, err, sizeof(int)));
     if (herr) return sgp_fail(ctx, SGP_ERR_NOT_SPD, "tree_factor: a pivot block is not positive definite");
@@ -2490,12 +1222,13 @@ sgp_status sgp_factor_info(const sgp_factor *F, int32_t *rounds, int32_t *levels
     return SGP_OK;
 }
 
-sgp_status sgp_factor_layout(const sgp_factor *F, int32_t *bins, int32_t *top, int32_t *bin_cap, int32_t *fp32,
-                             int32_t *fp64)
+sgp_status sgp_factor_layout(const sgp_factor *F, int32_t *bins, int32_t *top, int32_t *leaks, int32_t *bin_cap,
+                             int32_t *fp32, int32_t *fp64)
 {
     if (!F) return SGP_ERR_INVALID_ARG;
     if (bins) *bins = F->bl.nb;
     if (top) *top = F->bl.nt;
+    if (leaks) *leaks = F->bl.nly;
     if (bin_cap) *bin_cap = F->bl.bmax;
     if (fp32) *fp32 = F->bl.ok32;
     if (fp64) *fp64 = F->bl.ok64;
@@ -2511,13 +1244,7 @@ void sgp_factor_destroy(sgp_factor *F)
                     &F->eref, &F->deg, &F->lev, &F->nrec, &F->rq, &F->re, &F->ren, &F->pos,
                     &F->flag, &F->alive_a, &F->alive_b, &F->acc, &F->fill, &F->sbuf, &F->tmp,
                     &F->rflag, &F->cnt, &F->ctv, &F->Lf, &F->Lf32, &F->tail_idx, &F->tail_q,
-                    &F->tail_c, &F->tail_b, &F->pre, &F->inv_pre, &F->loc_r, &F->loc_c, &F->loc_o,
-                    &F->loc_q, &F->roff, &F->poff, &F->et_succ, &F->et_dist, &F->et_succ2,
-                    &F->et_dist2, &F->et_tid, &F->et_size, &F->et_flag, &F->pinned, &F->bm_tab,
-                    &F->bm_tot, &F->bm_base, &F->bm_max, &F->bm_q, &F->bm_beg, &F->bm_cloc, &F->bm_oloc,
-                    &F->bm_pbeg, &F->bm_qloc, &F->bm_Lf, &F->bm_Lf32, &F->bm_Lb, &F->bm_Lb32, &F->bm_D,
-                    &F->bm_D32, &F->coop_idx, &F->ct_fo, &F->ct_eoff, &F->ct_coff, &F->ct_fq,
-                    &F->ct_fbeg, &F->ct_fcon, &F->ct_fidx, &F->comp_int, &F->orig_of, &F->small};
+                    &F->tail_c, &F->tail_b, &F->orig_of, &F->small};
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     BinLayout &B = F->bl;

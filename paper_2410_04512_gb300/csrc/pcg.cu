@@ -485,6 +485,83 @@ __global__ void k_accumulate(int64_t n3, const float *__restrict__ d, double sca
     if (k < n3) v[k] += scale * (double)d[k];
 }
 
+// Flexible CG (sgp_fcg_solve).  beta = -z^T q_prev / p_prev^T q_prev, the
+// previous step's p^T q being sc->pq.
+__global__ void __launch_bounds__(RB) k_fcg_zq(int64_t n3, const double *__restrict__ z,
+                                               const double *__restrict__ q, double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    double a = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+        a = fma(z[k], q[k], a);
+    const double s = block_sum<RB>(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->cnt)) {
+        const double zq = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) sc->beta = -zq / sc->pq;
+    }
+}
+
+// p = z (FIRST) or z + beta p, and rho = p^T r for alpha = p^T r / p^T q
+template <bool FIRST>
+__global__ void __launch_bounds__(RB) k_fcg_dir(int64_t n3, const double *__restrict__ z,
+                                                const double *__restrict__ r, double *p, double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    const double beta = FIRST ? 0.0 : sc->beta;
+    double a = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double pk = FIRST ? z[k] : fma(beta, p[k], z[k]);
+        p[k] = pk;
+        a = fma(pk, r[k], a);
+    }
+    const double s = block_sum<RB>(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->cnt)) {
+        const double pr = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) sc->rho = pr;
+    }
+}
+
+// v += alpha p, r -= alpha q, |r|^2 and the stopping test
+__global__ void __launch_bounds__(RB) k_fcg_upd(int64_t n3, const double *__restrict__ p,
+                                                const double *__restrict__ q, double *x, double *r,
+                                                double *partials, Scal *sc)
+{
+    __shared__ double sh[RB / 32];
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double a = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        x[k] = fma(alpha, p[k], x[k]);
+        const double rk = fma(-alpha, q[k], r[k]);
+        r[k] = rk;
+        a = fma(rk, rk, a);
+    }
+    const double s = block_sum<RB>(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (last_block(&sc->cnt)) {
+        const double rr = sum_partials<RB>(partials, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            sc->rr = rr;
+            sc->it += 1;
+            if (!isfinite(rr)) {
+                sc->status = SGP_ERR_NOT_SPD;
+                sc->done = 1;
+            } else if (rr <= sc->stop2) {
+                sc->done = 1;
+            } else if (sc->it >= sc->maxit) {
+                sc->status = SGP_ERR_NO_CONVERGENCE;
+                sc->done = 1;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -933,6 +1010,128 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         rc = sgp_fail(ctx, SGP_ERR_NO_CONVERGENCE, "pcg: no convergence after %lld iterations",
                       (long long)inf.iterations);
     return rc;
+}
+
+
+sgp_status sgp_fcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_aug *A, const sgp_factor *Fac,
+                         const double *F, double *v, const sgp_solve_opts *opts, int64_t inner_maxit,
+                         sgp_solve_info *info)
+{
+    if (!ctx || !M || !A || !Fac || !opts) return SGP_ERR_INVALID_ARG;
+    const int64_t n = M->n;
+    if (n > 0 && (!F || !v)) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: NULL vector");
+    if (!(opts->tol > 0.0) || opts->maxit <= 0 || inner_maxit <= 0)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: tol must be > 0, maxit and inner_maxit >= 1");
+    if (!(opts->inner_tol >= 0.0 && opts->inner_tol < 1.0))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: inner_tol must be in [0, 1)");
+    if (opts->precond != SGP_PRECOND_TREE || opts->precision != SGP_PREC_F64)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: the nested solve is FP64 with the tree preconditioner");
+    if (A->n != n || A->mgen != M->gen || !A->P)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: the augmented forest was built from another matrix");
+    if (Fac->n != n) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: the factor has another size");
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    sgp_solve_info inf{};
+    if (n == 0) {
+        if (info) *info = inf;
+        return SGP_OK;
+    }
+    const double itol = opts->inner_tol > 0.0 ? opts->inner_tol : 0.1;
+    const size_t v64 = sizeof(double) * 3 * n;
+    SGP_TRY(scratch_ensure(ctx, 10 * (v64 + 256) + sizeof(double) * 2 * MAXP + 4 * sizeof(Scal) + 8192));
+    char *base = reinterpret_cast<char *>(ctx->d_scratch) + 256;
+    auto take = [&](size_t b) {
+        char *p = base;
+        base += (b + 255) & ~size_t(255);
+        return p;
+    };
+    double *partials = reinterpret_cast<double *>(take(sizeof(double) * 2 * MAXP));
+    Scal *sco = reinterpret_cast<Scal *>(take(sizeof(Scal)));
+    Scal *sci = reinterpret_cast<Scal *>(take(sizeof(Scal)));
+    double *o2 = reinterpret_cast<double *>(take(64));
+    double *r = reinterpret_cast<double *>(take(v64)), *p = reinterpret_cast<double *>(take(v64)),
+           *q = reinterpret_cast<double *>(take(v64)), *z = reinterpret_cast<double *>(take(v64)),
+           *Fi = reinterpret_cast<double *>(take(v64)), *x = reinterpret_cast<double *>(take(v64)),
+           *ri = reinterpret_cast<double *>(take(v64)), *pi = reinterpret_cast<double *>(take(v64)),
+           *qi = reinterpret_cast<double *>(take(v64)), *wi = reinterpret_cast<double *>(take(v64));
+    const int32_t *orig_of = bp<const int32_t>(M->orig_of);
+    LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, F, Fi);
+    if (opts->x0_given)
+        LAUNCH(ctx, k_to_internal<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)v, x);
+    else
+        SGP_CUDA(ctx, cudaMemsetAsync(x, 0, v64, ctx->stream));
+    Blk<double> B64 = make_blk<double>(M);
+    const int32_t *row_ptr = bp<const int32_t>(M->row_ptr);
+    unsigned Gr = 1;
+    SGP_TRY(resident_grid(ctx, (const void *)k_resid64<false>, RB, (n + RB - 1) / RB, &Gr));
+    double hres[2] = {0, 0};
+    SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
+    if (opts->x0_given)
+        LAUNCH(ctx, k_resid64<false>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, (const double *)Fi, (const double *)x, r,
+               partials, o2);
+    else
+        LAUNCH(ctx, k_resid64<true>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, (const double *)Fi, (const double *)x, r,
+               partials, o2);
+    SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
+    const double ff = hres[1];
+    Scal h{};
+    h.FF = ff;
+    h.rr = hres[0];
+    h.stop2 = opts->tol * opts->tol * ff;
+    h.maxit = opts->maxit;
+    h.done = ff == 0.0 || h.rr <= h.stop2;
+    if (ff == 0.0) SGP_CUDA(ctx, cudaMemsetAsync(x, 0, v64, ctx->stream));
+    SGP_CUDA(ctx, cudaMemcpyAsync(sco, &h, sizeof(Scal), cudaMemcpyHostToDevice, ctx->stream));
+    const sgp_matrix *P = A->P;
+    const unsigned G = red_grid(n);
+    const int64_t n3 = 3 * n;
+    int64_t inner = 0;
+    for (int64_t k = 0; !h.done; ++k) {
+        // z ~ P'^-1 r: PCG on P' with the forest factor, from z = 0
+        Scal hi{};
+        SGP_TRY((pcg_core<double, double>(ctx, P, Fac, SGP_PRECOND_TREE, make_blk<double>(P),
+                                          bp<const int32_t>(P->row_ptr), n, false, (const double *)r, z, 0, itol,
+                                          inner_maxit, ri, pi, qi, wi, partials, sci, &hi)));
+        inner += hi.it;
+        if (hi.status == SGP_ERR_NOT_SPD || hi.status == SGP_ERR_TIMEOUT) {
+            h.status = hi.status;
+            break;
+        }
+        cudaEvent_t ev;
+        SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+        if (k == 0) {
+            LAUNCH(ctx, k_fcg_dir<true>, G, RB, 0, n3, (const double *)z, (const double *)r, p, partials, sco);
+        } else {
+            LAUNCH(ctx, k_fcg_zq, G, RB, 0, n3, (const double *)z, (const double *)q, partials, sco);
+            LAUNCH(ctx, k_fcg_dir<false>, G, RB, 0, n3, (const double *)z, (const double *)r, p, partials, sco);
+        }
+        SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
+        SGP_TRY(kt_begin(ctx, SGP_KT_SPMV, &ev));
+        SGP_TRY(launch_spmv_pq<double>(ctx, B64, row_ptr, M->gamma0, n, (const double *)p, q, partials, sco));
+        SGP_TRY(kt_end(ctx, SGP_KT_SPMV, ev));
+        SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
+        LAUNCH(ctx, k_fcg_upd, G, RB, 0, n3, (const double *)p, (const double *)q, x, r, partials, sco);
+        SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
+        SGP_TRY(read_back(ctx, &h, sco, sizeof(Scal)));
+        SGP_TRY(kt_collect(ctx));
+    }
+    inf.iterations = inner;
+    inf.outer_iterations = (int32_t)h.it;
+    inf.status = h.status;
+    inf.rel_residual = ff > 0 ? std::sqrt(h.rr / ff) : 0.0;
+    SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
+    LAUNCH(ctx, k_resid64<false>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, (const double *)Fi, (const double *)x,
+           (double *)nullptr, partials, o2);
+    SGP_TRY(read_back(ctx, hres, o2, sizeof(hres)));
+    inf.true_rel_residual = hres[1] > 0 ? std::sqrt(hres[0] / hres[1]) : 0.0;
+    LAUNCH(ctx, k_to_caller<double>, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, orig_of, (const double *)x, v);
+    if (info) *info = inf;
+    if (inf.status == SGP_ERR_TIMEOUT) return sgp_fail(ctx, SGP_ERR_TIMEOUT, "fcg: a bounded device wait gave up");
+    if (inf.status == SGP_ERR_NOT_SPD)
+        return sgp_fail(ctx, SGP_ERR_NOT_SPD, "fcg: breakdown (p^T Gamma p not positive)");
+    if (inf.status == SGP_ERR_NO_CONVERGENCE)
+        return sgp_fail(ctx, SGP_ERR_NO_CONVERGENCE, "fcg: no convergence after %d outer iterations",
+                        inf.outer_iterations);
+    return SGP_OK;
 }
 
 }  // extern "C"

@@ -63,11 +63,8 @@ struct sgp_ctx {
     int spmv_lpr = 0;
     int spmv_ilp = 0;       // row groups in flight per lane in the product (0: 1)
     int tail_cap = 1024;    // largest tail of the tree solve in vertices (-1: what fits)
-    int comp_size = 0;      // block of the local phase of the tree factor (0: none)
-    int coop_cap = 0;       // vertices left when one cooperative kernel takes over the levels (0: none)
-    int ctail_cap = 0;      // vertices left when the thread-block-cluster tail takes over (0: none)
-    int ctail_R = 0;        // cluster size of that tail on this device (0: not probed, -1: none)
-    int bin_cap = 1024;     // largest contraction subtree solved by one thread block (0: level kernels only)
+    int bin_cap = 0;        // largest contraction subtree solved by one thread block: 0 = 1024 for the
+                            // FP32 solve only, -1 = level kernels only, else that cap in both precisions
     int fused = 1;          // PCG step fused around the binned tree solve
     int use_pdl = 1;        // programmatic dependent launch of the level kernels
     int batch_chunk = 0;    // rows per work item of the batched solver
@@ -320,39 +317,30 @@ struct sgp_factor {
     DBuf Lf, Lf32;  // L blocks in ct order (forward pass streams them)
     // tail: levels >= tail_level run in one thread block (positions >= tail_P0)
     int32_t tail_level = 0, tail_P0 = 0, tail_R0 = 0, tail_C0 = 0, tail_Q0 = 0;
-    // cluster tail: levels >= tail_level in one cluster of ctail_R thread
-    // blocks; position i of the tail belongs to block i / ctail_S
-    int32_t ctail = 0, ctail_R = 0, ctail_S = 0, ctail_ne = 0, ctail_nc = 0;
-    size_t ctail_smem32 = 0, ctail_smem64 = 0;
-    DBuf ct_fo, ct_eoff, ct_coff, ct_fq, ct_fbeg, ct_fcon, ct_fidx;
-    // levels [coop_level, tail_level) run in one cooperative kernel per direction
-    int32_t coop_level = 0;
-    DBuf coop_idx;  // (nlev + 1) positions, then (nlev + 1) receiver offsets
     DBuf tail_idx;  // level positions and receiver offsets of the tail levels
     DBuf tail_q, tail_c, tail_b;  // local indices (position - tail_P0)
     DBuf work;      // n x 3 float64 apply workspace
     DBuf orig_of;   // n int32: the matrix's internal cell order (vectors are solved in it)
     DBuf small;     // counts of the short-tail contraction kernel (header + per-level records)
-    // local phase: the forest is cut into blocks of comp_size consecutive
-    // vertices of a depth-first preorder; levels < local_levels eliminate
-    // only vertices whose tree neighbours are all in their own block, and the
-    // solve runs those levels block by block in shared memory
-    int32_t local_levels = 0, comp_size = 0, ncomp = 0;
-    DBuf pre, inv_pre;          // n int32: preorder number of each vertex and its inverse
-    DBuf loc_r, loc_c, loc_o, loc_q;  // local (in-block) index of rv, ctv, ord, pr_q entries
-    DBuf roff, poff;            // local_levels x (ncomp + 1) receiver / position ranges per block
-    // block-major copies of the local levels' data (each block's forward
-    // entries, contributors, positions and pairs, level after level), so that
-    // a thread block stages its whole share with contiguous loads
-    DBuf bm_tab, bm_tot, bm_base, bm_max;   // per-block per-level prefix counts, totals, bases, maxima
-    DBuf bm_q, bm_beg, bm_cloc, bm_oloc, bm_pbeg, bm_qloc;
-    DBuf bm_Lf, bm_Lf32, bm_Lb, bm_Lb32, bm_D, bm_D32;
-    int32_t bm_maxv[4] = {0, 0, 0, 0};      // largest per-block count of each kind
-    DBuf et_succ, et_dist, et_succ2, et_dist2, et_tid, et_size, et_flag, pinned, comp_int;  // Euler tour scratch
     BinLayout bl;
     // structure-simulation scratch
     DBuf adj_ptr, nbr, twin, eref, deg, lev, nrec, rq, re, ren, pos, flag, alive_a, alive_b,
         acc, fill, sbuf, tmp, rflag, cnt;
+};
+
+// Vaidya's augmented spanning forest (augment.cu): the pieces of the
+// forest, the edges of T' and P' = gamma0 I + block Laplacian of T' as a
+// matrix in the same internal order as the matrix it was built from.
+#define SGP_AUG_SCRATCH 40
+struct sgp_aug {
+    int64_t n = 0, m = 0;           // cells, edges of the source matrix
+    int32_t t = 0, s = 0, npieces = 0;
+    int64_t nedges = 0, added = 0;  // edges of T', of which not tree edges
+    uint64_t mgen = 0;              // generation of the source matrix
+    DBuf piece;                     // n int32: piece of each cell (caller order)
+    DBuf edges;                     // nedges int32: edge ids of T', ascending
+    sgp_matrix *P = nullptr;        // P' (FP64)
+    DBuf scr[SGP_AUG_SCRATCH];
 };
 
 // ---------------------------------------------------------------------------

@@ -1,9 +1,9 @@
 // tune.cu -- the autotuner: picks the lanes per block row of the PCG
-// product, the contraction granularity of the tree factor (the block size of
-// its local phase and how many of the last levels run in one thread block
-// instead of one launch per level) and the rows per work item of the batched
-// solver, by timing a fixed number of PCG iterations on the caller's own
-// system for each candidate.
+// product, the launch shape of the tree solve (how many of the last
+// contraction levels run in one thread block, and the size of the subtrees
+// that one thread block solves in the binned layout) and the rows per work
+// item of the batched solver, by timing the caller's own system for each
+// candidate.
 // The paper has no counterpart (its solver runs on one CPU core).
 #include "sgp_internal.cuh"
 
@@ -63,11 +63,8 @@ sgp_status sgp_get_tuning(const sgp_ctx *ctx, sgp_tuning *t)
     t->spmv_lpr = ctx->spmv_lpr;
     t->tail_cap = ctx->tail_cap;
     t->batch_chunk = ctx->batch_chunk;
-    t->comp_size = ctx->comp_size;
-    t->coop_cap = ctx->coop_cap;
     t->spmv_ilp = ctx->spmv_ilp;
-    t->ctail_cap = ctx->ctail_cap;
-    t->bin_cap = ctx->bin_cap > 0 ? ctx->bin_cap : -1;
+    t->bin_cap = ctx->bin_cap;
     t->ms_per_iteration = 0.0;
     return SGP_OK;
 }
@@ -78,26 +75,16 @@ sgp_status sgp_set_tuning(sgp_ctx *ctx, const sgp_tuning *t)
     if (!(t->spmv_lpr == 0 || t->spmv_lpr == 1 || t->spmv_lpr == 2 || t->spmv_lpr == 4 || t->spmv_lpr == 8))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_lpr must be 0, 1, 2, 4 or 8");
     if (t->tail_cap < -1) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: tail_cap must be >= -1");
-    if (t->ctail_cap != 0 && (t->ctail_cap < 256 || t->ctail_cap > (1 << 24)))
-        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: ctail_cap must be 0 or in [256, 16777216]");
     if (t->spmv_ilp < 0 || t->spmv_ilp > 2)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: spmv_ilp must be 0, 1 or 2");
-    if (t->coop_cap != 0 && (t->coop_cap < 256 || t->coop_cap > (1 << 24)))
-        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: coop_cap must be 0 or in [256, 16777216]");
     if (t->batch_chunk != 0 && (t->batch_chunk < 256 || t->batch_chunk > 65536))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: batch_chunk must be 0 or in [256, 65536]");
-    if (!(t->comp_size == 0 || (t->comp_size >= 64 && t->comp_size <= 8192 &&
-                                (t->comp_size & (t->comp_size - 1)) == 0)))
-        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: comp_size must be 0 or a power of two in [64, 8192]");
     if (!(t->bin_cap == 0 || t->bin_cap == -1 || (t->bin_cap >= 64 && t->bin_cap <= 8192)))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "set_tuning: bin_cap must be 0, -1 or in [64, 8192]");
     ctx->spmv_lpr = t->spmv_lpr;
-    ctx->bin_cap = t->bin_cap == 0 ? 1024 : t->bin_cap;
+    ctx->bin_cap = t->bin_cap;
     ctx->tail_cap = t->tail_cap;
-    ctx->comp_size = t->comp_size;
-    ctx->coop_cap = t->coop_cap;
     ctx->spmv_ilp = t->spmv_ilp;
-    ctx->ctail_cap = t->ctail_cap;
     ctx->batch_chunk = t->batch_chunk;
     return SGP_OK;
 }
@@ -155,52 +142,25 @@ sgp_status sgp_autotune(sgp_ctx *ctx, const sgp_matrix *M, const sgp_tree *T, sg
     if (cudaEventCreate(&run.e0) != cudaSuccess || cudaEventCreate(&run.e1) != cudaSuccess)
         return finish(sgp_fail(ctx, SGP_ERR_CUDA, "autotune: event creation failed"));
 
-    // 1. local block size, then tail size (each candidate rebuilds the factor)
+    // 1. tail size, then bin size (each candidate rebuilds the factor)
     if (tree) {
-        const int sizes[] = {0, 256, 512, 1024, 2048, 4096};
-        int best_cs = ctx->comp_size;
-        best_ms = 1e300;
-        for (int cs : sizes) {
-            ctx->comp_size = cs;
-            if ((st = build()) != SGP_OK) return finish(st);
-            double ms;
-            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
-            if (ms < best_ms) best_ms = ms, best_cs = cs;
-        }
-        ctx->comp_size = best_cs;
+        auto pick = [&](int *knob, const int *cand, int nc) -> sgp_status {
+            int best = *knob;
+            best_ms = 1e300;
+            for (int k = 0; k < nc; ++k) {
+                *knob = cand[k];
+                SGP_TRY(build());
+                double ms;
+                SGP_TRY(run.time_it(&ms));
+                if (ms < best_ms) best_ms = ms, best = cand[k];
+            }
+            *knob = best;
+            return SGP_OK;
+        };
         const int caps[] = {0, 256, 512, 1024, 2048, 4096, -1};
-        int best_cap = ctx->tail_cap;
-        best_ms = 1e300;
-        for (int cap : caps) {
-            ctx->tail_cap = cap;
-            if ((st = build()) != SGP_OK) return finish(st);
-            double ms;
-            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
-            if (ms < best_ms) best_ms = ms, best_cap = cap;
-        }
-        ctx->tail_cap = best_cap;
-        const int ctails[] = {0, 8192, 16384, 32768};
-        int best_ct = ctx->ctail_cap;
-        best_ms = 1e300;
-        for (int cc : ctails) {
-            ctx->ctail_cap = cc;
-            if ((st = build()) != SGP_OK) return finish(st);
-            double ms;
-            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
-            if (ms < best_ms) best_ms = ms, best_ct = cc;
-        }
-        ctx->ctail_cap = best_ct;
-        const int coops[] = {0, 8192, 32768, 131072};
-        int best_coop = ctx->coop_cap;
-        best_ms = 1e300;
-        for (int cc : coops) {
-            ctx->coop_cap = cc;
-            if ((st = build()) != SGP_OK) return finish(st);
-            double ms;
-            if ((st = run.time_it(&ms)) != SGP_OK) return finish(st);
-            if (ms < best_ms) best_ms = ms, best_coop = cc;
-        }
-        ctx->coop_cap = best_coop;
+        if ((st = pick(&ctx->tail_cap, caps, 7)) != SGP_OK) return finish(st);
+        const int bins[] = {0, -1, 512, 1024, 2048};
+        if ((st = pick(&ctx->bin_cap, bins, 5)) != SGP_OK) return finish(st);
         if ((st = build()) != SGP_OK) return finish(st);
     }
     // 2. lanes per block row of the product and rows in flight per lane

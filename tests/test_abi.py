@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared():
     with open(os.path.join(ROOT, "include", "sgp.h")) as f:
         txt = f.read()
-    names = re.findall(r"^\s*(?:sgp_status|void|const char \*)\s*\*?(sgp_\w+)\s*\(", txt, re.M)
+    names = re.findall(r"^\s*(?:sgp_status|void|const \w+ \*)\s*\*?(sgp_\w+)\s*\(", txt, re.M)
     return sorted(set(names))
 
 

@@ -19,36 +19,30 @@ def ctx(cuda_device):
 
 def test_set_tuning_validates(ctx):
     for bad in (dict(spmv_lpr=3), dict(tail_cap=-2), dict(batch_chunk=100), dict(batch_chunk=70000),
-                dict(comp_size=1000), dict(comp_size=32), dict(comp_size=16384), dict(coop_cap=100),
-                dict(coop_cap=1 << 25), dict(spmv_ilp=3), dict(ctail_cap=100)):
+                dict(spmv_ilp=3), dict(bin_cap=32), dict(bin_cap=-2), dict(bin_cap=9000)):
         with pytest.raises(sgp.SgpError):
             ctx.set_tuning(**bad)
-    for bad in (dict(bin_cap=32), dict(bin_cap=-2), dict(bin_cap=9000)):
-        with pytest.raises(sgp.SgpError):
-            ctx.set_tuning(**bad)
-    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, comp_size=256, coop_cap=4096, spmv_ilp=2,
-                   ctail_cap=8192, bin_cap=512)
-    assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "comp_size": 256,
-                                "coop_cap": 4096, "spmv_ilp": 2, "ctail_cap": 8192, "bin_cap": 512,
-                                "ms_per_iteration": 0.0}
+    ctx.set_tuning(spmv_lpr=4, tail_cap=512, batch_chunk=1024, spmv_ilp=2, bin_cap=512)
+    assert ctx.get_tuning() == {"spmv_lpr": 4, "tail_cap": 512, "batch_chunk": 1024, "spmv_ilp": 2,
+                                "bin_cap": 512, "ms_per_iteration": 0.0}
     ctx.set_tuning(bin_cap=-1)
     assert ctx.get_tuning()["bin_cap"] == -1
     ctx.set_tuning()
-    assert ctx.get_tuning()["bin_cap"] == 1024
+    assert ctx.get_tuning()["bin_cap"] == 0
 
 
-@pytest.mark.parametrize("cap,cs,coop,ct", [(0, 0, 0, 0), (64, 1024, 0, 0), (256, 64, 2048, 0), (-1, 256, 0, 0),
-                                            (1024, 8192, 0, 0), (0, 4096, 0, 0), (1024, 0, 8192, 0),
-                                            (0, 0, 20000, 0), (256, 1024, 4096, 0), (1024, 0, 0, 8192),
-                                            (256, 0, 0, 20000), (1024, 0, 16384, 4096), (256, 1024, 0, 16384)])
+@pytest.mark.parametrize("cap,bins", [(0, -1), (64, -1), (256, -1), (-1, -1), (1024, -1), (1024, 0), (-1, 0),
+                                      (1024, 512), (256, 2048), (0, 1024)])
 @pytest.mark.parametrize("prec", [sgp.PREC_F64, sgp.PREC_MIXED])
-def test_contraction_granularity_does_not_change_the_solution(ctx, cap, cs, coop, ct, prec):
+def test_contraction_granularity_does_not_change_the_solution(ctx, cap, bins, prec):
     c = workloads.ball(n=20000, seed=2002, gamma0=1e-3)
-    ctx.set_tuning(tail_cap=cap, comp_size=cs, coop_cap=coop, ctail_cap=ct)
+    ctx.set_tuning(tail_cap=cap, bin_cap=bins)
     s = GpuSystem(ctx, c, precision=prec)
     F = c.forces()
     v, info = ctx.pcg_solve(s.M, s.Fac, dev_tensor(F), tol=1e-10, precision=prec)
-    assert info.status == 0 and info.true_rel_residual <= 1e-10
+    # the recursive residual meets tol; the true one differs from it by
+    # rounding (about eps kappa(Gamma), 1e-13 here)
+    assert info.status == 0 and info.true_rel_residual <= 1.05e-10
     ctx.set_tuning(tail_cap=-1)
     ref = GpuSystem(ctx, c, precision=sgp.PREC_F64)
     vr, _ = ctx.pcg_solve(ref.M, ref.Fac, dev_tensor(F), tol=1e-12)
@@ -74,9 +68,7 @@ def test_autotune_single_system(ctx):
     F = dev_tensor(c.forces())
     t = ctx.autotune(s.M, s.T, s.Fac, F, precision=sgp.PREC_MIXED, iterations=20)
     assert t["tail_cap"] in (0, 256, 512, 1024, 2048, 4096, -1)
-    assert t["comp_size"] in (0, 256, 512, 1024, 2048, 4096)
-    assert t["coop_cap"] in (0, 8192, 32768, 131072)
-    assert t["ctail_cap"] in (0, 8192, 16384, 32768)
+    assert t["bin_cap"] in (0, -1, 512, 1024, 2048)
     assert t["spmv_lpr"] in (1, 2, 4, 8) and t["spmv_ilp"] in (1, 2)
     assert t["ms_per_iteration"] > 0
     assert ctx.get_tuning()["tail_cap"] == t["tail_cap"]
