@@ -502,7 +502,8 @@ def other_configs(args):
     runs = [("cube1k", ["--workload", "cube1k", "--steps", "20", "--compare", "1"]),
             ("hex4m", ["--workload", "hex4m", "--steps", "2", "--compare", "1"]),
             ("batch512", ["--workload", "batch512", "--steps", "2"]),
-            ("warm200k", ["--workload", "warm200k"])]
+            ("warm200k", ["--workload", "warm200k"]),
+            ("aug1m", ["--workload", "aug1m", "--steps", "2"])]
     out = {}
     for name, extra in runs:
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "3", "--autotune", "0",
@@ -523,7 +524,8 @@ def other_configs(args):
         keep = {k: rec[k] for k in ("value", "unit", "ms_per_step", "iterations", "true_rel_residual",
                                     "outer_iterations", "true_rel_residual_max", "solve_only", "forms",
                                     "latency_ms", "looped_plain_fp64", "looped_mixed", "learned", "zero_guess",
-                                    "previous_v", "solve_only_ms_mean", "tree_layout", "clocks")
+                                    "previous_v", "solve_only_ms_mean", "tree_layout", "clocks", "augmented",
+                                    "plain_fp64", "outer_vs_plain_iterations")
                 if k in rec}
         keep["workload"] = rec.get("config", {}).get("workload")
         if "roofline" in rec:
@@ -644,6 +646,79 @@ def run_batch(args):
                          "note": "the same precision as the batch, one instance per solve: the batching gain "
                                  "is value / this"},
         "gpu_launches": int(launches), "tuning": tuning, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_augmented(args):
+    """The augmented spanning-forest preconditioner (Section 3.1) with the
+    nested flexible CG of Section 5 against the plain spanning-forest PCG on
+    the 1e6-cell spheroid, FP64 both (the nested solve is FP64): setup of
+    graph, blocks, forest and factor once, then per step the augmentation
+    (partition + added edges + P') and one flexible solve, and separately
+    one plain solve; iteration counts and solves/s of each."""
+    import torch
+
+    import paper_2410_04512_gb300 as sgp
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgp.Context(0, stream)
+    c = WORKLOADS["ball1m"]["make"](replica_seed(0))
+    n = c.n
+    pos = torch.from_numpy(c.pos).to(dev)
+    radii = torch.from_numpy(c.radii).to(dev)
+    tp, tq = (torch.from_numpy(t).to(dev) for t in c.tables())
+    F = torch.from_numpy(c.forces()).to(dev)
+    g = ctx.collision_graph(pos, radii)
+    ij = g.edges()
+    gp, gq = workloads.pair_gamma_torch(c.seed, ij, tp, tq)
+    M = ctx.friction_assemble(g, pos, gp.contiguous(), gq.contiguous(), c.gamma0, sgp.PREC_F64)
+    T = ctx.max_spanning_tree(M)
+    Fh = ctx.tree_factor(M, T)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        a, b = ev(), ev()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    A = None
+    plain, aug = [], []
+    for step in range(args.warmup + args.steps):
+        (_, ip), pms = timed(lambda: ctx.pcg_solve(M, Fh, F, tol=args.tol))
+        A, ams = timed(lambda: ctx.augment_tree(M, T, args.aug_t, A))
+        (_, ia), fms = timed(lambda: ctx.fcg_solve(M, A, Fh, F, tol=args.tol, inner_tol=args.aug_delta))
+        if step >= args.warmup:
+            plain.append((pms, ip))
+            aug.append((ams, fms, ia))
+    info = A.info()
+    p_ms = float(np.median([x[0] for x in plain]))
+    a_ms = float(np.median([x[0] + x[1] for x in aug]))
+    ia = aug[-1][2]
+    ip = plain[-1][1]
+    line = {
+        "metric": METRIC, "value": round(1e3 / a_ms, 4), "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(a_ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["ball1m"]["desc"] + "; augmented spanning forest (t=%d pieces of at "
+                               "most %d cells, %d edges added) + flexible CG, inner PCG to delta=%g"
+                               % (info["t"], info["piece_cap"], info["added"], args.aug_delta),
+                   "n_cells": n, "tol": args.tol,
+                   "step": "augmentation (partition, added edges, P') + flexible CG solve; graph, blocks, "
+                           "forest and factor built once"},
+        "augmented": {"t": info["t"], "pieces": info["pieces"], "added_edges": info["added"],
+                      "outer_iterations": ia.outer_iterations, "inner_iterations": ia.iterations,
+                      "true_rel_residual": ia.true_rel_residual,
+                      "augment_ms": round(float(np.median([x[0] for x in aug])), 3),
+                      "solve_ms": round(float(np.median([x[1] for x in aug])), 3),
+                      "solves_per_s": round(1e3 / a_ms, 4)},
+        "plain_fp64": {"iterations": ip.iterations, "true_rel_residual": ip.true_rel_residual,
+                       "solve_ms": round(p_ms, 3), "solves_per_s": round(1e3 / p_ms, 4)},
+        "outer_vs_plain_iterations": round(ia.outer_iterations / max(ip.iterations, 1), 3),
     }
     print(json.dumps(line), flush=True)
 
@@ -918,7 +993,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgp", choices=["sgp", "reference"])
-    ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS) + ["batch512", "warm200k"])
+    ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS) + ["batch512", "warm200k", "aug1m"])
+    ap.add_argument("--aug-t", dest="aug_t", type=int, default=0,
+                    help="aug1m: pieces of the augmented forest (0: round(n^(1/4)))")
+    ap.add_argument("--aug-delta", dest="aug_delta", type=float, default=0.1,
+                    help="aug1m: relative tolerance of the inner PCG")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batch512 workload")
     ap.add_argument("--precision", default="mixed", choices=["f64", "mixed"])
     ap.add_argument("--precond", default="tree", choices=["tree", "jacobi", "none"])
@@ -943,6 +1022,8 @@ def main():
         run_batch(args)
     elif args.workload == "warm200k":
         run_warm(args)
+    elif args.workload == "aug1m":
+        run_augmented(args)
     else:
         run_gpu(args)
 
