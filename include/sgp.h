@@ -60,6 +60,11 @@ typedef enum {
     SGP_PRECOND_NONE = 2           /* plain CG */
 } sgp_precond;
 
+typedef enum {
+    SGP_STOP_RESIDUAL = 0,  /* |r|_2 <= tol |F|_2 on the recursive residual */
+    SGP_STOP_ERROR = 1      /* Gauss-Radau bound on the Gamma-norm error <= tol (Sections 4-5) */
+} sgp_stop;
+
 typedef struct sgp_ctx sgp_ctx;
 typedef struct sgp_graph sgp_graph;
 typedef struct sgp_matrix sgp_matrix;
@@ -67,13 +72,20 @@ typedef struct sgp_tree sgp_tree;
 typedef struct sgp_factor sgp_factor;
 
 typedef struct {
-    double tol;          /* stop when |F - Gamma v|_2 <= tol |F|_2 (recursive residual) */
+    double tol;          /* stop when |F - Gamma v|_2 <= tol |F|_2 (recursive residual), or
+                            with stop = SGP_STOP_ERROR when the error bound is <= tol */
     int64_t maxit;       /* iteration cap (inner iterations in total for MIXED) */
     int32_t precond;     /* sgp_precond */
     int32_t precision;   /* sgp_precision; MIXED needs a matrix assembled with MIXED */
     int32_t x0_given;    /* 0: start from v = 0; 1: v holds the initial guess on entry */
     int32_t max_outer;   /* MIXED: refinement steps cap (<= 0 means 30) */
-    double inner_tol;    /* MIXED: relative residual target of each FP32 inner solve (<= 0: 1e-3) */
+    double inner_tol;    /* MIXED: relative residual target of each FP32 inner solve (<= 0: 1e-3);
+                            sgp_fcg_solve: that of each inner PCG (0: 0.1) */
+    int32_t stop;        /* sgp_stop (sgp_pcg_solve in FP64 only; 0 elsewhere) */
+    double mu;           /* SGP_STOP_ERROR: a lower bound of lambda_min(H Gamma) for the
+                            Gauss-Radau rule; <= 0 takes 1 for the tree preconditioner
+                            (Section 4: lambda_min(Gamma, P) >= 1) and gamma0 for none
+                            (Lemma 2.4); block Jacobi needs it given */
 } sgp_solve_opts;
 
 typedef struct {
@@ -84,6 +96,10 @@ typedef struct {
     int32_t status;            /* sgp_status of the solve */
     double rel_residual;       /* final recursive |r|/|F| (FP64 outer residual for MIXED) */
     double true_rel_residual;  /* |F - Gamma v|/|F| recomputed in FP64 at exit */
+    double err_bound;          /* FP64 sgp_pcg_solve: Gauss-Radau upper bound on
+                                  |v* - v|_Gamma / |v - v0|_Gamma at the last preconditioned
+                                  residual the solve computed (v* the exact solution);
+                                  0 elsewhere */
 } sgp_solve_info;
 
 /* ---- context ------------------------------------------------------------ */
@@ -221,6 +237,13 @@ void sgp_factor_destroy(sgp_factor *factor);
  * Solves Gamma v = F.  r = F - Gamma v0, z = H r, p = z, rho = r^T z; each
  * iteration: q = Gamma p, alpha = rho / p^T q, v += alpha p, r -= alpha q,
  * stop when |r|_2 <= tol |F|_2, z = H r, beta = r^T z / rho, p = z + beta p.
+ * SGP_STOP_ERROR (FP64 only; the paper monitors CG with Gauss-Radau error
+ * estimates, Section 5): after each new rho the Gauss-Radau upper bound of
+ * the Gamma-norm error, phi rho with phi_0 = 1/mu and
+ * phi <- (phi - alpha) / (mu (phi - alpha) + beta), is compared with
+ * tol^2 sum_j alpha_j rho_j (= |v - v0|_Gamma^2); the solve stops when the
+ * bound is below it, so |v* - v|_Gamma <= tol |v - v0|_Gamma in exact
+ * arithmetic.  Scalars only: no extra pass over memory.
  * H is P^{-1} from `factor` (required for SGP_PRECOND_TREE), the block-Jacobi
  * inverse (computed inside the call) or I.  MIXED runs FP64 iterative
  * refinement: r = F - Gamma v in FP64, an FP32 inner PCG on r/|r| to

@@ -23,6 +23,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_NOT_SPD, ERR_NO_CONV
 PREC_F64, PREC_MIXED = 0, 1
 PRECOND_TREE, PRECOND_BLOCK_JACOBI, PRECOND_NONE = 0, 1, 2
 KT_SPMV, KT_TREE_SOLVE, KT_PCG_VECTOR = 0, 1, 2
+STOP_RESIDUAL, STOP_ERROR = 0, 1
 MPNN_PARAMS = 25539
 MPNN_LOSS_L2, MPNN_LOSS_ENERGY = 0, 1
 WARM_MR_SCALE = 1
@@ -40,7 +41,8 @@ class SgpError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int64), ("precond", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("x0_given", ctypes.c_int32),
-                ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+                ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("stop", ctypes.c_int32),
+                ("mu", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -54,7 +56,7 @@ class Tuning(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("outer_iterations", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("true_rel_residual", ctypes.c_double)]
+                ("true_rel_residual", ctypes.c_double), ("err_bound", ctypes.c_double)]
 
 
 _lib = None
@@ -293,6 +295,7 @@ class Info:
     status: int
     rel_residual: float
     true_rel_residual: float
+    err_bound: float = 0.0
 
 
 class Context:
@@ -365,16 +368,18 @@ class Context:
     def pcg_solve(self, M: Matrix, Fh: Factor | None, F: torch.Tensor, v: torch.Tensor | None = None,
                   tol: float = 1e-8, maxit: int = 100000, precond: int = PRECOND_TREE,
                   precision: int = PREC_F64, x0_given: bool = False, max_outer: int = 0,
-                  inner_tol: float = 0.0, raise_on_error: bool = True):
+                  inner_tol: float = 0.0, raise_on_error: bool = True, stop: int = 0, mu: float = 0.0):
+        """PCG (Section 1.1); stop=STOP_ERROR stops on the Gauss-Radau bound
+        of the Gamma-norm error (FP64), mu its lower eigenvalue bound."""
         _check_vec(F, M.n, name="F")
         v = torch.zeros_like(F) if v is None else v
         _check_vec(v, M.n, name="v")
-        o = SolveOpts(tol, maxit, precond, precision, int(x0_given), max_outer, inner_tol)
+        o = SolveOpts(tol, maxit, precond, precision, int(x0_given), max_outer, inner_tol, stop, mu)
         inf = SolveInfo()
         rc = _lib.sgp_pcg_solve(self.ptr, M.ptr, Fh.ptr if Fh is not None else None, _ptr(F), _ptr(v),
                                 ctypes.byref(o), ctypes.byref(inf))
         info = Info(inf.iterations, inf.outer_iterations, inf.status, inf.rel_residual,
-                    inf.true_rel_residual)
+                    inf.true_rel_residual, inf.err_bound)
         if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
             self._ok(rc)
         return v, info
@@ -398,7 +403,8 @@ class Context:
         inf = SolveInfo()
         rc = _lib.sgp_fcg_solve(self.ptr, M.ptr, A.ptr, Fh.ptr, _ptr(F), _ptr(v), ctypes.byref(o), inner_maxit,
                                 ctypes.byref(inf))
-        info = Info(inf.iterations, inf.outer_iterations, inf.status, inf.rel_residual, inf.true_rel_residual)
+        info = Info(inf.iterations, inf.outer_iterations, inf.status, inf.rel_residual, inf.true_rel_residual,
+                    inf.err_bound)
         if rc != OK and (raise_on_error or rc not in (ERR_NO_CONVERGENCE,)):
             self._ok(rc)
         return v, info

@@ -498,6 +498,8 @@ sgp_status sgp_pcg_solve_batched(sgp_ctx *ctx, const sgp_matrix *M, const sgp_fa
     if (n > 0 && (!F || !v)) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg_batched: NULL vector");
     if (!(opts->tol > 0.0) || opts->maxit <= 0)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg_batched: tol must be > 0 and maxit >= 1");
+    if (opts->stop != SGP_STOP_RESIDUAL)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg_batched: residual stopping only");
     if (opts->precond < 0 || opts->precond > 2)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg_batched: bad preconditioner");
     if (opts->precond == SGP_PRECOND_TREE && (!Fac || Fac->n != n))

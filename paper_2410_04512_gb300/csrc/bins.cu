@@ -1627,6 +1627,10 @@ sgp_status bins_build(sgp_ctx *ctx, sgp_factor *F, const sgp_matrix *M)
     const bool f64_bins = ctx->bin_cap > 0;
     if (n == 0 || bmax <= 0 || LV == 0) return SGP_OK;
     if (!f64_bins && F->precision != SGP_PREC_MIXED) return SGP_OK;
+    // default: a factor whose every level fits the one-block tail is solved
+    // by that single launch (the three bin launches measured slower on the
+    // 1000-cell cube)
+    if (ctx->bin_cap == 0 && F->tail_level == 0) return SGP_OK;
     B.LV = LV;
     B.LVP = pad4(LV + 1);
     B.bmax = bmax;

@@ -158,7 +158,7 @@ template <typename T, int PREC>
 __global__ void k_init(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, int64_t n,
                        const T *__restrict__ F, const T *__restrict__ x, int x_given, T *r, T *w,
                        const T *__restrict__ jac, double tol2, long long maxit, double *partials,
-                       Scal *sc)
+                       Scal *sc, double mu, int stopE, double tolE2)
 {
     __shared__ double sh[RB / 32];
     double ff = 0.0, rr = 0.0;
@@ -197,6 +197,12 @@ __global__ void k_init(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, 
             sc->maxit = maxit;
             sc->status = 0;
             sc->done = (a == 0.0 || b <= tol2 * a) ? 1 : 0;
+            sc->mu = mu;
+            sc->phi = mu > 0.0 ? 1.0 / mu : 0.0;
+            sc->gsum = 0.0;
+            sc->est = 0.0;
+            sc->stopE = stopE;
+            sc->tolE2 = tolE2;
         }
     }
 }
@@ -222,6 +228,7 @@ __global__ void k_rz_init(int64_t n, const T *__restrict__ r, const T *__restric
         if (threadIdx.x == 0) {
             sc->rho = rz;
             sc->rz = rz;
+            sc->est = sc->phi * rz;
             if (!(rz > 0.0) || !isfinite(rz)) {
                 sc->status = SGP_ERR_NOT_SPD;
                 sc->done = 1;
@@ -281,9 +288,7 @@ __global__ void k_update(int64_t n, X *x, const T *__restrict__ p, T *r, const T
                 sc->done = 1;
                 sc->status = SGP_ERR_NO_CONVERGENCE;
             } else if (PREC != 0) {
-                sc->beta = Bz / sc->rho;
-                sc->rho = Bz;
-                sc->rz = Bz;
+                rz_finish(sc, Bz);
             }
         }
     }
@@ -338,9 +343,7 @@ __global__ void __launch_bounds__(RB) k_update_v(int64_t n, T *x, const T *__res
                 sc->done = 1;
                 sc->status = SGP_ERR_NO_CONVERGENCE;
             } else if (PREC != 0) {  // identity: z = r, so r^T z = |r|^2
-                sc->beta = A / sc->rho;
-                sc->rho = A;
-                sc->rz = A;
+                rz_finish(sc, A);
             }
         }
     }
@@ -631,7 +634,8 @@ inline Blk<float> tree_blk<float>(const sgp_factor *F)
 template <typename T, typename X>
 sgp_status pcg_core(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int precond, Blk<T> B,
                     const int32_t *row_ptr, int64_t n, bool tree, const T *F, X *x, int x_given, double tol,
-                    int64_t maxit, T *r, T *p, T *q, T *w, double *partials, Scal *sc, Scal *hs)
+                    int64_t maxit, T *r, T *p, T *q, T *w, double *partials, Scal *sc, Scal *hs, double mu = 0.0,
+                    int stopE = 0)
 {
     const T g0 = (T)M->gamma0;
     const T *jac = nullptr;
@@ -645,17 +649,20 @@ sgp_status pcg_core(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, in
     const T *xin = reinterpret_cast<const T *>(x);
     if (x_given && sizeof(X) != sizeof(T))
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: initial guess precision mismatch");
+    // error mode: the residual test never fires (stop2 = -|F|^2); the
+    // Gauss-Radau test in rz_finish decides
+    const double tol2 = stopE ? -1.0 : tol * tol;
     cudaEvent_t ev;
     SGP_TRY(kt_begin(ctx, SGP_KT_PCG_VECTOR, &ev));
     if (precond == SGP_PRECOND_TREE)
-        LAUNCH(ctx, (k_init<T, 0>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol * tol,
-               (long long)maxit, partials, sc);
+        LAUNCH(ctx, (k_init<T, 0>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol2,
+               (long long)maxit, partials, sc, mu, stopE, tol * tol);
     else if (precond == SGP_PRECOND_BLOCK_JACOBI)
-        LAUNCH(ctx, (k_init<T, 1>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol * tol,
-               (long long)maxit, partials, sc);
+        LAUNCH(ctx, (k_init<T, 1>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol2,
+               (long long)maxit, partials, sc, mu, stopE, tol * tol);
     else
-        LAUNCH(ctx, (k_init<T, 2>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol * tol,
-               (long long)maxit, partials, sc);
+        LAUNCH(ctx, (k_init<T, 2>), G, RB, 0, B, row_ptr, g0, n, F, xin, x_given, r, w, jac, tol2,
+               (long long)maxit, partials, sc, mu, stopE, tol * tol);
     SGP_TRY(kt_end(ctx, SGP_KT_PCG_VECTOR, ev));
     SGP_TRY(read_back(ctx, hs, sc, sizeof(Scal)));
     if (hs->done) return SGP_OK;
@@ -788,17 +795,17 @@ sgp_status pcg_core(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, in
 template <typename T, typename X>
 sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int precond, const T *F, X *x,
                    int x_given, double tol, int64_t maxit, T *r, T *p, T *q, T *w, T *Ft, T *xt,
-                   double *partials, Scal *sc, Scal *hs)
+                   double *partials, Scal *sc, Scal *hs, double mu = 0.0, int stopE = 0)
 {
     static_assert(sizeof(X) == sizeof(T), "iterate and vectors share one precision");
     const bool tree = precond == SGP_PRECOND_TREE && ctx->fused && Ft && xt && bins_tree_ready<T>(Fac, M);
     if (!tree)
         return pcg_core<T, X>(ctx, M, Fac, precond, make_blk<T>(M), bp<const int32_t>(M->row_ptr), M->n, false, F,
-                              x, x_given, tol, maxit, r, p, q, w, partials, sc, hs);
+                              x, x_given, tol, maxit, r, p, q, w, partials, sc, hs, mu, stopE);
     SGP_TRY(bins_to_tree<T>(ctx, Fac, F, Ft));
     if (x_given) SGP_TRY(bins_to_tree<T>(ctx, Fac, reinterpret_cast<const T *>(x), xt));
     SGP_TRY((pcg_core<T, T>(ctx, M, Fac, precond, tree_blk<T>(Fac), bp<const int32_t>(Fac->bl.rpt), Fac->bl.NT,
-                            true, Ft, xt, x_given, tol, maxit, r, p, q, w, partials, sc, hs)));
+                            true, Ft, xt, x_given, tol, maxit, r, p, q, w, partials, sc, hs, mu, stopE)));
     return bins_from_tree<T>(ctx, Fac, xt, reinterpret_cast<T *>(x));
 }
 
@@ -878,6 +885,21 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: MIXED needs a matrix assembled with MIXED");
     if (mixed && opts->precond == SGP_PRECOND_TREE && Fac->precision != SGP_PREC_MIXED)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: MIXED needs a factor of a MIXED matrix");
+    if (opts->stop != SGP_STOP_RESIDUAL && opts->stop != SGP_STOP_ERROR)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: bad stopping rule");
+    const bool stopE = opts->stop == SGP_STOP_ERROR;
+    if (stopE && mixed) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: error-bound stopping is FP64 only");
+    if (!std::isfinite(opts->mu))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: mu must be finite");
+    // lower bound of lambda_min(H Gamma) for the Gauss-Radau rule
+    double mu = opts->mu;
+    if (!(mu > 0.0)) {
+        if (opts->precond == SGP_PRECOND_TREE) mu = 1.0;            // Section 4
+        else if (opts->precond == SGP_PRECOND_NONE) mu = M->gamma0;  // Lemma 2.4
+        else if (stopE)
+            return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "pcg: block Jacobi error-bound stopping needs mu > 0");
+        else mu = 0.0;
+    }
     SGP_CUDA(ctx, cudaSetDevice(ctx->device));
     sgp_solve_info inf{};
     if (n == 0) {
@@ -929,8 +951,9 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
     double hres[2] = {0, 0};
     if (!mixed) {
         SGP_TRY(pcg_run<double, double>(ctx, M, Fac, opts->precond, F, v, opts->x0_given, opts->tol,
-                                        opts->maxit, r, p, q, w, Ft64, xt64, partials, sc, &hs));
+                                        opts->maxit, r, p, q, w, Ft64, xt64, partials, sc, &hs, mu, stopE ? 1 : 0));
         inf.iterations = hs.it;
+        inf.err_bound = (mu > 0.0 && hs.gsum > 0.0) ? std::sqrt(std::max(hs.est, 0.0) / hs.gsum) : 0.0;
         inf.status = hs.status;
         inf.rel_residual = hs.FF > 0 ? std::sqrt(hs.rr / hs.FF) : 0.0;
         if (hs.FF == 0.0) SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
@@ -1026,6 +1049,8 @@ sgp_status sgp_fcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_aug *A, co
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: inner_tol must be in [0, 1)");
     if (opts->precond != SGP_PRECOND_TREE || opts->precision != SGP_PREC_F64)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: the nested solve is FP64 with the tree preconditioner");
+    if (opts->stop != SGP_STOP_RESIDUAL)
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: residual stopping only");
     if (A->n != n || A->mgen != M->gen || !A->P)
         return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: the augmented forest was built from another matrix");
     if (Fac->n != n) return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "fcg: the factor has another size");

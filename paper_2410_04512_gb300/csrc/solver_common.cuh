@@ -17,19 +17,33 @@ struct Scal {
     unsigned cnt;
     int pad;
     int xpend;   // the step's x += alpha p is still to be applied
+    // Gauss-Radau bound of the Gamma-norm error (mu > 0): phi, the sum of
+    // alpha_j rho_j so far, the bound phi rho; stopE: stop on it (tolE2 = tol^2)
+    double mu, phi, gsum, est, tolE2;
+    int stopE;
 };
 
 // The end of a step's r^T z reduction: beta = rz / rho, rho = rz, or a
-// breakdown when rz is not positive.
+// breakdown when rz is not positive.  Also the Gauss-Radau recursion of the
+// Gamma-norm error (phi <- (phi - alpha) / (mu (phi - alpha) + beta), bound
+// phi rho) and, in error mode, the stopping test on it.
 __device__ __forceinline__ void rz_finish(Scal *sc, double rz)
 {
     if (!(rz > 0.0) || !isfinite(rz)) {
-        sc->status = SGP_ERR_NOT_SPD;
         sc->done = 1;
-    } else {
-        sc->beta = rz / sc->rho;
-        sc->rho = rz;
-        sc->rz = rz;
+        if (!(sc->stopE && rz == 0.0)) sc->status = SGP_ERR_NOT_SPD;   // rz = 0: solved exactly
+        return;
+    }
+    const double alpha = sc->alpha, rho = sc->rho;
+    sc->beta = rz / rho;
+    sc->rho = rz;
+    sc->rz = rz;
+    if (sc->mu > 0.0) {
+        sc->gsum += alpha * rho;
+        const double d = sc->phi - alpha;
+        sc->phi = d / (sc->mu * d + sc->beta);
+        sc->est = sc->phi * rz;
+        if (sc->stopE && sc->est <= sc->tolE2 * sc->gsum) sc->done = 1;
     }
 }
 
