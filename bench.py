@@ -525,7 +525,8 @@ def other_configs(args):
                                     "outer_iterations", "true_rel_residual_max", "solve_only", "forms",
                                     "latency_ms", "looped_plain_fp64", "looped_mixed", "learned", "zero_guess",
                                     "previous_v", "solve_only_ms_mean", "tree_layout", "clocks", "augmented",
-                                    "plain_fp64", "outer_vs_plain_iterations")
+                                    "plain_fp64", "outer_vs_plain_iterations", "augmented_sweep",
+                                    "error_bound_stopping")
                 if k in rec}
         keep["workload"] = rec.get("config", {}).get("workload")
         if "roofline" in rec:
@@ -656,7 +657,10 @@ def run_augmented(args):
     the 1e6-cell spheroid, FP64 both (the nested solve is FP64): setup of
     graph, blocks, forest and factor once, then per step the augmentation
     (partition + added edges + P') and one flexible solve, and separately
-    one plain solve; iteration counts and solves/s of each."""
+    one plain solve; iteration counts and solves/s of each.  Also one solve
+    each of two other settings (1000 pieces; inner tolerance 1e-3) and the
+    plain PCG stopped on the Gauss-Radau error bound (Sections 4-5) next to
+    residual stopping at this tolerance and at the paper's 1e-5."""
     import torch
 
     import paper_2410_04512_gb300 as sgp
@@ -700,6 +704,26 @@ def run_augmented(args):
     a_ms = float(np.median([x[0] + x[1] for x in aug]))
     ia = aug[-1][2]
     ip = plain[-1][1]
+    # one solve each of other piece counts and inner tolerances
+    sweep = []
+    for t, delta in ((1000, args.aug_delta), (0, 1e-3)):
+        At, ams2 = timed(lambda: ctx.augment_tree(M, T, t))
+        (_, it2), fms2 = timed(lambda: ctx.fcg_solve(M, At, Fh, F, tol=args.tol, inner_tol=delta))
+        i2 = At.info()
+        sweep.append({"t": i2["t"], "pieces": i2["pieces"], "added_edges": i2["added"], "inner_tol": delta,
+                      "outer_iterations": it2.outer_iterations, "inner_iterations": it2.iterations,
+                      "solve_ms": round(fms2, 3), "true_rel_residual": it2.true_rel_residual})
+    # Gauss-Radau error-bound stopping (mu = 1) against residual stopping,
+    # plain forest PCG, at this tolerance and at the paper's 1e-5
+    estop = []
+    for tol in (args.tol, 1e-5):
+        (_, ir), rms = timed(lambda: ctx.pcg_solve(M, Fh, F, tol=tol))
+        (_, ie), ems = timed(lambda: ctx.pcg_solve(M, Fh, F, tol=tol, stop=sgp.STOP_ERROR))
+        estop.append({"tol": tol, "residual_stop": {"iterations": ir.iterations, "solve_ms": round(rms, 3),
+                                                     "err_bound": ir.err_bound,
+                                                     "true_rel_residual": ir.true_rel_residual},
+                      "error_stop": {"iterations": ie.iterations, "solve_ms": round(ems, 3),
+                                     "err_bound": ie.err_bound, "true_rel_residual": ie.true_rel_residual}})
     line = {
         "metric": METRIC, "value": round(1e3 / a_ms, 4), "unit": "solves/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(a_ms, 3),
@@ -719,6 +743,8 @@ def run_augmented(args):
         "plain_fp64": {"iterations": ip.iterations, "true_rel_residual": ip.true_rel_residual,
                        "solve_ms": round(p_ms, 3), "solves_per_s": round(1e3 / p_ms, 4)},
         "outer_vs_plain_iterations": round(ia.outer_iterations / max(ip.iterations, 1), 3),
+        "augmented_sweep": sweep,
+        "error_bound_stopping": estop,
     }
     print(json.dumps(line), flush=True)
 
