@@ -207,11 +207,14 @@ def outer_bytes(n: int, m: int) -> int:
     return 2 * m * 52 + n * (4 + 4 * 24) + n * (24 + 12 + 12) + n * (12 + 24 + 24)
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the current kernels on the default workload and form
-# (cold, serialised launches: the tree solve's levels re-read from DRAM what
-# the previous level left in L2); other workloads report null.
-MEASURED_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the current kernels on the default workload and form, one kernel per ncu
+# capture, one launch each (profiles/dram_fused_step_ball1m.md): the tree
+# step is its four launches (k_bin_fwd 87.77 MB, k_leaksum 0.17 MB, k_top
+# 0.22 MB, k_bin_bwd 107.91 MB); other workloads and forms report null.
+MEASURED_TRAFFIC = {
+    ("ball1m", "mixed", "tree"): {"spmv": 140545792, "tree": 196073984, "vector": 36145920},
+}
 
 
 def spmv_bytes(n: int, m: int, fp: int) -> int:
@@ -831,7 +834,26 @@ def run_warm(args):
             vprev = v_next
             pos = (pos + 0.01 * v_next).contiguous()
     launches = ctx.launch_count()
+    # inference broken into its stages (per-stage CUDA events, repeated on
+    # the last step's system after the timed sequence)
+    KW = (sgp.KT_WARM_BASIS, sgp.KT_WARM_LAYERS, sgp.KT_WARM_CHECK)
+    ctx.set_kernel_timing(True)
+    for k in KW:
+        ctx.kernel_time(k, reset=True)
+    reps = 10
+    for _ in range(reps):
+        ctx.warm_start(net, H["M"], H["Fh"], F, vprev, mr_scale=True)
+    torch.cuda.synchronize()
+    stage = {name: round(ctx.kernel_time(k)[0] / reps, 4)
+             for name, k in zip(("basis_and_features", "layers_and_output", "scaling_and_check"), KW)}
+    ctx.set_kernel_timing(False)
     R = {k: np.array([r[k] for r in rows], dtype=np.float64) for k in rows[0]}
+    # what the guess's error should save: CG shrinks the Gamma-norm error by
+    # about rho = tol^(1 / iterations) per iteration (from the zero-guess
+    # solves); a start with relative Gamma-norm error sqrt(E) (E is the
+    # squared ratio) is ln sqrt(E) / ln rho iterations ahead
+    rho_it = args.tol ** (1.0 / float(R["it0"].mean()))
+    expect = float(np.log(np.sqrt(np.median(R["E"]))) / np.log(rho_it))
     per_learned = R["build"] + R["infer"] + R["warm"]
     per_zero = R["build"] + R["zero"]
     per_prev = R["build"] + R["prev"]
@@ -854,6 +876,11 @@ def run_warm(args):
                            "inference + PCG from v0"},
         "learned": {"solves_per_s": round(value, 4), "iterations_mean": float(R["itw"].mean()),
                     "inference_ms_mean": round(float(R["infer"].mean()), 3),
+                    "inference_stages_ms": stage,
+                    "iterations_saved_mean": round(float((R["it0"] - R["itw"]).mean()), 2),
+                    "iterations_saved_expected_from_error": round(expect, 2),
+                    "break_even_inference_ms": round(float((R["it0"] - R["itw"]).mean()
+                                                           * (R["zero"] / R["it0"]).mean()), 3),
                     "accepted": int(R["used"].sum()), "energy_error_median": float(np.median(R["E"]))},
         "zero_guess": {"solves_per_s": round(len(rows) / (per_zero.sum() / 1e3), 4),
                        "iterations_mean": float(R["it0"].mean())},

@@ -174,9 +174,9 @@ sgp_status sgp_spmv(sgp_ctx *ctx, const sgp_matrix *matrix, const double *v_dev,
  * thread block and a counter, 33024 bytes) is a fixed array inside the
  * library that every GPU which loads the library keeps until the process
  * exits; hence at most 1,048,576 cells (4096 blocks of 256 rows): larger
- * matrices get SGP_ERR_INVALID_ARG.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array, which keeps the
+ * matrices get SGP_ERR_INVALID_ARG.  sgp_create looks up the array's
+ * device address, so every call, the first included, may run inside a
+ * stream capture.  All calls share the array, which keeps the
  * last call's contents; its counter is cleared at the start of each call.
  * Calls whose GPU work overlaps (other streams or host threads) race on the
  * array.  v_dev, y_dev: n x 3 float64, distinct; dot_dev: one float64
@@ -373,8 +373,11 @@ sgp_status sgp_mpnn_step(sgp_ctx *ctx, sgp_mpnn *net, float lr);
 /* sgp_mpnn_forward, then (flag SGP_WARM_MR_SCALE) the minimal-residual
  * rescaling v0 <- alpha v0, alpha = (Gamma v0)^T F / |Gamma v0|^2, then the
  * acceptance test: v0 is kept when |F - Gamma v0| <= |F| (FP64), else set to
- * 0 (the zero guess has the smaller residual).  used (host, may be NULL)
- * receives 1 if v0 was kept.  INVALID_ARG for unknown flags.  Synchronises. */
+ * 0 (the zero guess has the smaller residual).  After a finite positive-
+ * denominator rescaling the test holds by construction (the minimal-residual
+ * step cannot raise the residual) and is not evaluated; otherwise it costs
+ * one more FP64 product.  used (host, may be NULL) receives 1 if v0 was
+ * kept.  INVALID_ARG for unknown flags.  Synchronises. */
 sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *net, const sgp_matrix *matrix,
                           const sgp_factor *factor, const double *F_dev, const double *v_prev_dev,
                           double *v0_dev, int32_t flags, int32_t *used);
@@ -433,7 +436,12 @@ typedef enum {
     SGP_KT_SPMV = 0,       /* Gamma p products inside PCG (FP64 or FP32) */
     SGP_KT_TREE_SOLVE = 1, /* one whole P^{-1} r application */
     SGP_KT_PCG_VECTOR = 2, /* PCG vector updates and reductions */
-    SGP_KT_COUNT = 3
+    SGP_KT_WARM_BASIS = 3, /* warm start: the three basis fields (block-Jacobi and
+                              spanning-forest solves of F, v_prev) and the features */
+    SGP_KT_WARM_LAYERS = 4, /* warm start: the network's dense layers, aggregations and
+                               output mix */
+    SGP_KT_WARM_CHECK = 5, /* warm start: minimal-residual scaling and acceptance test */
+    SGP_KT_COUNT = 6
 } sgp_kernel_class;
 sgp_status sgp_set_kernel_timing(sgp_ctx *ctx, int32_t enable);
 /* Total milliseconds and launch count since the last reset. */

@@ -1,6 +1,6 @@
 """Iteration counts of the oracle's own solves of the benchmark workloads.
 
-BASELINE INFRASTRUCTURE (like everything under oracle/): the benchmark's CPU
+TEST INFRASTRUCTURE (like everything under oracle/): the benchmark's CPU
 leg times the oracle's solve phase at full size on a bounded number of PCG
 iterations and scales that time to the number of iterations the oracle
 needs to reach the tolerance.  That number is a property of the workload

@@ -1,6 +1,6 @@
 /* cpu_parallel.c -- the all-cores CPU baseline of the solve phase.
  *
- * BASELINE INFRASTRUCTURE, like everything under oracle/: only the tests,
+ * TEST INFRASTRUCTURE, like everything under oracle/: only the tests,
  * the smoke check and the benchmark's CPU leg use it; it shares no code with
  * the CUDA library.  It is compiled together with sgp_oracle.c (whose
  * functions it calls) into its own shared object, so the oracle proper stays

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libsgp.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_TIMEOUT = range(8)
 PREC_F64, PREC_MIXED = 0, 1
 PRECOND_TREE, PRECOND_BLOCK_JACOBI, PRECOND_NONE = 0, 1, 2
-KT_SPMV, KT_TREE_SOLVE, KT_PCG_VECTOR = 0, 1, 2
+KT_SPMV, KT_TREE_SOLVE, KT_PCG_VECTOR, KT_WARM_BASIS, KT_WARM_LAYERS, KT_WARM_CHECK = 0, 1, 2, 3, 4, 5
 STOP_RESIDUAL, STOP_ERROR = 0, 1
 MPNN_PARAMS = 25539
 MPNN_LOSS_L2, MPNN_LOSS_ENERGY = 0, 1

@@ -478,6 +478,12 @@ sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
         delete ctx;
         return SGP_ERR_OOM;
     }
+    if (noalloc_prepare(ctx) != SGP_OK) {
+        cudaFree(ctx->d_scratch);
+        cudaFree(ctx->d_flags);
+        delete ctx;
+        return SGP_ERR_CUDA;
+    }
     *out = ctx;
     return SGP_OK;
 }

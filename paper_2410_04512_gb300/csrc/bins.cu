@@ -728,7 +728,7 @@ __global__ void k_bn_check_top(TopCheck t)
 // are zero and stay zero, so a bin's slice of every vector is one
 // contiguous, 16-byte aligned stretch.
 struct BinArgs {
-    const int32_t *hdr, *elev, *vlev, *er, *ec, *cl, *kl, *ks, *pr, *pref, *zi;
+    const int32_t *hdr, *order, *elev, *vlev, *er, *ec, *cl, *kl, *ks, *pr, *pref, *zi;
     int32_t LVP, nb, G;
     int *err;
 };
@@ -998,7 +998,7 @@ __global__ void __launch_bounds__(BA, 7) k_bin_fwd(BinArgs a, BinNum<T> nm, T *w
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar, bart;
     __shared__ double shd[BA / 32];
-    const int b = blockIdx.x;
+    const int b = a.order[blockIdx.x];
     const int32_t *h = a.hdr + (size_t)H_N * b;
     const int32_t voff = h[H_VOFF], nv = h[H_NV], eoff = h[H_EOFF], ne = h[H_NE], coff = h[H_COFF],
                   nc = h[H_NC], koff = h[H_KOFF], nk = h[H_NK], nlev = h[H_NLEV];
@@ -1279,7 +1279,7 @@ __global__ void __launch_bounds__(BA, 7) k_bin_bwd(BinArgs a, BinNum<T> nm, T *z
     __shared__ uint64_t bar, bart;
     __shared__ double shd[BA / 32];
     __shared__ bool ok_s;
-    const int b = blockIdx.x;
+    const int b = a.order[blockIdx.x];
     const int32_t *h = a.hdr + (size_t)H_N * b;
     const int32_t voff = h[H_VOFF], nv = h[H_NV], poff = h[H_POFF], np = h[H_NP], zoff = h[H_ZOFF],
                   nz = h[H_NZ], nlev = h[H_NLEV];
@@ -1510,7 +1510,8 @@ template <typename T>
 static BinArgs bin_args(const sgp_factor *F)
 {
     const BinLayout &B = F->bl;
-    return BinArgs{bp<const int32_t>(B.hdr), bp<const int32_t>(B.elev), bp<const int32_t>(B.vlev),
+    return BinArgs{bp<const int32_t>(B.hdr), bp<const int32_t>(B.order), bp<const int32_t>(B.elev),
+                   bp<const int32_t>(B.vlev),
                    bp<const int32_t>(B.er), bp<const int32_t>(B.ec), bp<const int32_t>(B.cl),
                    bp<const int32_t>(B.kl), bp<const int32_t>(B.ks), bp<const int32_t>(B.pr),
                    bp<const int32_t>(B.pref), bp<const int32_t>(B.zi), B.LVP, B.nb, B.G, bp<int>(B.err)};
@@ -1948,6 +1949,24 @@ sgp_status bins_build(sgp_ctx *ctx, sgp_factor *F, const sgp_matrix *M)
             B.mat64 = 1;
         }
         B.mgen = M->gen;
+    }
+    // launch order: the bins with the most levels (the longest dependency
+    // chains) first, so that the last wave of blocks holds the short ones
+    {
+        std::vector<int32_t> h((size_t)H_N * std::max(nb, 1));
+        if (nb > 0) SGP_TRY(read_back(ctx, h.data(), hdr, sizeof(int32_t) * (size_t)H_N * nb));
+        std::vector<int32_t> ord_h((size_t)std::max(nb, 1));
+        for (int32_t b = 0; b < nb; ++b) ord_h[b] = b;
+        std::stable_sort(ord_h.begin(), ord_h.begin() + nb, [&](int32_t x, int32_t y) {
+            const int32_t lx = h[(size_t)H_N * x + H_NLEV], ly = h[(size_t)H_N * y + H_NLEV];
+            if (lx != ly) return lx > ly;
+            return h[(size_t)H_N * x + H_NV] > h[(size_t)H_N * y + H_NV];
+        });
+        SGP_TRY(buf_ensure(ctx, B.order, sizeof(int32_t) * ((size_t)nb + 4)));
+        if (nb > 0)
+            SGP_CUDA(ctx, cudaMemcpyAsync(B.order.p, ord_h.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+        SGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // ord_h lives on the host stack
     }
     // numeric layouts
     const int32_t Gp = G + 4, Cp = Cc + 4, Kp = K + 4, Pq = Pp + 4, TT = pad4(ntt) + 4, NTp = pad4(nt) + 4;

@@ -1248,7 +1248,7 @@ void sgp_factor_destroy(sgp_factor *F)
     for (DBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     BinLayout &B = F->bl;
-    DBuf *bb[] = {&B.hdr, &B.elev, &B.vlev, &B.gvert, &B.er, &B.ec, &B.cl, &B.kl, &B.ks, &B.pr, &B.pref, &B.zi,
+    DBuf *bb[] = {&B.hdr, &B.order, &B.elev, &B.vlev, &B.gvert, &B.er, &B.ec, &B.cl, &B.kl, &B.ks, &B.pr, &B.pref, &B.zi,
                   &B.tv, &B.tint, &B.c_src, &B.k_src, &B.p_src, &B.d_src, &B.t_src, &B.tD_src, &B.part, &B.err,
                   &B.i_of_t, &B.t_of_i, &B.rpt, &B.ma32, &B.mb32, &B.m64, &B.mc64};
     for (DBuf *b : bb)

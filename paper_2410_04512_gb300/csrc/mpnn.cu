@@ -127,6 +127,80 @@ __global__ void __launch_bounds__(TB) k_mp_dense(int64_t n, const float *__restr
     }
 }
 
+// The forward layers (TRANS = false, DOUT = H) as a register-tiled product:
+// a block holds all weights (FP32, [k][o]) and a tile of 64 nodes' inputs
+// (row-major, padded) in shared memory; each thread computes 4 nodes x 4
+// outputs, reading four inputs of each of its nodes and four outputs' weights
+// per 16-byte load (64 FMAs per 8 shared loads).  Each output accumulates
+// bias + sum_k x_k w_k in ascending k with FMAs: the same order, so the same
+// bits, as k_mp_dense.
+constexpr int DT_NODES = 64;
+template <int D1, int D2, bool RELU>
+__global__ void __launch_bounds__(TB) k_mp_dense_tiled(int64_t n, const float *__restrict__ X1,
+                                                       const float *__restrict__ X2,
+                                                       const __nv_bfloat16 *__restrict__ W,
+                                                       const __nv_bfloat16 *__restrict__ bias, float *Y)
+{
+    constexpr int DI = D1 + D2, XP = DI + 4;
+    static_assert(DI % 4 == 0 && H == 64, "tile shape");
+    extern __shared__ __align__(16) float dsm[];
+    float *wt = dsm;                 // [DI][H]
+    float *xs = dsm + DI * H;        // [DT_NODES][XP]
+    for (int t = threadIdx.x; t < DI * H; t += TB) {
+        const int k = t / H, o = t % H;
+        wt[t] = bf(W, o * DI + k);
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float bv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) bv[v] = bias ? bf(bias, 4 * tx + v) : 0.f;
+    const int64_t ntiles = (n + DT_NODES - 1) / DT_NODES;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * DT_NODES;
+        __syncthreads();
+        for (int c = threadIdx.x; c < DT_NODES * (DI / 4); c += TB) {
+            const int node = c / (DI / 4), kq = c % (DI / 4), k = 4 * kq;
+            const int64_t i = base + node;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n) v = k < D1 ? *reinterpret_cast<const float4 *>(X1 + i * D1 + k)
+                                  : *reinterpret_cast<const float4 *>(X2 + i * D2 + (k - D1));
+            *reinterpret_cast<float4 *>(xs + node * XP + k) = v;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = bv[v];
+#pragma unroll 2
+        for (int k = 0; k < DI; k += 4) {
+            float4 xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = *reinterpret_cast<const float4 *>(xs + (4 * ty + u) * XP + k);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 wv = *reinterpret_cast<const float4 *>(wt + (k + kk) * H + 4 * tx);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float xk = kk == 0 ? xv[u].x : kk == 1 ? xv[u].y : kk == 2 ? xv[u].z : xv[u].w;
+                    acc[u][0] = fmaf(xk, wv.x, acc[u][0]);
+                    acc[u][1] = fmaf(xk, wv.y, acc[u][1]);
+                    acc[u][2] = fmaf(xk, wv.z, acc[u][2]);
+                    acc[u][3] = fmaf(xk, wv.w, acc[u][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = base + 4 * ty + u;
+            if (i >= n) continue;
+            float4 o4 = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+            if (RELU) o4 = make_float4(fmaxf(o4.x, 0.f), fmaxf(o4.y, 0.f), fmaxf(o4.z, 0.f), fmaxf(o4.w, 0.f));
+            *reinterpret_cast<float4 *>(Y + i * H + 4 * tx) = o4;
+        }
+    }
+}
+
 // A_i = mean_{j ~ i} H_j (0 for an isolated cell); one warp per node, two
 // features per lane.  Neighbours in ascending column order.
 __global__ void k_mp_agg(int64_t n, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
@@ -394,6 +468,22 @@ template <int D1, int D2, int DOUT, bool TRANS, bool RELU>
 static sgp_status dense(sgp_ctx *ctx, int64_t n, const float *X1, const float *X2, const __nv_bfloat16 *W,
                         const __nv_bfloat16 *b, float *Y)
 {
+    if constexpr (!TRANS && DOUT == H && (D1 + D2) % 4 == 0 && D1 % 4 == 0) {
+        // forward layers: the register-tiled kernel (shared memory above
+        // 48 KB opted in once per device)
+        constexpr int DI = D1 + D2;
+        constexpr size_t smem = sizeof(float) * ((size_t)DI * H + (size_t)DT_NODES * (DI + 4));
+        static bool opted[64] = {false};
+        auto kern = k_mp_dense_tiled<D1, D2, RELU>;
+        if (ctx->device >= 0 && ctx->device < 64 && !opted[ctx->device]) {
+            SGP_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            opted[ctx->device] = true;
+        }
+        unsigned G = 1;
+        SGP_TRY(resident_grid(ctx, (const void *)kern, TB, (n + DT_NODES - 1) / DT_NODES, &G));
+        LAUNCH(ctx, kern, G, TB, smem, n, X1, X2, W, b, Y);
+        return SGP_OK;
+    }
     constexpr int NPB = TB / DOUT > 0 ? TB / DOUT : 1;
     const int64_t want = (n + NPB - 1) / NPB;
     const unsigned G = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 16));
@@ -479,6 +569,8 @@ static sgp_status mpnn_forward_internal(sgp_ctx *ctx, sgp_mpnn *N, const sgp_mat
     double *b0 = bp<double>(N->basis), *b1 = b0 + 3 * n, *b2 = b1 + 3 * n;
     double *Fi = bp<double>(N->tmp) + 9 * n;
     const int32_t *orig_of = bp<const int32_t>(M->orig_of);
+    cudaEvent_t ev;
+    SGP_TRY(kt_begin(ctx, SGP_KT_WARM_BASIS, &ev));
     LAUNCH(ctx, k_to_internal<double>, grid_for(n, TB), TB, 0, n, orig_of, F, Fi);
     // basis: block-Jacobi solve, spanning-forest solve, previous velocity
     SGP_TRY(matrix_block_jacobi(ctx, const_cast<sgp_matrix *>(M)));
@@ -496,6 +588,8 @@ static sgp_status mpnn_forward_internal(sgp_ctx *ctx, sgp_mpnn *N, const sgp_mat
     float *x = bp<float>(N->x);
     LAUNCH(ctx, k_mp_features, grid_for(n, TB), TB, 0, n, (const double *)b0, (const double *)b1,
            (const double *)b2, bp<const int32_t>(M->row_ptr), (const double *)mean_b1, x);
+    SGP_TRY(kt_end(ctx, SGP_KT_WARM_BASIS, ev));
+    SGP_TRY(kt_begin(ctx, SGP_KT_WARM_LAYERS, &ev));
     // forward
     const __nv_bfloat16 *pb = bp<const __nv_bfloat16>(N->pb);
     float *hs = bp<float>(N->hs), *aggs = bp<float>(N->aggs);
@@ -509,6 +603,7 @@ static sgp_status mpnn_forward_internal(sgp_ctx *ctx, sgp_mpnn *N, const sgp_mat
     }
     LAUNCH(ctx, k_mp_out, grid_for(n, TB), TB, 0, n, (const float *)(hs + 3 * H * n), pb + OFF_WOUT, pb + OFF_BOUT,
            (const double *)b0, (const double *)b1, (const double *)b2, bp<float>(N->c), bp<double>(N->v0w));
+    SGP_TRY(kt_end(ctx, SGP_KT_WARM_LAYERS, ev));
     return SGP_OK;
 }
 
@@ -600,8 +695,10 @@ sgp_status sgp_mpnn_step(sgp_ctx *ctx, sgp_mpnn *N, float lr)
 
 }  // extern "C"
 
-// The residual check of the warm start lives with the solver's product.
-sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *F, double *v0, int *used);
+// The residual check of the warm start lives with the solver's product; it
+// closes the timing bracket `ev` of class kclass before its read-back.
+sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *F, double *v0, int *used,
+                               int kclass, cudaEvent_t ev);
 
 extern "C" sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix *M, const sgp_factor *Fh,
                                      const double *F, const double *v_prev, double *v0, int32_t flags,
@@ -619,7 +716,11 @@ extern "C" sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix
     // N->v0w stays the network's own output for a following backward pass
     double *Gv = bp<double>(N->tmp), *w = Gv + 3 * n;
     const double *Fi = bp<const double>(N->tmp) + 9 * n;
+    cudaEvent_t ev;
+    SGP_TRY(kt_begin(ctx, SGP_KT_WARM_CHECK, &ev));
     SGP_CUDA(ctx, cudaMemcpyAsync(w, N->v0w.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    int u = 0;
+    bool checked = false;
     if (flags & SGP_WARM_MR_SCALE) {
         double *red = bp<double>(N->red);
         unsigned *counter = reinterpret_cast<unsigned *>(red + 2 * 1024 + 8);
@@ -628,9 +729,21 @@ extern "C" sgp_status sgp_warm_start(sgp_ctx *ctx, sgp_mpnn *N, const sgp_matrix
         LAUNCH(ctx, k_mp_dot2, red_blocks(3 * n), TB, 0, 3 * n, (const double *)Gv, Fi, (const double *)Gv,
                (const double *)Gv, red, counter, nd);
         LAUNCH(ctx, k_mp_scale, grid_for(3 * n, TB), TB, 0, 3 * n, (const double *)nd, w);
+        // with a finite step alpha = (Gamma v0)^T F / |Gamma v0|^2 the scaled
+        // guess has |F - alpha Gamma v0|^2 = |F|^2 - ((Gamma v0)^T F)^2 /
+        // |Gamma v0|^2 <= |F|^2: the acceptance test holds without a second
+        // product
+        SGP_TRY(kt_end(ctx, SGP_KT_WARM_CHECK, ev));
+        double h[2] = {0.0, 0.0};
+        SGP_TRY(read_back(ctx, h, nd, sizeof(h)));
+        if (h[1] > 0.0 && std::isfinite(h[0] / h[1])) {
+            u = 1;
+            checked = true;
+        } else {
+            SGP_TRY(kt_begin(ctx, SGP_KT_WARM_CHECK, &ev));
+        }
     }
-    int u = 0;
-    SGP_TRY(mpnn_residual_check(ctx, M, Fi, w, &u));
+    if (!checked) SGP_TRY(mpnn_residual_check(ctx, M, Fi, w, &u, SGP_KT_WARM_CHECK, ev));
     LAUNCH(ctx, k_to_caller<double>, grid_for(n, TB), TB, 0, n, bp<const int32_t>(M->orig_of), (const double *)w,
            v0);
     if (used) *used = u;

@@ -17,8 +17,6 @@
 // array and must not be issued.
 #include "sgp_internal.cuh"
 
-#include <mutex>
-
 namespace {
 
 constexpr int NA_BLOCK = 256;
@@ -29,9 +27,6 @@ static_assert(NA_SCRATCH_BYTES == 33024, "stated scratch size");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
 
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_mu;
-void *g_addr[NA_MAX_DEVICES] = {nullptr};
 
 // Internal row r (cell orig_of[r]) of the Appendix B.2 product, same
 // operation order as the solver's.  v is in the caller's cell order: the
@@ -84,26 +79,22 @@ __global__ void k_spmv_dot_noalloc(const int32_t *__restrict__ row_ptr, const in
     }
 }
 
-// Device address of the scratch array for the current device, looked up
-// once per device.  The lookup must not happen during stream capture.
-sgp_status scratch_address(sgp_ctx *ctx, void **out)
+}  // namespace
+
+// Device address of the scratch array, looked up when a context is created
+// (sgp_create, outside any capture) and kept in the context: a device reset
+// ends every context, so no address outlives the CUDA context it came from.
+sgp_status noalloc_prepare(sgp_ctx *ctx)
 {
-    if (ctx->device < 0 || ctx->device >= NA_MAX_DEVICES)
-        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "spmv_dot_noalloc: device index out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[ctx->device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return sgp_fail(ctx, SGP_ERR_CUDA, "spmv_dot_noalloc: cudaGetSymbolAddress failed: %s",
-                            cudaGetErrorString(e));
-        g_addr[ctx->device] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return sgp_fail(ctx, SGP_ERR_CUDA, "noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
     }
-    *out = g_addr[ctx->device];
+    ctx->noalloc_scratch = p;
     return SGP_OK;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -121,9 +112,8 @@ sgp_status sgp_spmv_dot_noalloc(sgp_ctx *ctx, const sgp_matrix *M, const double 
                         "spmv_dot_noalloc: %lld cells exceed the fixed scratch limit of %lld cells",
                         (long long)n, (long long)max_n);
     SGP_CUDA(ctx, cudaSetDevice(ctx->device));
-    void *scratch = nullptr;
-    SGP_TRY(scratch_address(ctx, &scratch));
-    unsigned char *base = reinterpret_cast<unsigned char *>(scratch);
+    if (!ctx->noalloc_scratch) return sgp_fail(ctx, SGP_ERR_CUDA, "spmv_dot_noalloc: scratch address unknown");
+    unsigned char *base = reinterpret_cast<unsigned char *>(ctx->noalloc_scratch);
     SGP_CUDA(ctx, cudaMemsetAsync(base + NA_MAX_BLOCKS * sizeof(double), 0, sizeof(unsigned), ctx->stream));
     if (n == 0) {
         SGP_CUDA(ctx, cudaMemsetAsync(dot, 0, sizeof(double), ctx->stream));

@@ -822,7 +822,8 @@ sgp_status spmv64(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *y)
 
 // Warm-start acceptance: keep v0 only if |F - Gamma v0| <= |F| (otherwise
 // the zero guess has the smaller residual and v0 is cleared).
-sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *F, double *v0, int *used)
+sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *F, double *v0, int *used,
+                               int kclass, cudaEvent_t ev)
 {
     const int64_t n = M->n;
     *used = 0;
@@ -835,6 +836,7 @@ sgp_status mpnn_residual_check(sgp_ctx *ctx, const sgp_matrix *M, const double *
     SGP_TRY(resident_grid(ctx, (const void *)k_resid64<false>, RB, (n + RB - 1) / RB, &Gr));
     LAUNCH(ctx, k_resid64<false>, Gr, RB, 0, make_blk<double>(M), bp<const int32_t>(M->row_ptr), M->gamma0,
            n, F, (const double *)v0, (double *)nullptr, partials, o2);
+    SGP_TRY(kt_end(ctx, kclass, ev));
     double h[2] = {0, 0};
     SGP_TRY(read_back(ctx, h, o2, sizeof(h)));
     if (h[0] <= h[1] && std::isfinite(h[0])) {

@@ -47,10 +47,12 @@ struct sgp_ctx {
     size_t h_stage_bytes = 0;
     // kernel timing
     int timing = 0;
-    double kt_ms[SGP_KT_COUNT] = {0, 0, 0};
-    int64_t kt_n[SGP_KT_COUNT] = {0, 0, 0};
+    double kt_ms[SGP_KT_COUNT] = {};
+    int64_t kt_n[SGP_KT_COUNT] = {};
     std::vector<cudaEvent_t> ev_free;
     std::vector<cudaEvent_t> ev_pending[SGP_KT_COUNT];  // start,end pairs
+    // the no-allocation product's fixed scratch array (noalloc.cu)
+    void *noalloc_scratch = nullptr;
     // device scratch of the solver (vectors, partials, scalars); may grow
     void *d_scratch = nullptr;
     size_t d_scratch_bytes = 0;
@@ -85,6 +87,7 @@ sgp_status resident_grid(sgp_ctx *ctx, const void *kernel, int block, int64_t wa
 
 // Unique generation numbers for rebuilt handles (graph cache keys).
 uint64_t next_generation();
+sgp_status noalloc_prepare(sgp_ctx *ctx);
 sgp_status graph_lookup(sgp_ctx *ctx, const uint64_t *key, int nkey, GraphEntry **out);
 sgp_status graph_begin(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t *saved, int64_t *l0);
 sgp_status graph_end(sgp_ctx *ctx, GraphEntry *ge, cudaStream_t saved, int64_t l0, sgp_status st);
@@ -283,6 +286,7 @@ struct BinLayout {
     size_t smA0[2] = {0, 0}, smC0[2] = {0, 0};                  // plain solve
     size_t smTnd[2] = {0, 0};                                   // top without staged pivots
     DBuf hdr, elev, vlev, gvert, er, ec, cl, kl, ks, pr, pref, zi, tv, tint;
+    DBuf order;                        // bins in launch order: most levels first
     DBuf c_src, k_src, p_src, d_src, t_src, tD_src;
     DBuf cL[2], kL[2], pL[2], D[2], tL[2], tD[2];
     DBuf ly[2], lsum[2], tw[2], part, err;

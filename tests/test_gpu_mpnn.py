@@ -138,6 +138,10 @@ def test_gradients_match_oracle(ctx, case, energy):
                 best, flips = e, trial
     assert abs(L - L_or) <= 1e-5 * abs(L_or)
     assert best <= 1e-3, (best, len(amb), len(flips))
+    # flips stay the exception: a handful of units at a kink, not a drift of
+    # the FP32 forward pass (run with -s to see the counts)
+    print("relu units within rounding of a kink: %d; flipped to match: %d" % (len(amb), len(flips)))
+    assert len(flips) <= max(4, len(amb) // 10), (len(amb), len(flips))
 
 
 def test_backward_is_bitwise_reproducible(ctx, case):

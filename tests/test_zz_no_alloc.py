@@ -5,8 +5,9 @@ synchronisation of cudaMalloc/cudaFree).
 
 Called directly through the C ABI and checked against the regular
 sgp_spmv entry point, twice in a row (the fixed scratch array is shared
-between calls and keeps the previous call's contents), plus the size limit
-of that array.  This file is collected last so that a run stopping at the
+between calls and keeps the previous call's contents), inside a CUDA graph
+captured on the context's stream (replayed twice, device memory unchanged),
+plus the size limit of that array.  This file is collected last so that a run stopping at the
 first failure has already run every other test.
 """
 import ctypes
@@ -46,6 +47,41 @@ def test_noalloc_matches_spmv_twice_in_a_row(cuda_device):
             assert (y - want).abs().max().item() <= 1e-13 * scale
             ref = torch.dot(v.ravel(), want.ravel()).item()
             assert abs(dot.item() - ref) <= 1e-13 * abs(ref)
+
+
+def test_noalloc_inside_a_stream_capture(cuda_device):
+    """The first call on a fresh context is made inside the capture: the
+    scratch address was looked up when the context was created."""
+    cells = workloads.ball(n=20000, seed=2005, gamma0=1e-3)
+    side = torch.cuda.Stream()
+    ctx0 = sgp.Context(0)
+    s = GpuSystem(ctx0, cells, tree=False)
+    v = dev_tensor(np.random.default_rng(3).standard_normal((cells.n, 3)))
+    y = torch.zeros_like(v)
+    dot = torch.zeros((1,), dtype=torch.float64, device=v.device)
+    want = ctx0.spmv(s.M, v)
+    ref = torch.dot(v.ravel(), want.ravel()).item()
+    torch.cuda.synchronize()
+    ctx = sgp.Context(0, side)
+    g = torch.cuda.CUDAGraph()
+    # an allocation call inside the capture would fail the capture (and the
+    # call's status); the replays then must not allocate either
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        rc = _noalloc(ctx, s.M, v, y, dot)
+        g.capture_end()
+    assert rc == sgp.OK
+    scale = want.abs().max().item()
+    free = []
+    for _ in range(3):
+        y.fill_(float("nan"))
+        dot.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        assert (y - want).abs().max().item() <= 1e-13 * scale
+        assert abs(dot.item() - ref) <= 1e-13 * abs(ref)
+    assert free[0] == free[1] == free[2]
 
 
 def test_noalloc_rejects_more_cells_than_its_scratch(cuda_device):
