@@ -212,6 +212,8 @@ def outer_bytes(n: int, m: int) -> int:
 # capture, one launch each (profiles/dram_fused_step_ball1m.md): the tree
 # step is its four launches (k_bin_fwd 87.77 MB, k_leaksum 0.17 MB, k_top
 # 0.22 MB, k_bin_bwd 107.91 MB); other workloads and forms report null.
+FP64_TFLOPS = 1.25   # FP64 FMA rate of the GB300 (no FP64 tensor path is used)
+
 MEASURED_TRAFFIC = {
     ("ball1m", "mixed", "tree"): {"spmv": 140545792, "tree": 196073984, "vector": 36145920},
 }
@@ -391,6 +393,20 @@ def run_gpu(args):
         its = max(int(kres["iters_total"]), 1)   # iterations of every timed step
         out = {"spmv": roof(label + "k_spmv_pq<%s>" % tn, spmv_bytes(n, mm, fpx), spmv_ms, spmv_n,
                             "one product Gamma p + p^T q over all rows", traffic.get("spmv"))}
+        if fpx == 8:
+            # FP64 is issue-bound on this GPU: the product against the FP64
+            # rate too (per slot 9 FMA + 3 subtractions, per row 3 FMA for
+            # gamma0 and 3 for p^T q)
+            flops = 2 * mm * (2 * 9 + 3) + n * (2 * 3 + 2 * 3)
+            avg_s = (spmv_ms / max(spmv_n, 1)) / 1e3
+            tf = flops / avg_s / 1e12 if avg_s > 0 else 0.0
+            out["spmv_alu"] = {"kernel": label + "k_spmv_pq<double> (FP64 arithmetic)", "bound": "alu",
+                               "achieved": round(tf, 4), "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                               "frac": round(tf / FP64_TFLOPS, 4), "traffic": None,
+                               "peak_source": "nominal FP64 rate (152 SMs x 2 FMA/clock x 2070 MHz; an FMA loop "
+                                              "measured 1.20 TFLOP/s)",
+                               "algorithmic_flops_per_launch": int(flops), "avg_launch_us": round(avg_s * 1e6, 2),
+                               "launches": spmv_n}
         it_bytes = spmv_bytes(n, mm, fpx)
         if form.precond == sgp.PRECOND_TREE:
             _, levels, npairs, nrecv = H["Fh"].stats()
@@ -506,7 +522,8 @@ def other_configs(args):
             ("hex4m", ["--workload", "hex4m", "--steps", "2", "--compare", "1"]),
             ("batch512", ["--workload", "batch512", "--steps", "2"]),
             ("warm200k", ["--workload", "warm200k"]),
-            ("aug1m", ["--workload", "aug1m", "--steps", "2"])]
+            ("aug1m", ["--workload", "aug1m", "--steps", "2"]),
+            ("paper", ["--workload", "paper", "--paper-reps", "3"])]
     out = {}
     for name, extra in runs:
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "3", "--autotune", "0",
@@ -529,7 +546,7 @@ def other_configs(args):
                                     "latency_ms", "looped_plain_fp64", "looped_mixed", "learned", "zero_guess",
                                     "previous_v", "solve_only_ms_mean", "tree_layout", "clocks", "augmented",
                                     "plain_fp64", "outer_vs_plain_iterations", "augmented_sweep",
-                                    "error_bound_stopping")
+                                    "error_bound_stopping", "paper_workloads", "hex_scaling")
                 if k in rec}
         keep["workload"] = rec.get("config", {}).get("workload")
         if "roofline" in rec:
@@ -748,6 +765,157 @@ def run_augmented(args):
         "outer_vs_plain_iterations": round(ia.outer_iterations / max(ip.iterations, 1), 3),
         "augmented_sweep": sweep,
         "error_bound_stopping": estop,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_paper(args):
+    """The paper's own experiments re-created (Section 5): noisy hexagonal
+    close packing at gamma_med 3e4 and 3e3, a rejection-sampled spheroid and
+    a dumbbell, n = 50,000 equal cells with Hertz contact areas, a known
+    solution x* (F = Gamma x*), tolerance 1e-5; iterations of no
+    preconditioner, block Jacobi, the spanning forest and the augmented
+    forest (flexible CG), averaged over independent realizations, and their
+    ratios next to the ones the paper prints.  Three stopping readings:
+    the true relative error |x_k - x*| <= 1e-5 |x*| (the count found by runs
+    of fixed length), the Gauss-Radau bound of the Gamma-norm error, and the
+    relative residual.  Also the hexagonal lattice from 1e2 to 1e5 cells:
+    wall clock of assembly, preconditioner construction and factorization
+    and CG, the forest against no preconditioner.  FP64."""
+    import torch
+
+    import paper_2410_04512_gb300 as sgp
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgp.Context(0, stream)
+    reps = args.paper_reps
+    n = args.paper_n
+    tol = 1e-5
+    paper_ratio = {"hex": {"none_over_tree": 4.9, "none_over_jacobi": 1.2},
+                   "hex_high_kappa": {"none_over_tree": 9.2},
+                   "random": {"none_over_tree": 3.8}, "dumbbell": {"none_over_tree": 8.5}}
+    makers = {"hex": lambda s: workloads.paper_hex(n=n, seed=6000 + s),
+              "hex_high_kappa": lambda s: workloads.paper_hex(n=n, seed=6100 + s, gamma_med=3.0e3),
+              "random": lambda s: workloads.paper_random(n=n, seed=7000 + s),
+              "dumbbell": lambda s: workloads.paper_dumbbell(n=n, seed=8000 + s)}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def system(c):
+        pos = torch.from_numpy(c.pos).to(dev)
+        radii = torch.from_numpy(c.radii).to(dev)
+        g = ctx.collision_graph(pos, radii)
+        ij = g.edges()
+        gp, gq = c.gammas_torch(ij, pos, radii)
+        M = ctx.friction_assemble(g, pos, gp.contiguous(), gq.contiguous(), c.gamma0, sgp.PREC_F64)
+        T = ctx.max_spanning_tree(M)
+        Fh = ctx.tree_factor(M, T)
+        return pos, radii, g, M, T, Fh
+
+    def rel(v, xs):
+        return float(torch.linalg.norm(v - xs) / torch.linalg.norm(xs))
+
+    def to_true_error(M, Fh, F, xs, pc, start):
+        """Fewest iterations whose iterate has |x_k - x*| <= tol |x*|: runs of
+        a fixed count (maxit, no other stop) doubled, then bisected."""
+        def err(k):
+            v, _ = ctx.pcg_solve(M, Fh, F, tol=1e-300, maxit=k, precond=pc, raise_on_error=False)
+            return rel(v, xs)
+        lo, hi = 0, max(1, start)
+        while err(hi) > tol:
+            lo, hi = hi, 2 * hi
+            if hi > 200_000:
+                return -1
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            lo, hi = (lo, mid) if err(mid) <= tol else (mid, hi)
+        return hi
+
+    out = {}
+    for name, make in makers.items():
+        rows = []
+        for rep in range(reps):
+            c = make(rep)
+            pos, radii, g, M, T, Fh = system(c)
+            xs = torch.from_numpy(np.random.Generator(np.random.PCG64([9100, rep])).standard_normal((c.n, 3))).to(dev)
+            F = ctx.spmv(M, xs)
+            row = {}
+            for label, kw in (("none", dict(precond=sgp.PRECOND_NONE)),
+                              ("jacobi", dict(precond=sgp.PRECOND_BLOCK_JACOBI)),
+                              ("tree", dict(precond=sgp.PRECOND_TREE)),
+                              ("tree_error_bound", dict(precond=sgp.PRECOND_TREE, stop=sgp.STOP_ERROR)),
+                              ("none_error_bound", dict(precond=sgp.PRECOND_NONE, stop=sgp.STOP_ERROR))):
+                a, b = ev(), ev()
+                a.record(stream)
+                v, info = ctx.pcg_solve(M, Fh, F, tol=tol, **kw)
+                b.record(stream)
+                b.synchronize()
+                row[label] = (info.iterations, a.elapsed_time(b), rel(v, xs))
+            for label, pc in (("none", sgp.PRECOND_NONE), ("jacobi", sgp.PRECOND_BLOCK_JACOBI),
+                              ("tree", sgp.PRECOND_TREE)):
+                row[label + "_to_true_error"] = (to_true_error(M, Fh, F, xs, pc, row[label][0]), 0.0, tol)
+            A = ctx.augment_tree(M, T, 0)
+            a, b = ev(), ev()
+            a.record(stream)
+            v, info = ctx.fcg_solve(M, A, Fh, F, tol=tol, inner_tol=0.1)
+            b.record(stream)
+            b.synchronize()
+            row["augmented"] = (info.outer_iterations, a.elapsed_time(b), rel(v, xs))
+            rows.append(row)
+        mean = {k: float(np.mean([r[k][0] for r in rows])) for k in rows[0]}
+        out[name] = {"iterations_mean": {k: round(v, 1) for k, v in mean.items()},
+                     "solve_ms_mean": {k: round(float(np.mean([r[k][1] for r in rows])), 3) for k in rows[0]
+                                       if not k.endswith("_to_true_error")},
+                     "true_rel_error_max": {k: float(np.max([r[k][2] for r in rows])) for k in rows[0]
+                                            if not k.endswith("_to_true_error")},
+                     "none_over_tree_true_error": round(mean["none_to_true_error"] / mean["tree_to_true_error"], 2),
+                     "none_over_jacobi_true_error": round(mean["none_to_true_error"] /
+                                                          mean["jacobi_to_true_error"], 2),
+                     "none_over_tree_residual": round(mean["none"] / mean["tree"], 2),
+                     "none_over_tree_error_bound": round(mean["none_error_bound"] / mean["tree_error_bound"], 2),
+                     "tree_over_augmented": round(mean["tree"] / mean["augmented"], 3),
+                     "paper": paper_ratio[name], "cells": n, "realizations": reps}
+    # wall-clock scaling on the hexagonal lattice: what the paper's scaling
+    # figure times (assembly, preconditioner construction and factorization,
+    # CG), with the contact graph and the Hertz coefficients given
+    scaling = []
+    for ns in (100, 1000, 10_000, 100_000):
+        c = workloads.paper_hex(n=ns, seed=6200)
+        pos = torch.from_numpy(c.pos).to(dev)
+        radii = torch.from_numpy(c.radii).to(dev)
+        g = ctx.collision_graph(pos, radii)
+        gp, gq = (t.contiguous() for t in c.gammas_torch(g.edges(), pos, radii))
+        xs = torch.from_numpy(np.random.Generator(np.random.PCG64([9200, ns])).standard_normal((ns, 3))).to(dev)
+        F = ctx.spmv(ctx.friction_assemble(g, pos, gp, gq, c.gamma0, sgp.PREC_F64), xs)
+        entry = {"cells": ns}
+        for pname, prec in (("f64", sgp.PREC_F64), ("mixed", sgp.PREC_MIXED)):
+            res = {}
+            for label, pc in (("tree", sgp.PRECOND_TREE), ("none", sgp.PRECOND_NONE),
+                              ("jacobi", sgp.PRECOND_BLOCK_JACOBI)):
+                times = []
+                for rep in range(4):
+                    a, b = ev(), ev()
+                    a.record(stream)
+                    M = ctx.friction_assemble(g, pos, gp, gq, c.gamma0, prec)
+                    Fh = ctx.tree_factor(M, ctx.max_spanning_tree(M)) if pc == sgp.PRECOND_TREE else None
+                    v, info = ctx.pcg_solve(M, Fh, F, tol=tol, precond=pc, precision=prec)
+                    b.record(stream)
+                    b.synchronize()
+                    times.append(a.elapsed_time(b))
+                res[label] = {"step_ms": round(float(np.median(times[1:])), 3), "iterations": info.iterations,
+                              "true_rel_error": float(torch.linalg.norm(v - xs) / torch.linalg.norm(xs))}
+            res["none_over_tree_time"] = round(res["none"]["step_ms"] / res["tree"]["step_ms"], 2)
+            entry[pname] = res
+        scaling.append(entry)
+    line = {
+        "metric": METRIC, "value": None, "unit": "iterations", "n_gpus": 1, "steps": reps, "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "the paper's Section 5 geometries re-created: noisy hexagonal close packing "
+                               "(spacing 2r, noise N(0,(0.3 r)^2)), rejection-sampled spheroid and dumbbell "
+                               "(minimum distance 0.7, density 1.6), r = 0.5, Hertz contact areas, gamma_par 2e6, "
+                               "gamma_perp 8e7, gamma_med 3e4 (3e3 for high kappa), known solution, tol 1e-5",
+                   "cells": n},
+        "paper_workloads": out, "hex_scaling": scaling,
     }
     print(json.dumps(line), flush=True)
 
@@ -1046,7 +1214,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgp", choices=["sgp", "reference"])
-    ap.add_argument("--workload", default="ball1m", choices=sorted(WORKLOADS) + ["batch512", "warm200k", "aug1m"])
+    ap.add_argument("--workload", default="ball1m",
+                    choices=sorted(WORKLOADS) + ["batch512", "warm200k", "aug1m", "paper"])
+    ap.add_argument("--paper-reps", dest="paper_reps", type=int, default=5,
+                    help="paper: independent realizations per geometry")
+    ap.add_argument("--paper-n", dest="paper_n", type=int, default=50_000, help="paper: cells per geometry")
     ap.add_argument("--aug-t", dest="aug_t", type=int, default=0,
                     help="aug1m: pieces of the augmented forest (0: round(n^(1/4)))")
     ap.add_argument("--aug-delta", dest="aug_delta", type=float, default=0.1,
@@ -1077,6 +1249,8 @@ def main():
         run_warm(args)
     elif args.workload == "aug1m":
         run_augmented(args)
+    elif args.workload == "paper":
+        run_paper(args)
     else:
         run_gpu(args)
 

@@ -30,8 +30,7 @@ class GpuSystem:
         self.radii = dev_tensor(cells.radii)
         self.graph = ctx.collision_graph(self.pos, self.radii)
         self.ij = self.graph.edges()
-        tp, tq = cells.tables()
-        self.gp, self.gq = workloads.pair_gamma_torch(cells.seed, self.ij, dev_tensor(tp), dev_tensor(tq))
+        self.gp, self.gq = cells.gammas_torch(self.ij, self.pos, self.radii)
         self.M = ctx.friction_assemble(self.graph, self.pos, self.gp.contiguous(), self.gq.contiguous(),
                                        cells.gamma0, precision)
         self.T = self.Fac = None

@@ -13,6 +13,12 @@ Input laws (the paper's cell model, Section 2 Steps 1-4 and eq. (1)):
 * ``hex_sheet``  a monolayer: centres on a jittered hexagonal lattice in the
              z = 0 plane (jitter U[-j, j] on all three coordinates).
 * ``batch``  many independent balls of log-uniform size.
+* ``paper_hex``, ``paper_random``, ``paper_dumbbell``  the geometries of the
+             paper's experiments (Section 5): equal cells r = 0.5 on a noisy
+             hexagonal close packing, a rejection-sampled spheroid, and two
+             lobes joined by a thin bridge; their coefficients follow the
+             Hertz contact area (``hertz_gamma_np``) times the paper's
+             gamma_par = 2e6 and gamma_perp = 8e7.
 
 Per-contact friction coefficients gamma_par and gamma_perp (eq. (1)) are
 drawn log-uniformly per unordered pair {i, j} by a counter-based generator:
@@ -143,6 +149,13 @@ class Cells:
     def gammas_np(self, ij: np.ndarray):
         tp, tq = self.tables()
         return pair_gamma_np(self.seed, ij[:, 0], ij[:, 1], tp, tq)
+
+    def gammas_torch(self, ij, pos=None, radii=None):
+        """The same coefficients for an (m, 2) torch tensor of pairs (on the
+        pairs' device); pos and radii are the law's inputs where it has any."""
+        import torch
+        tp, tq = (torch.from_numpy(t).to(ij.device) for t in self.tables())
+        return pair_gamma_torch(self.seed, ij, tp, tq)
 
     def forces(self, k: int = 0) -> np.ndarray:
         """F ~ N(0, 1) per component; ``k`` selects an independent draw."""
@@ -315,3 +328,164 @@ def spheroid_200k(seed: int = 5000) -> Cells:
     """The learned-warm-start workload's spheroid: 200,000 cells in a ball at
     packing fraction 0.6 (radius 34.78), gamma in [0.1, 10], gamma0 = 1e-3."""
     return ball(n=200_000, seed=seed, gamma0=1e-3)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own experiment geometries (Section 5, Experimental Setup):
+# equal cells of radius r = 0.5, Hertz contact areas, gamma_par = 2e6,
+# gamma_perp = 8e7 per unit area, cell-substrate friction gamma_med I
+# ---------------------------------------------------------------------------
+PAPER_R = 0.5
+PAPER_G_PAR, PAPER_G_PERP = 2.0e6, 8.0e7
+
+
+def hertz_gamma_np(pos: np.ndarray, radii: np.ndarray, ij: np.ndarray, g_par: float, g_perp: float):
+    """Per-contact coefficients A_ij g_par and A_ij g_perp with the Hertz
+    contact area A_ij = pi R* delta (contact radius sqrt(R* delta)), R* =
+    R_i R_j / (R_i + R_j), delta = R_i + R_j - |r_j - r_i| the overlap.
+    Every operation in a fixed order (the torch twin repeats it)."""
+    ij = np.asarray(ij, dtype=np.int64)
+    a, b = ij[:, 0], ij[:, 1]
+    d0 = pos[b, 0] - pos[a, 0]
+    d1 = pos[b, 1] - pos[a, 1]
+    d2 = pos[b, 2] - pos[a, 2]
+    dist = np.sqrt(d0 * d0 + d1 * d1 + d2 * d2)
+    s = radii[a] + radii[b]
+    area = (math.pi * ((radii[a] * radii[b]) / s)) * (s - dist)
+    return area * g_par, area * g_perp
+
+
+def hertz_gamma_torch(pos, radii, ij, g_par: float, g_perp: float):
+    """``hertz_gamma_np`` for torch tensors: evaluated on the host and copied
+    to the pairs' device, so both sides hold the same bits (the square root
+    of torch's CPU kernels is not always the correctly rounded one)."""
+    import torch
+    gp, gq = hertz_gamma_np(pos.detach().cpu().numpy(), radii.detach().cpu().numpy(),
+                            ij.detach().cpu().numpy(), g_par, g_perp)
+    return torch.from_numpy(gp).to(ij.device), torch.from_numpy(gq).to(ij.device)
+
+
+class HertzCells(Cells):
+    """A configuration whose per-contact coefficients follow the Hertz law."""
+
+    def gammas_np(self, ij: np.ndarray):
+        return hertz_gamma_np(self.pos, self.radii, ij, self.meta["g_par"], self.meta["g_perp"])
+
+    def gammas_torch(self, ij, pos, radii):
+        return hertz_gamma_torch(pos, radii, ij, self.meta["g_par"], self.meta["g_perp"])
+
+
+def _paper_cells(name, pos, seed, gamma_med, meta):
+    n = pos.shape[0]
+    meta = dict(meta, g_par=PAPER_G_PAR, g_perp=PAPER_G_PERP)
+    return HertzCells(name, np.ascontiguousarray(pos), np.full(n, PAPER_R), seed, 0.0, 0.0, gamma_med, meta)
+
+
+def _nearest_to_centre(pts: np.ndarray, n: int) -> np.ndarray:
+    c = pts.mean(axis=0)
+    d2 = np.sum((pts - c) ** 2, axis=1)
+    order = np.lexsort((np.arange(pts.shape[0]), d2))   # distance, then index
+    return pts[np.sort(order[:n])]
+
+
+def paper_hex(n: int = 50_000, spacing: float = 2 * PAPER_R, noise: float = 0.3, seed: int = 6000,
+              gamma_med: float = 3.0e4) -> HertzCells:
+    """Hexagonal close packing (ABAB stacking of hexagonal layers, 12
+    neighbours at distance ``spacing``, by default 2r: the spheres of the
+    packing touch their 12 neighbours): the n lattice sites nearest the
+    centre of a large block, each coordinate perturbed by N(0, (noise r)^2).
+    The noise turns about half of the touching pairs into overlaps (contacts
+    with a Hertz area) and separates the rest."""
+    k = int(math.ceil((n * 1.6) ** (1.0 / 3.0))) + 2
+    h = spacing * math.sqrt(2.0 / 3.0)
+    p, q, l = np.meshgrid(np.arange(k, dtype=np.float64), np.arange(k, dtype=np.float64),
+                          np.arange(k, dtype=np.float64), indexing="ij")
+    odd = np.mod(l, 2.0)
+    x = spacing * (p + 0.5 * q + 0.5 * odd)
+    y = spacing * (math.sqrt(3.0) / 2.0) * (q + odd / 3.0)
+    z = h * l
+    pts = _nearest_to_centre(np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1), n)
+    g = _rng(seed, 6)
+    pts = pts + g.normal(0.0, noise * PAPER_R, size=pts.shape)
+    return _paper_cells("paper_hex", pts, seed, gamma_med, {"spacing": spacing, "noise": noise})
+
+
+def _rejection_sample(g: np.random.Generator, n: int, inside, lo: np.ndarray, hi: np.ndarray, dmin: float,
+                      max_tries: int):
+    """Random sequential addition: points drawn uniformly in the box [lo, hi]
+    and, in draw order, kept when ``inside`` holds and no kept point lies
+    closer than dmin.  Candidates are drawn in batches; a batch is checked
+    against the kept points with a k-d tree and then against its own earlier
+    members in draw order, which is the sequential rule."""
+    from scipy.spatial import cKDTree
+    kept = np.empty((0, 3))
+    tree = None
+    tries = 0
+    while kept.shape[0] < n:
+        if tries >= max_tries:
+            raise RuntimeError("rejection sampling: the domain is too full")
+        m = max(4096, 4 * (n - kept.shape[0]))
+        cand = g.uniform(lo, hi, size=(m, 3))
+        tries += m
+        cand = cand[inside(cand)]
+        if tree is not None and cand.shape[0]:
+            d, _ = tree.query(cand, k=1, distance_upper_bound=dmin)
+            cand = cand[~(d < dmin)]
+        if cand.shape[0] == 0:
+            continue
+        pairs = cKDTree(cand).query_pairs(dmin, output_type="ndarray")
+        first, second = np.minimum(pairs[:, 0], pairs[:, 1]), np.maximum(pairs[:, 0], pairs[:, 1])
+        # in draw order: a candidate is kept unless an earlier kept candidate
+        # conflicts with it; decided by rounds (undecided 0, kept 1, dead 2)
+        state = np.zeros(cand.shape[0], dtype=np.int8)
+        while (state == 0).any():
+            hit = np.zeros(cand.shape[0], dtype=bool)
+            np.logical_or.at(hit, second, state[first] == 1)
+            state[(state == 0) & hit] = 2
+            wait = np.zeros(cand.shape[0], dtype=bool)
+            np.logical_or.at(wait, second, state[first] == 0)
+            state[(state == 0) & ~wait] = 1
+        take = np.nonzero(state == 1)[0][: n - kept.shape[0]]
+        kept = np.concatenate([kept, cand[take]])
+        tree = cKDTree(kept)
+    return kept
+
+
+def paper_random(n: int = 50_000, density: float = 1.6, dmin: float = 0.7, aspect: float = 1.5,
+                 seed: int = 7000, gamma_med: float = 3.0e4) -> HertzCells:
+    """Random packing in a spheroid (semi-axes a, a, aspect a, volume n /
+    density) by rejection sampling with a minimum centre distance dmin < 2r
+    (cells may overlap, so they touch, but not pile up)."""
+    a = (3.0 * n / (4.0 * math.pi * aspect * density)) ** (1.0 / 3.0)
+    inside = lambda c: (c[:, 0] / a) ** 2 + (c[:, 1] / a) ** 2 + (c[:, 2] / (aspect * a)) ** 2 <= 1.0
+    g = _rng(seed, 7)
+    lo = np.array([-a, -a, -aspect * a])
+    pts = _rejection_sample(g, n, inside, lo, -lo, dmin, 400 * n)
+    return _paper_cells("paper_random", pts, seed, gamma_med, {"a": a, "density": density, "dmin": dmin})
+
+
+def paper_dumbbell(n: int = 50_000, density: float = 1.6, dmin: float = 0.7, bridge_radius: float = 1.5,
+                   seed: int = 8000, gamma_med: float = 3.0e4) -> HertzCells:
+    """Two equal spherical lobes joined by a thin cylindrical bridge (radius
+    bridge_radius, length one lobe radius), all filled by the same rejection
+    sampling: the graph has a bottleneck."""
+    # volumes: 2 lobes of radius a and a bridge of length a
+    f = lambda a: 2 * (4.0 / 3.0) * math.pi * a ** 3 + math.pi * bridge_radius ** 2 * a - n / density
+    lo_a, hi_a = 1.0, 1000.0
+    for _ in range(200):
+        mid = 0.5 * (lo_a + hi_a)
+        lo_a, hi_a = (mid, hi_a) if f(mid) < 0 else (lo_a, mid)
+    a = 0.5 * (lo_a + hi_a)
+    cx = a + 0.5 * a   # lobe centres at x = +-cx; the bridge spans |x| <= a / 2 plus the caps' overlap
+
+    def inside(c):
+        l1 = (c[:, 0] - cx) ** 2 + c[:, 1] ** 2 + c[:, 2] ** 2 <= a * a
+        l2 = (c[:, 0] + cx) ** 2 + c[:, 1] ** 2 + c[:, 2] ** 2 <= a * a
+        br = (np.abs(c[:, 0]) <= cx) & (c[:, 1] ** 2 + c[:, 2] ** 2 <= bridge_radius ** 2)
+        return l1 | l2 | br
+
+    g = _rng(seed, 8)
+    lo = np.array([-cx - a, -a, -a])
+    pts = _rejection_sample(g, n, inside, lo, -lo, dmin, 400 * n)
+    return _paper_cells("paper_dumbbell", pts, seed, gamma_med,
+                        {"a": a, "density": density, "dmin": dmin, "bridge_radius": bridge_radius})
