@@ -60,7 +60,7 @@ __global__ void k_spmv(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0, 
 // ILP row groups are in flight per lane at once (their slot loads and
 // gathers interleave), which hides the block-load -> gather latency chain.
 template <typename T, int LPR, int ILP>
-__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? (ILP == 1 ? 8 : 4) : (ILP == 1 ? 4 : 2)) k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0,
+__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? (ILP == 1 ? 6 : 4) : (ILP == 1 ? 4 : 2)) k_spmv_pq(Blk<T> B, const int32_t *__restrict__ row_ptr, T gamma0,
                                                 int64_t n, const T *__restrict__ p, T *q, double *partials,
                                                 Scal *sc)
 {
@@ -89,6 +89,12 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? (ILP == 1 ? 8 : 4) : (ILP
                 e[u] = row_ptr[i[u] + 1];
             }
         }
+        // each lane's next slot record is loaded while the current slot's
+        // gather and products run
+        typename Blk<T>::Raw R[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u)
+            if (s[u] < e[u]) R[u] = B.fetch(s[u]);
         bool more = true;
         while (more) {
             more = false;
@@ -96,7 +102,10 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? (ILP == 1 ? 8 : 4) : (ILP
             int32_t j[ILP];
 #pragma unroll
             for (int u = 0; u < ILP; ++u)
-                if (s[u] < e[u]) B.load(s[u], S[u], j[u]);
+                if (s[u] < e[u]) B.expand(R[u], S[u], j[u]);
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (s[u] + LPR < e[u]) R[u] = B.fetch(s[u] + LPR);
 #pragma unroll
             for (int u = 0; u < ILP; ++u)
                 if (s[u] < e[u]) {

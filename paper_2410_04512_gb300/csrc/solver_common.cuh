@@ -51,16 +51,27 @@ __device__ __forceinline__ void rz_finish(Scal *sc, double rz)
 // the column.  FP64: 6 doubles (three 16-byte loads) plus the column array;
 // FP32: an 8-float record (6 floats, the column's bits, pad; two loads).
 template <typename T> struct Blk;
+// fetch() issues a slot's loads, expand() turns them into the six entries
+// and the column (split so that the next slot's loads can be in flight
+// while the current one is used).
 template <> struct Blk<double> {
     const int32_t *col;
     const double *blk;
-    __device__ __forceinline__ void load(int32_t s, double *S, int32_t &j) const
+    struct Raw {
+        double2 a, b, c;
+        int32_t j;
+    };
+    __device__ __forceinline__ Raw fetch(int32_t s) const
     {
         const double2 *b2 = reinterpret_cast<const double2 *>(blk + 6 * (int64_t)s);
-        double2 a = b2[0], b = b2[1], c = b2[2];
-        S[0] = a.x; S[1] = a.y; S[2] = b.x; S[3] = b.y; S[4] = c.x; S[5] = c.y;
-        j = col[s];
+        return Raw{b2[0], b2[1], b2[2], col[s]};
     }
+    __device__ __forceinline__ void expand(const Raw &r, double *S, int32_t &j) const
+    {
+        S[0] = r.a.x; S[1] = r.a.y; S[2] = r.b.x; S[3] = r.b.y; S[4] = r.c.x; S[5] = r.c.y;
+        j = r.j;
+    }
+    __device__ __forceinline__ void load(int32_t s, double *S, int32_t &j) const { expand(fetch(s), S, j); }
 };
 // FP32: the block is kept in the form of eq. (1), Upsilon = g_perp I +
 // (g_par - g_perp) u u^T: a 16-byte record (g_perp, g_par - g_perp, u_x, u_y)
@@ -70,10 +81,16 @@ template <> struct Blk<double> {
 template <> struct Blk<float> {
     const float4 *a;
     const float2 *b;
-    __device__ __forceinline__ void load(int32_t s, float *S, int32_t &j) const
+    struct Raw {
+        float4 x;
+        float2 y;
+    };
+    __device__ __forceinline__ Raw fetch(int32_t s) const { return Raw{a[s], b[s]}; }
+    __device__ __forceinline__ void load(int32_t s, float *S, int32_t &j) const { expand(fetch(s), S, j); }
+    __device__ __forceinline__ void expand(const Raw &r, float *S, int32_t &j) const
     {
-        const float4 x = a[s];
-        const float2 y = b[s];
+        const float4 x = r.x;
+        const float2 y = r.y;
         const float gq = x.x, dg = x.y, ux = x.z, uy = x.w, uz = y.x;
         const float dx = dg * ux, dy = dg * uy;
         S[0] = fmaf(dx, ux, gq);
