@@ -523,6 +523,7 @@ def other_configs(args):
             ("batch512", ["--workload", "batch512", "--steps", "2"]),
             ("warm200k", ["--workload", "warm200k"]),
             ("aug1m", ["--workload", "aug1m", "--steps", "2"]),
+            ("local1m", ["--workload", "local1m", "--steps", "3"]),
             ("paper", ["--workload", "paper", "--paper-reps", "3"])]
     out = {}
     for name, extra in runs:
@@ -546,7 +547,8 @@ def other_configs(args):
                                     "latency_ms", "looped_plain_fp64", "looped_mixed", "learned", "zero_guess",
                                     "previous_v", "solve_only_ms_mean", "tree_layout", "clocks", "augmented",
                                     "plain_fp64", "outer_vs_plain_iterations", "augmented_sweep",
-                                    "error_bound_stopping", "paper_workloads", "hex_scaling")
+                                    "error_bound_stopping", "paper_workloads", "hex_scaling", "global_forest",
+                                    "local_forests", "best_local_vs_global_step", "paper_hex_1e5_tol_1e-5")
                 if k in rec}
         keep["workload"] = rec.get("config", {}).get("workload")
         if "roofline" in rec:
@@ -765,6 +767,101 @@ def run_augmented(args):
         "outer_vs_plain_iterations": round(ia.outer_iterations / max(ip.iterations, 1), 3),
         "augmented_sweep": sweep,
         "error_bound_stopping": estop,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_local(args):
+    """The partitioned spanning-forest preconditioner (Section 6) on the
+    1e6-cell spheroid, mixed precision (the chosen form): per step the
+    leaves of a uniform grid, the union of the leaves' forests, its factor
+    and one solve, against the same step with the global forest, for leaf
+    sides giving about 190, 510 and 1000 cells per leaf (grid, blocks and
+    the contact graph built once)."""
+    import torch
+
+    import paper_2410_04512_gb300 as sgp
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgp.Context(0, stream)
+    c = WORKLOADS["ball1m"]["make"](replica_seed(0))
+    n = c.n
+    pos = torch.from_numpy(c.pos).to(dev)
+    radii = torch.from_numpy(c.radii).to(dev)
+    tp, tq = (torch.from_numpy(t).to(dev) for t in c.tables())
+    F = torch.from_numpy(c.forces()).to(dev)
+    g = ctx.collision_graph(pos, radii)
+    ij = g.edges()
+    gp, gq = workloads.pair_gamma_torch(c.seed, ij, tp, tq)
+    prec = sgp.PREC_MIXED
+    M = ctx.friction_assemble(g, pos, gp.contiguous(), gq.contiguous(), c.gamma0, prec)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    density = n / (4.0 / 3.0 * np.pi * c.meta["radius"] ** 3) if "radius" in c.meta else None
+
+    def run(h):
+        H = {"leaf": None, "T": None, "Fh": None}
+        rows = []
+        for step in range(args.warmup + args.steps):
+            a, b, m = ev(), ev(), ev()
+            a.record(stream)
+            if h is None:
+                H["T"] = ctx.max_spanning_tree(M, H["T"])
+            else:
+                H["leaf"] = ctx.grid_leaves(pos, h, H["leaf"])
+                H["T"] = ctx.local_spanning_forest(M, H["leaf"], H["T"])
+            H["Fh"] = ctx.tree_factor(M, H["T"], H["Fh"])
+            m.record(stream)
+            _, info = ctx.pcg_solve(M, H["Fh"], F, tol=args.tol, precision=prec)
+            b.record(stream)
+            b.synchronize()
+            if step >= args.warmup:
+                rows.append((a.elapsed_time(b), m.elapsed_time(b), info))
+        info = rows[-1][2]
+        step_ms = float(np.median([r[0] for r in rows]))
+        lay = H["Fh"].layout()
+        out = {"step_ms": round(step_ms, 3), "solve_ms": round(float(np.median([r[1] for r in rows])), 3),
+               "solves_per_s": round(1e3 / step_ms, 4), "inner_iterations": info.iterations,
+               "outer_iterations": info.outer_iterations, "true_rel_residual": info.true_rel_residual,
+               "forest_edges": H["T"].info()[0], "components": H["T"].info()[1],
+               "bins": lay["bins"], "top": lay["top"]}
+        if h is not None:
+            out["leaf_side"] = h
+            out["leaves"] = int(torch.unique(H["leaf"]).numel())
+            out["cells_per_leaf_mean"] = round(n / out["leaves"], 1)
+        return out
+
+    glob = run(None)
+    # sides for about 190, 510 and 1000 cells per leaf at the spheroid's density
+    rho = density if density else n / (8.0 * float(pos.abs().max()) ** 3)
+    sides = [round((k / rho) ** (1.0 / 3.0), 3) for k in (190, 510, 1000)]
+    local = [run(h) for h in sides]
+    best = max(local, key=lambda r: r["solves_per_s"])
+    # the paper's noisy hexagonal packing (1e5 cells, gamma_med 3e4, Hertz
+    # areas, tol 1e-5 as in its Section 5), global against local forests
+    hx = workloads.paper_hex(n=100_000, seed=6400)
+    pos, radii = torch.from_numpy(hx.pos).to(dev), torch.from_numpy(hx.radii).to(dev)
+    g = ctx.collision_graph(pos, radii)
+    gp, gq = hx.gammas_torch(g.edges(), pos, radii)
+    M = ctx.friction_assemble(g, pos, gp.contiguous(), gq.contiguous(), hx.gamma0, prec)
+    F = torch.from_numpy(np.random.Generator(np.random.PCG64([6400, 1])).standard_normal((hx.n, 3))).to(dev)
+    n = hx.n
+    tol_saved, args.tol = args.tol, 1e-5
+    hex_rows = {"global": run(None)}
+    for k in (190, 510, 1000):
+        hex_rows["cells_%d" % k] = run(round((k / 1.4142) ** (1.0 / 3.0), 3))   # 1.414 cells per unit volume
+    args.tol = tol_saved
+    line = {
+        "metric": METRIC, "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": best["step_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["ball1m"]["desc"] + "; partitioned spanning forest: uniform-grid "
+                               "leaves, each leaf's own maximum spanning forest, contacts between leaves dropped",
+                   "n_cells": n, "tol": args.tol,
+                   "step": "leaves + local forest + factor + mixed solve (graph and blocks built once)"},
+        "global_forest": glob, "local_forests": local,
+        "best_local_vs_global_step": round(glob["step_ms"] / best["step_ms"], 3),
+        "paper_hex_1e5_tol_1e-5": hex_rows,
     }
     print(json.dumps(line), flush=True)
 
@@ -1215,7 +1312,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgp", choices=["sgp", "reference"])
     ap.add_argument("--workload", default="ball1m",
-                    choices=sorted(WORKLOADS) + ["batch512", "warm200k", "aug1m", "paper"])
+                    choices=sorted(WORKLOADS) + ["batch512", "warm200k", "aug1m", "paper", "local1m"])
     ap.add_argument("--paper-reps", dest="paper_reps", type=int, default=5,
                     help="paper: independent realizations per geometry")
     ap.add_argument("--paper-n", dest="paper_n", type=int, default=50_000, help="paper: cells per geometry")
@@ -1251,6 +1348,8 @@ def main():
         run_augmented(args)
     elif args.workload == "paper":
         run_paper(args)
+    elif args.workload == "local1m":
+        run_local(args)
     else:
         run_gpu(args)
 

@@ -203,6 +203,29 @@ sgp_status sgp_tree_info(const sgp_tree *tree, int64_t *n_edges, int64_t *n_comp
                          const int32_t **edge_ids_dev);
 void sgp_tree_destroy(sgp_tree *tree);
 
+/* ---- Section 6: the partitioned ("local") spanning-forest preconditioner -----
+ * The cells are split into spatial leaves; each leaf keeps the maximum
+ * spanning forest of its own contacts, contacts between leaves are dropped,
+ * and P_loc = gamma0 I + the block Laplacian of the union is block diagonal
+ * over the leaves (its leaves are solved independently).  The forest is a
+ * subgraph of the collision graph, so lambda_min(Gamma, P_loc) >= 1 still
+ * holds (Section 4) and SGP_STOP_ERROR's mu = 1 stays valid.
+ *
+ * Leaf of every cell in the uniform grid of side h (the leaves of an octree
+ * at one depth): k = floor(x / h) per axis (FP64, correctly rounded
+ * division), label = (kx & 1023) | (ky & 1023) << 10 | (kz & 1023) << 20.
+ * Leaves 1024 h apart along an axis share a label (no contact joins them).
+ * pos_dev: n x 3 float64; leaf_dev: n int32, written.  INVALID_ARG unless
+ * h is positive and finite. */
+sgp_status sgp_grid_leaves(sgp_ctx *ctx, int64_t n, const double *pos_dev, double h, int32_t *leaf_dev);
+/* The union of the leaves' maximum spanning forests: Boruvka under the same
+ * strict order as sgp_max_spanning_tree over the contacts whose two cells
+ * have equal labels in leaf_dev (n int32, any labels, the matrix's cell
+ * numbering).  The result is an sgp_tree like that call's (sgp_tree_info,
+ * sgp_tree_factor, the tree preconditioner of the solvers). */
+sgp_status sgp_local_spanning_forest(sgp_ctx *ctx, const sgp_matrix *matrix, const int32_t *leaf_dev,
+                                     sgp_tree **tree);
+
 /* ---- Section 3.3 (Algorithm 2) and Appendix B.1: tree factor ----------------
  * P = gamma0 I + block Laplacian of the spanning forest (the self-loops kept,
  * Section 3.1) is factored P = L D L^T by block elimination.  The elimination

@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "sgp_matrix_edge_blocks": ([P, P, P, P], I32),
         "sgp_matrix_destroy": ([P], None),
         "sgp_max_spanning_tree": ([P, P, PP], I32),
+        "sgp_grid_leaves": ([P, I64, P, D, P], I32),
+        "sgp_local_spanning_forest": ([P, P, P, PP], I32),
         "sgp_tree_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64), PP], I32),
         "sgp_tree_destroy": ([P], None),
         "sgp_tree_factor": ([P, P, P, PP], I32),
@@ -353,6 +355,26 @@ class Context:
     def max_spanning_tree(self, M: Matrix, tree: Tree | None = None) -> Tree:
         T = tree if tree is not None else Tree(self)
         self._ok(_lib.sgp_max_spanning_tree(self.ptr, M.ptr, ctypes.byref(T.ptr)))
+        return T
+
+    # -- partitioned spanning forest (Section 6) --------------------------
+    def grid_leaves(self, pos: torch.Tensor, h: float, leaf: torch.Tensor | None = None) -> torch.Tensor:
+        """Leaf label of every cell in the uniform grid of side h (int32)."""
+        n = pos.shape[0]
+        _check_vec(pos, n, name="pos")
+        leaf = torch.empty(n, dtype=torch.int32, device=pos.device) if leaf is None else leaf
+        if leaf.dtype != torch.int32 or leaf.shape != (n,) or not leaf.is_contiguous() or not leaf.is_cuda:
+            raise ValueError("leaf must be a contiguous CUDA int32 tensor of n entries")
+        self._ok(_lib.sgp_grid_leaves(self.ptr, n, _ptr(pos), float(h), _ptr(leaf)))
+        return leaf
+
+    def local_spanning_forest(self, M: Matrix, leaf: torch.Tensor, tree: Tree | None = None) -> Tree:
+        """Union of the leaves' maximum spanning forests (contacts between
+        leaves dropped)."""
+        if leaf.dtype != torch.int32 or leaf.shape != (M.n,) or not leaf.is_contiguous() or not leaf.is_cuda:
+            raise ValueError("leaf must be a contiguous CUDA int32 tensor of n entries")
+        T = tree if tree is not None else Tree(self)
+        self._ok(_lib.sgp_local_spanning_forest(self.ptr, M.ptr, _ptr(leaf), ctypes.byref(T.ptr)))
         return T
 
     def tree_factor(self, M: Matrix, T: Tree, factor: Factor | None = None) -> Factor:

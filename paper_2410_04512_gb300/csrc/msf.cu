@@ -123,14 +123,37 @@ __global__ void k_u8_to_i32(const uint8_t *__restrict__ a, int32_t *b, int64_t n
     if (k < n) b[k] = a[k];
 }
 
-}  // namespace
-
-extern "C" {
-
-sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *M, sgp_tree **out)
+// Section 6 (partitioned forest): contacts whose two cells share a leaf.
+__global__ void k_leaf_keep(const int32_t *__restrict__ ij, const int32_t *__restrict__ leaf, int64_t m,
+                            int32_t *keep)
 {
-    if (!ctx || !M || !out) return SGP_ERR_INVALID_ARG;
-    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < m) keep[e] = leaf[ij[2 * e]] == leaf[ij[2 * e + 1]];
+}
+
+// Leaf of each cell in the uniform grid of side h: k = floor(x / h) per
+// axis (FP64 division, correctly rounded), label = the low 10 bits of each
+// k packed x | y << 10 | z << 20.  Quotients beyond +-2^62 are clamped
+// before the conversion (a leaf label either way).
+__global__ void k_grid_leaves(int64_t n, const double *__restrict__ pos, double h, int32_t *leaf)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t lab = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double q = floor(pos[3 * i + c] / h);
+        q = fmin(fmax(q, -4.6e18), 4.6e18);
+        const long long k = (long long)q;
+        lab |= (int32_t)(k & 1023) << (10 * c);
+    }
+    leaf[i] = lab;
+}
+
+// The maximum spanning forest of the contacts whose cells share a leaf
+// (all contacts when leaf is null).
+sgp_status msf_build(sgp_ctx *ctx, const sgp_matrix *M, const int32_t *leaf, sgp_tree **out)
+{
     const int64_t n = M->n, m = M->m;
     sgp_tree *T = *out ? *out : new sgp_tree();
     *out = T;
@@ -155,8 +178,18 @@ sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *M, sgp_tree **o
 
     LAUNCH(ctx, k_init_comp, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n);
     if (m > 0) SGP_CUDA(ctx, cudaMemsetAsync(intree, 0, (size_t)m, ctx->stream));
-    LAUNCH(ctx, k_iota, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, liveA, m);
     int64_t nlive = m;
+    if (leaf) {
+        LAUNCH(ctx, k_leaf_keep, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, ij, leaf, m, keep);
+        SGP_TRY(scan_exclusive_i32(ctx, keep, off, m));
+        LAUNCH(ctx, k_compact, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)nullptr,
+               (const int32_t *)keep, (const int32_t *)off, m, liveA);
+        int32_t h = 0;
+        SGP_TRY(read_back(ctx, &h, off + m, sizeof(int32_t)));
+        nlive = h;
+    } else {
+        LAUNCH(ctx, k_iota, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, liveA, m);
+    }
     int rounds = 0;
     while (nlive > 0) {
         if (++rounds > 64) return sgp_fail(ctx, SGP_ERR_TIMEOUT, "spanning forest: too many rounds");
@@ -195,6 +228,35 @@ sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *M, sgp_tree **o
     LAUNCH(ctx, k_compact, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, (const int32_t *)nullptr,
            (const int32_t *)keep, (const int32_t *)off, m, bp<int32_t>(T->edges));
     return SGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *M, sgp_tree **out)
+{
+    if (!ctx || !M || !out) return SGP_ERR_INVALID_ARG;
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return msf_build(ctx, M, nullptr, out);
+}
+
+sgp_status sgp_grid_leaves(sgp_ctx *ctx, int64_t n, const double *pos, double h, int32_t *leaf)
+{
+    if (!ctx || n < 0 || (n > 0 && (!pos || !leaf)))
+        return ctx ? sgp_fail(ctx, SGP_ERR_INVALID_ARG, "grid_leaves: bad pointers or size") : SGP_ERR_INVALID_ARG;
+    if (!(h > 0.0) || !std::isfinite(h))
+        return sgp_fail(ctx, SGP_ERR_INVALID_ARG, "grid_leaves: h must be positive and finite");
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    LAUNCH(ctx, k_grid_leaves, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, n, pos, h, leaf);
+    return SGP_OK;
+}
+
+sgp_status sgp_local_spanning_forest(sgp_ctx *ctx, const sgp_matrix *M, const int32_t *leaf, sgp_tree **out)
+{
+    if (!ctx || !M || !out || (M->n > 0 && !leaf)) return SGP_ERR_INVALID_ARG;
+    SGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return msf_build(ctx, M, leaf, out);
 }
 
 sgp_status sgp_tree_info(const sgp_tree *T, int64_t *n_edges, int64_t *n_comp,
