@@ -1225,9 +1225,14 @@ __global__ void __launch_bounds__(BT) k_top(TopArgs a, const T *__restrict__ tL,
     __syncthreads();
     if (FUSE && stop_s) return;
     // forward levels of the top (only the entries with top contributors);
-    // empty levels are skipped, warps without entries only meet the barrier
-    const int warp = threadIdx.x >> 5;
-    for (int lv = 0; lv < a.LVP - 1; ++lv) {
+    // empty levels are skipped, warps without entries only meet the
+    // barrier; from the first level after which no level has more than 32
+    // entries, warp 0 runs the rest alone with warp barriers
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nlv = a.LVP - 1;
+    int fsplit = nlv;
+    while (fsplit > 0 && telev[fsplit] - telev[fsplit - 1] <= 32) --fsplit;
+    for (int lv = 0; lv < fsplit; ++lv) {
         const int32_t e0 = telev[lv], e1 = telev[lv + 1];
         if (e0 == e1) continue;
         if (warp * 32 < e1 - e0)
@@ -1238,21 +1243,47 @@ __global__ void __launch_bounds__(BT) k_top(TopArgs a, const T *__restrict__ tL,
             }
         __syncthreads();
     }
-    // diagonal and backward levels
-    for (int lv = a.LVP - 2; lv >= 0; --lv) {
+    if (warp == 0) {
+        for (int lv = fsplit; lv < nlv; ++lv) {
+            const int32_t e0 = telev[lv], e1 = telev[lv + 1];
+            if (e0 == e1) continue;
+            if (lane < e1 - e0) {
+                FwdEnt<T> f;
+                fwd_fetch(f, e0 + lane, e1, ter, tcp, a.nte, a.ntt, tcc, L_s);
+                fwd_apply(f, w_s, tcc, L_s);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // diagonal and backward levels: warp 0 alone while the levels have at
+    // most 32 vertices, then the warps with vertices in the level
+    auto bwd_vertex = [&](int32_t i) {
+        T x[3] = {w_s[3 * i], w_s[3 * i + 1], w_s[3 * i + 2]}, zz[3];
+        sym_mv((DST ? (const T *)D_s : tD) + 6 * i, x, zz);
+        for (int32_t p = tpp[i]; p < tpp[i + 1]; ++p) {
+            T u[3];
+            full_mtv(L_s + 9 * tpL[p], w_s + 3 * tpq[p], u);
+            zz[0] -= u[0]; zz[1] -= u[1]; zz[2] -= u[2];
+        }
+        w_s[3 * i] = zz[0]; w_s[3 * i + 1] = zz[1]; w_s[3 * i + 2] = zz[2];
+    };
+    int bsplit = nlv - 1;
+    while (bsplit >= 0 && tvlev[bsplit + 1] - tvlev[bsplit] <= 32) --bsplit;
+    if (warp == 0) {
+        for (int lv = nlv - 1; lv > bsplit; --lv) {
+            const int32_t i0 = tvlev[lv], i1 = tvlev[lv + 1];
+            if (i0 == i1) continue;
+            if (lane < i1 - i0) bwd_vertex(i0 + lane);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int lv = bsplit; lv >= 0; --lv) {
         const int32_t i0 = tvlev[lv], i1 = tvlev[lv + 1];
         if (i0 == i1) continue;
         if (warp * 32 < i1 - i0)
-        for (int32_t i = i0 + threadIdx.x; i < i1; i += BT) {
-            T x[3] = {w_s[3 * i], w_s[3 * i + 1], w_s[3 * i + 2]}, zz[3];
-            sym_mv((DST ? (const T *)D_s : tD) + 6 * i, x, zz);
-            for (int32_t p = tpp[i]; p < tpp[i + 1]; ++p) {
-                T u[3];
-                full_mtv(L_s + 9 * tpL[p], w_s + 3 * tpq[p], u);
-                zz[0] -= u[0]; zz[1] -= u[1]; zz[2] -= u[2];
-            }
-            w_s[3 * i] = zz[0]; w_s[3 * i + 1] = zz[1]; w_s[3 * i + 2] = zz[2];
-        }
+            for (int32_t i = i0 + threadIdx.x; i < i1; i += BT) bwd_vertex(i);
         __syncthreads();
     }
     T *zt = z + 3 * (size_t)a.G;
