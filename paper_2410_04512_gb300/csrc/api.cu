@@ -469,6 +469,8 @@ sgp_status sgp_create(sgp_ctx **out, int device, void *stream)
     if (tc) ctx->tail_cap = atoi(tc);
     const char *bc = getenv("SGP_BIN_CAP");
     if (bc) ctx->bin_cap = atoi(bc);
+    const char *ns = getenv("SGP_NO_SMALL");
+    if (ns && atoi(ns)) ctx->small_solve = 0;
     const char *nf = getenv("SGP_NO_FUSE");
     if (nf && atoi(nf)) ctx->fused = 0;
     if (scratch_ensure(ctx, 1 << 20) != SGP_OK || cudaMalloc(&ctx->d_flags, 4096) != cudaSuccess ||

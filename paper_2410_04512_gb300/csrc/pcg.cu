@@ -14,6 +14,7 @@
 // with per-kernel timing on, as replayed chunk graphs with the host polling
 // the `done` word between chunks.
 #include "solver_common.cuh"
+#include "tail.cuh"
 
 namespace {
 
@@ -574,6 +575,320 @@ __global__ void __launch_bounds__(RB) k_fcg_upd(int64_t n3, const double *__rest
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Small systems: the whole mixed-precision solve in one thread block.  When
+// the factor's one-block tail holds every contraction level (a few thousand
+// cells at most), the FP64 residual, the FP32 inner PCG (product, tree
+// solve, updates, reductions) and the FP64 accumulation all run in one
+// launch with every vector in shared memory: no launch or host round trip
+// per iteration.  The arithmetic is that of the multi-launch path: eq. (1)
+// FP32 records and FP64 blocks for the product, the tail's level solve with
+// FP32 L and D^-1, FP64 accumulators for the dot products.
+// ---------------------------------------------------------------------------
+constexpr int SB = 1024;
+
+struct SmallOut {
+    long long it;
+    int outer, status;
+    double rr, ff;
+};
+
+struct SmallArgs {
+    int32_t n;
+    double gamma0, tol, itol;
+    long long maxit;
+    int max_outer, x_given;
+    Blk<float> B32;
+    Blk<double> B64;
+    const int32_t *row_ptr;
+    Tail tl;
+    const int32_t *ord, *rc_ptr, *pr_ptr;
+    const float *L, *Lf, *Dinv;
+    const double *F;
+    double *v;
+    SmallOut *out;
+};
+
+__host__ __device__ inline size_t small_smem_bytes(int32_t n, int32_t np, int32_t nr)
+{
+    // the tail's staged arrays, the position -> cell map, r, p, q (FP32),
+    // and one FP64 vector whose storage also holds z and d (FP32)
+    return tail_smem_staged<float>(n, np, nr) + tail_align(4 * (size_t)n) + 3 * tail_align(12 * (size_t)n) +
+           tail_align(24 * (size_t)n);
+}
+
+// Block sums whose total only thread 0 needs (it takes the scalar
+// decisions and broadcasts them): FP32 partials are summed within each warp
+// in FP32 and across warps in FP64; FP64 partials in FP64.  One SM's FP64
+// rate is low, so FP64 work per thread is kept to the partials that need
+// it.  The caller synchronises before the scratch is used again.
+__device__ __forceinline__ double small_red32(float x, double *shd)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = (double)x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = shd[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+__device__ __forceinline__ double small_red64(double x, double *shd)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = shd[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+__global__ void __launch_bounds__(SB, 1) k_pcg_small(SmallArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double shd[SB / 32];
+    // scalars decided by thread 0 and read by all
+    __shared__ double b_nr;
+    __shared__ float b_al, b_be;
+    __shared__ int b_go;
+    const Tail &tl = a.tl;
+    const int32_t n = a.n, n3 = 3 * n;
+    unsigned char *cur = smem_raw;
+    auto take = [&](size_t b) { unsigned char *p = cur; cur += tail_align(b); return p; };
+    float *sw = reinterpret_cast<float *>(take(12 * (size_t)tl.n));
+    int32_t *spr = reinterpret_cast<int32_t *>(take(4 * (size_t)(tl.n + 1)));
+    int32_t *stb = reinterpret_cast<int32_t *>(take(4 * (size_t)tl.np));
+    int32_t *spc = reinterpret_cast<int32_t *>(take(4 * (size_t)tl.np));
+    int32_t *sct = reinterpret_cast<int32_t *>(take(4 * (size_t)tl.np));
+    int32_t *src = reinterpret_cast<int32_t *>(take(4 * (size_t)(tl.nr + 1)));
+    int32_t *stq = reinterpret_cast<int32_t *>(take(4 * (size_t)tl.nr));
+    float *sD = reinterpret_cast<float *>(take(24 * (size_t)tl.n));
+    float *sL = reinterpret_cast<float *>(take(36 * (size_t)tl.np));
+    int32_t *sord = reinterpret_cast<int32_t *>(take(4 * (size_t)n));
+    float *r = reinterpret_cast<float *>(take(12 * (size_t)n));
+    float *p = reinterpret_cast<float *>(take(12 * (size_t)n));
+    float *q = reinterpret_cast<float *>(take(12 * (size_t)n));
+    double *r64 = reinterpret_cast<double *>(take(24 * (size_t)n));
+    float *z = reinterpret_cast<float *>(r64), *d = z + n3;   // share r64's storage
+    // stage the tail (it covers every position: P0 = Q0 = R0 = C0 = 0)
+    const float *Lt = a.L + 9 * (int64_t)tl.Q0, *Dt = a.Dinv + 6 * (int64_t)tl.P0;
+    for (int32_t i = threadIdx.x; i < 6 * tl.n; i += SB) sD[i] = Dt[i];
+    for (int32_t i = threadIdx.x; i < 9 * tl.np; i += SB) sL[i] = Lt[i];
+    for (int32_t i = threadIdx.x; i <= tl.n; i += SB) spr[i] = a.pr_ptr[tl.P0 + i] - tl.Q0;
+    for (int32_t i = threadIdx.x; i < tl.np; i += SB) {
+        stb[i] = tl.tb[i];
+        spc[i] = tl.tpc[i];
+        sct[i] = tl.tct[i];
+    }
+    for (int32_t i = threadIdx.x; i <= tl.nr; i += SB) src[i] = a.rc_ptr[tl.R0 + i] - tl.C0;
+    for (int32_t i = threadIdx.x; i < tl.nr; i += SB) stq[i] = tl.tq[i];
+    for (int32_t i = threadIdx.x; i < n; i += SB) sord[i] = a.ord[i];
+    __syncthreads();
+
+    // z = P^-1 r: gather r into elimination order, forward levels,
+    // diagonal and backward levels, scatter back (the tail's level solve)
+    auto tree_solve = [&]() {
+        for (int32_t i = threadIdx.x; i < n; i += SB) {
+            const int32_t c = sord[i];
+            sw[3 * i] = r[3 * c]; sw[3 * i + 1] = r[3 * c + 1]; sw[3 * i + 2] = r[3 * c + 2];
+        }
+        __syncthreads();
+        for (int l = 0; l < tl.nlev; ++l) {
+            const int32_t k0 = tl.lvl_rv[l] - tl.R0, k1 = tl.lvl_rv[l + 1] - tl.R0;
+            for (int32_t k = k0 + threadIdx.x; k < k1; k += SB) {
+                float s3[3] = {0.f, 0.f, 0.f};
+                for (int32_t j = src[k]; j < src[k + 1]; ++j) {
+                    const int32_t pp = sct[j];
+                    float y[3];
+                    full_mv(sL + 9 * pp, sw + 3 * spc[pp], y);
+                    s3[0] += y[0]; s3[1] += y[1]; s3[2] += y[2];
+                }
+                const int32_t qq = stq[k];
+                sw[3 * qq] -= s3[0]; sw[3 * qq + 1] -= s3[1]; sw[3 * qq + 2] -= s3[2];
+            }
+            __syncthreads();
+        }
+        for (int l = tl.nlev - 1; l >= 0; --l) {
+            const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
+            for (int32_t i = i0 + threadIdx.x; i < i1; i += SB) {
+                float zz[3];
+                sym_mv(sD + 6 * i, sw + 3 * i, zz);
+                for (int32_t pp = spr[i]; pp < spr[i + 1]; ++pp) {
+                    float u[3];
+                    full_mtv(sL + 9 * pp, sw + 3 * stb[pp], u);
+                    zz[0] -= u[0]; zz[1] -= u[1]; zz[2] -= u[2];
+                }
+                sw[3 * i] = zz[0]; sw[3 * i + 1] = zz[1]; sw[3 * i + 2] = zz[2];
+            }
+            __syncthreads();
+        }
+        for (int32_t i = threadIdx.x; i < n; i += SB) {
+            const int32_t c = sord[i];
+            z[3 * c] = sw[3 * i]; z[3 * c + 1] = sw[3 * i + 1]; z[3 * c + 2] = sw[3 * i + 2];
+        }
+        __syncthreads();
+    };
+
+    double ff = 0.0;
+    {
+        double x = 0.0;
+        for (int32_t k = threadIdx.x; k < n3; k += SB) x += a.F[k] * a.F[k];
+        ff = small_red64(x, shd);   // thread 0
+    }
+    if (!a.x_given)
+        for (int32_t k = threadIdx.x; k < n3; k += SB) a.v[k] = 0.0;
+    __syncthreads();
+    // thread 0's state
+    long long total = 0;
+    int outer = 0, status = SGP_OK;
+    double rr = 0.0, fi = 0.0, stop2 = 0.0, rho = 0.0;
+    long long it = 0;
+    const float g32 = (float)a.gamma0;
+    for (;;) {
+        // FP64 residual r = F - Gamma v
+        double acc = 0.0;
+        for (int32_t i = threadIdx.x; i < n; i += SB) {
+            double vi[3], yi[3];
+            row_product(a.B64, a.row_ptr, a.gamma0, (const double *)a.v, i, vi, yi);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double rc = a.F[3 * i + c] - yi[c];
+                r64[3 * i + c] = rc;
+                acc += rc * rc;
+            }
+        }
+        acc = small_red64(acc, shd);
+        if (threadIdx.x == 0) {
+            rr = acc;
+            int go = 1;
+            if (ff == 0.0) {
+                rr = 0.0;
+                go = 2;                 // v = 0
+            } else if (rr <= a.tol * a.tol * ff) {
+                go = 0;
+            } else if (outer >= a.max_outer || total >= a.maxit) {
+                status = SGP_ERR_NO_CONVERGENCE;
+                go = 0;
+            }
+            b_go = go;
+            b_nr = sqrt(rr);
+        }
+        __syncthreads();
+        const int go = b_go;
+        if (go == 2)
+            for (int32_t k = threadIdx.x; k < n3; k += SB) a.v[k] = 0.0;
+        if (go != 1) break;
+        const double nr = b_nr, inv = 1.0 / nr;
+        float fx = 0.f;
+        for (int32_t k = threadIdx.x; k < n3; k += SB) {
+            const float rk = (float)(r64[k] * inv);
+            r[k] = rk;
+            fx = fmaf(rk, rk, fx);
+        }
+        fx = (float)small_red32(fx, shd);   // r64's storage becomes z and d below
+        if (threadIdx.x == 0) {
+            fi = (double)fx;
+            const double need = 0.5 * a.tol * sqrt(ff) / nr;
+            const double itk = fmax(a.itol, fmin(need, 0.5));
+            stop2 = itk * itk * fi;
+            it = 0;
+            b_go = fi > stop2;
+        }
+        __syncthreads();
+        for (int32_t k = threadIdx.x; k < n3; k += SB) d[k] = 0.f;
+        // inner FP32 PCG on Gamma d = r from d = 0
+        if (b_go) {
+            tree_solve();
+            float x = 0.f;
+            for (int32_t k = threadIdx.x; k < n3; k += SB) {
+                p[k] = z[k];
+                x = fmaf(r[k], z[k], x);
+            }
+            const double t = small_red32(x, shd);
+            if (threadIdx.x == 0) {
+                rho = t;
+                b_go = rho > 0.0 ? 1 : 3;    // 3: breakdown
+            }
+            __syncthreads();
+            while (b_go == 1) {
+                float xp = 0.f;
+                for (int32_t i = threadIdx.x; i < n; i += SB) {
+                    float vi[3], yi[3];
+                    row_product(a.B32, a.row_ptr, g32, (const float *)p, i, vi, yi);
+                    q[3 * i] = yi[0]; q[3 * i + 1] = yi[1]; q[3 * i + 2] = yi[2];
+                    xp += fmaf(vi[0], yi[0], fmaf(vi[1], yi[1], vi[2] * yi[2]));
+                }
+                const double pq = small_red32(xp, shd);
+                if (threadIdx.x == 0) {
+                    if (!(pq > 0.0) || !isfinite(pq)) b_go = 3;
+                    else b_al = (float)(rho / pq);
+                }
+                __syncthreads();
+                if (b_go != 1) break;
+                const float al = b_al;
+                float xr = 0.f;
+                for (int32_t k = threadIdx.x; k < n3; k += SB) {
+                    d[k] = fmaf(al, p[k], d[k]);
+                    const float rk = fmaf(-al, q[k], r[k]);
+                    r[k] = rk;
+                    xr = fmaf(rk, rk, xr);
+                }
+                const double rl = small_red32(xr, shd);
+                if (threadIdx.x == 0) {
+                    ++it;
+                    if (rl <= stop2) b_go = 0;
+                    else if (total + it >= a.maxit) b_go = 4;   // inner cap
+                }
+                __syncthreads();
+                if (b_go != 1) break;
+                tree_solve();
+                float xz = 0.f;
+                for (int32_t k = threadIdx.x; k < n3; k += SB) xz = fmaf(r[k], z[k], xz);
+                const double rz = small_red32(xz, shd);
+                if (threadIdx.x == 0) {
+                    if (!(rz > 0.0)) {
+                        b_go = 3;
+                    } else {
+                        b_be = (float)(rz / rho);
+                        rho = rz;
+                    }
+                }
+                __syncthreads();
+                if (b_go != 1) break;
+                const float be = b_be;
+                for (int32_t k = threadIdx.x; k < n3; k += SB) p[k] = fmaf(be, p[k], z[k]);
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) {
+            total += it;
+            ++outer;
+            if (b_go == 3) status = SGP_ERR_NOT_SPD;
+        }
+        __syncthreads();
+        if (b_go == 3) break;
+        // v += |r| d (FP64)
+        for (int32_t k = threadIdx.x; k < n3; k += SB) a.v[k] += nr * (double)d[k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.out->it = total;
+        a.out->outer = outer;
+        a.out->status = status;
+        a.out->rr = rr;
+        a.out->ff = ff;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -820,6 +1135,55 @@ sgp_status pcg_run(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, int
 
 }  // namespace
 
+
+// The one-block solve applies: MIXED, tree preconditioner, residual
+// stopping, the factor's tail covering every level, and everything fitting
+// in one block's shared memory.
+static bool small_pcg_fits(const sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, const sgp_solve_opts *o)
+{
+    if (!ctx->small_solve || o->precision != SGP_PREC_MIXED || o->precond != SGP_PRECOND_TREE ||
+        o->stop != SGP_STOP_RESIDUAL || !Fac || Fac->precision != SGP_PREC_MIXED || M->precision != SGP_PREC_MIXED)
+        return false;
+    if (Fac->levels == 0 || Fac->tail_level != 0 || Fac->tail_P0 != 0 || !Fac->L32.p || !Fac->Dinv32.p) return false;
+    const Tail tl = tail_of(Fac);
+    if (tl.n != M->n) return false;
+    return small_smem_bytes(tl.n, tl.np, tl.nr) <= (size_t)TREE_TAIL_SMEM;
+}
+
+static sgp_status small_pcg(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fac, const double *F, double *v,
+                     const sgp_solve_opts *o, SmallOut *dout, SmallOut *hout)
+{
+    static int done_dev[64] = {0};
+    if (ctx->device >= 0 && ctx->device < 64 && !done_dev[ctx->device]) {
+        SGP_CUDA(ctx, cudaFuncSetAttribute(k_pcg_small, cudaFuncAttributeMaxDynamicSharedMemorySize, TREE_TAIL_SMEM));
+        done_dev[ctx->device] = 1;
+    }
+    const Tail tl = tail_of(Fac);
+    SmallArgs a{};
+    a.n = (int32_t)M->n;
+    a.gamma0 = M->gamma0;
+    a.tol = o->tol;
+    a.itol = o->inner_tol > 0 ? o->inner_tol : 1e-3;
+    a.maxit = o->maxit;
+    a.max_outer = o->max_outer > 0 ? o->max_outer : 30;
+    a.x_given = o->x0_given;
+    a.B32 = make_blk<float>(M);
+    a.B64 = make_blk<double>(M);
+    a.row_ptr = bp<const int32_t>(M->row_ptr);
+    a.tl = tl;
+    a.ord = bp<const int32_t>(Fac->ord);
+    a.rc_ptr = bp<const int32_t>(Fac->rc_ptr);
+    a.pr_ptr = bp<const int32_t>(Fac->pr_ptr);
+    a.L = bp<const float>(Fac->L32);
+    a.Lf = bp<const float>(Fac->Lf32);
+    a.Dinv = bp<const float>(Fac->Dinv32);
+    a.F = F;
+    a.v = v;
+    a.out = dout;
+    LAUNCH(ctx, k_pcg_small, 1, SB, small_smem_bytes(tl.n, tl.np, tl.nr), a);
+    return read_back(ctx, hout, dout, sizeof(SmallOut));
+}
+
 // FP64 product y = Gamma v without the timing hooks (used by the warm-start
 // network's loss and scaling).
 sgp_status spmv64(sgp_ctx *ctx, const sgp_matrix *M, const double *v, double *y)
@@ -982,7 +1346,18 @@ sgp_status sgp_pcg_solve(sgp_ctx *ctx, const sgp_matrix *M, const sgp_factor *Fa
         if (!opts->x0_given) SGP_CUDA(ctx, cudaMemsetAsync(v, 0, v64, ctx->stream));
         int64_t total = 0;
         int outer = 0;
-        for (;;) {
+        const bool small = small_pcg_fits(ctx, M, Fac, opts);
+        if (small) {
+            SmallOut ho{};
+            SGP_TRY(small_pcg(ctx, M, Fac, F, v, opts, reinterpret_cast<SmallOut *>(o2), &ho));
+            total = ho.it;
+            outer = ho.outer;
+            inf.status = ho.status;
+            hres[0] = ho.rr;
+            hres[1] = ho.ff;
+            inf.rel_residual = ho.ff > 0 ? std::sqrt(ho.rr / ho.ff) : 0.0;
+        }
+        for (; !small;) {
             SGP_CUDA(ctx, cudaMemsetAsync(o2 + 2, 0, 16, ctx->stream));
             if (outer == 0 && !opts->x0_given)
                 LAUNCH(ctx, k_resid64<true>, Gr, RB, 0, B64, row_ptr, M->gamma0, n, F, (const double *)v, r,

@@ -68,6 +68,7 @@ struct sgp_ctx {
     int bin_cap = 0;        // largest contraction subtree solved by one thread block: 0 = 1024 for the
                             // FP32 solve only, -1 = level kernels only, else that cap in both precisions
     int fused = 1;          // PCG step fused around the binned tree solve
+    int small_solve = 1;    // whole mixed solves of small systems in one thread block
     int use_pdl = 1;        // programmatic dependent launch of the level kernels
     int batch_chunk = 0;    // rows per work item of the batched solver
     int num_sms = 0;
