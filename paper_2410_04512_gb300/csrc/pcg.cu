@@ -695,40 +695,62 @@ __global__ void __launch_bounds__(SB, 1) k_pcg_small(SmallArgs a)
     __syncthreads();
 
     // z = P^-1 r: gather r into elimination order, forward levels,
-    // diagonal and backward levels, scatter back (the tail's level solve)
+    // diagonal and backward levels, scatter back (the tail's level solve).
+    // Levels with at most 32 receivers (forward: the last ones; backward:
+    // the first ones) run in warp 0 alone with warp barriers.
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int fsplit = tl.nlev;
+    while (fsplit > 0 && tl.lvl_rv[fsplit] - tl.lvl_rv[fsplit - 1] <= 32) --fsplit;
+    int bsplit = tl.nlev;
+    while (bsplit > 0 && tl.lvl_pos[bsplit] - tl.lvl_pos[bsplit - 1] <= 32) --bsplit;
+    auto fwd_recv = [&](int32_t k) {
+        float s3[3] = {0.f, 0.f, 0.f};
+        for (int32_t j = src[k]; j < src[k + 1]; ++j) {
+            const int32_t pp = sct[j];
+            float y[3];
+            full_mv(sL + 9 * pp, sw + 3 * spc[pp], y);
+            s3[0] += y[0]; s3[1] += y[1]; s3[2] += y[2];
+        }
+        const int32_t qq = stq[k];
+        sw[3 * qq] -= s3[0]; sw[3 * qq + 1] -= s3[1]; sw[3 * qq + 2] -= s3[2];
+    };
+    auto bwd_vert = [&](int32_t i) {
+        float zz[3];
+        sym_mv(sD + 6 * i, sw + 3 * i, zz);
+        for (int32_t pp = spr[i]; pp < spr[i + 1]; ++pp) {
+            float u[3];
+            full_mtv(sL + 9 * pp, sw + 3 * stb[pp], u);
+            zz[0] -= u[0]; zz[1] -= u[1]; zz[2] -= u[2];
+        }
+        sw[3 * i] = zz[0]; sw[3 * i + 1] = zz[1]; sw[3 * i + 2] = zz[2];
+    };
     auto tree_solve = [&]() {
         for (int32_t i = threadIdx.x; i < n; i += SB) {
             const int32_t c = sord[i];
             sw[3 * i] = r[3 * c]; sw[3 * i + 1] = r[3 * c + 1]; sw[3 * i + 2] = r[3 * c + 2];
         }
         __syncthreads();
-        for (int l = 0; l < tl.nlev; ++l) {
+        for (int l = 0; l < fsplit; ++l) {
             const int32_t k0 = tl.lvl_rv[l] - tl.R0, k1 = tl.lvl_rv[l + 1] - tl.R0;
-            for (int32_t k = k0 + threadIdx.x; k < k1; k += SB) {
-                float s3[3] = {0.f, 0.f, 0.f};
-                for (int32_t j = src[k]; j < src[k + 1]; ++j) {
-                    const int32_t pp = sct[j];
-                    float y[3];
-                    full_mv(sL + 9 * pp, sw + 3 * spc[pp], y);
-                    s3[0] += y[0]; s3[1] += y[1]; s3[2] += y[2];
-                }
-                const int32_t qq = stq[k];
-                sw[3 * qq] -= s3[0]; sw[3 * qq + 1] -= s3[1]; sw[3 * qq + 2] -= s3[2];
-            }
+            for (int32_t k = k0 + threadIdx.x; k < k1; k += SB) fwd_recv(k);
             __syncthreads();
         }
-        for (int l = tl.nlev - 1; l >= 0; --l) {
-            const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
-            for (int32_t i = i0 + threadIdx.x; i < i1; i += SB) {
-                float zz[3];
-                sym_mv(sD + 6 * i, sw + 3 * i, zz);
-                for (int32_t pp = spr[i]; pp < spr[i + 1]; ++pp) {
-                    float u[3];
-                    full_mtv(sL + 9 * pp, sw + 3 * stb[pp], u);
-                    zz[0] -= u[0]; zz[1] -= u[1]; zz[2] -= u[2];
-                }
-                sw[3 * i] = zz[0]; sw[3 * i + 1] = zz[1]; sw[3 * i + 2] = zz[2];
+        if (warp == 0) {
+            for (int l = fsplit; l < tl.nlev; ++l) {
+                const int32_t k0 = tl.lvl_rv[l] - tl.R0, k1 = tl.lvl_rv[l + 1] - tl.R0;
+                if (k0 + lane < k1) fwd_recv(k0 + lane);
+                __syncwarp();
             }
+            for (int l = tl.nlev - 1; l >= bsplit; --l) {
+                const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
+                if (i0 + lane < i1) bwd_vert(i0 + lane);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int l = bsplit - 1; l >= 0; --l) {
+            const int32_t i0 = tl.lvl_pos[l] - tl.P0, i1 = tl.lvl_pos[l + 1] - tl.P0;
+            for (int32_t i = i0 + threadIdx.x; i < i1; i += SB) bwd_vert(i);
             __syncthreads();
         }
         for (int32_t i = threadIdx.x; i < n; i += SB) {
