@@ -123,6 +123,86 @@ __global__ void k_u8_to_i32(const uint8_t *__restrict__ a, int32_t *b, int64_t n
     if (k < n) b[k] = a[k];
 }
 
+// Small graphs: every Boruvka round in one thread block, the component
+// labels, best weights and best edges in shared memory; the rounds, the
+// strict order and the hooking rule are those above (the forest is the
+// same).  Each round visits every kept edge.  The final labels go to
+// comp_out, as the multi-launch rounds leave them in the tree.
+constexpr int MSF_SMALL_N = 8192;
+__global__ void __launch_bounds__(1024) k_msf_small(const int32_t *__restrict__ ij, const double *__restrict__ w,
+                                                    int64_t m, int32_t n, const int32_t *__restrict__ leaf,
+                                                    uint8_t *intree, int32_t *comp_out, int *rounds_out)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long *bestw = reinterpret_cast<unsigned long long *>(sm);
+    int32_t *comp = reinterpret_cast<int32_t *>(bestw + n);
+    int32_t *beste = comp + n, *hook = beste + n;
+    __shared__ int any;
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) comp[v] = v;
+    int rounds = 0;
+    for (;;) {
+        for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+            bestw[v] = 0ull;
+            beste[v] = INT32_MAX;
+        }
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < m; e += blockDim.x) {
+            const int32_t i = ij[2 * e], j = ij[2 * e + 1];
+            if (leaf && leaf[i] != leaf[j]) continue;
+            const int32_t a = comp[i], b = comp[j];
+            if (a == b) continue;
+            const unsigned long long wb = (unsigned long long)__double_as_longlong(w[e]);
+            atomicMax(bestw + a, wb);
+            atomicMax(bestw + b, wb);
+        }
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < m; e += blockDim.x) {
+            const int32_t i = ij[2 * e], j = ij[2 * e + 1];
+            if (leaf && leaf[i] != leaf[j]) continue;
+            const int32_t a = comp[i], b = comp[j];
+            if (a == b) continue;
+            const unsigned long long wb = (unsigned long long)__double_as_longlong(w[e]);
+            if (wb == bestw[a]) atomicMin(beste + a, (int32_t)e);
+            if (wb == bestw[b]) atomicMin(beste + b, (int32_t)e);
+        }
+        __syncthreads();
+        for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
+            int32_t h = comp[c];
+            if (h == c) {
+                const int32_t e = beste[c];
+                if (e != INT32_MAX) {
+                    const int32_t a = comp[ij[2 * (int64_t)e]], b = comp[ij[2 * (int64_t)e + 1]];
+                    const int32_t d = (a == c) ? b : a;
+                    intree[e] = 1;
+                    any = 1;
+                    const bool mutual = (beste[d] == e);
+                    if (!(mutual && c < d)) h = d;
+                }
+            }
+            hook[c] = h;
+        }
+        __syncthreads();
+        ++rounds;
+        if (!any || rounds > 64) break;
+        for (int32_t v = threadIdx.x; v < n; v += blockDim.x)
+            if (comp[v] == v) comp[v] = hook[v];
+        __syncthreads();
+        for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+            int32_t c = comp[v], cc = comp[c];
+            while (c != cc) {
+                c = cc;
+                cc = comp[c];
+            }
+            comp[v] = c;
+        }
+        __syncthreads();
+    }
+    // the final component labels (the augmentation groups cells by them)
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) comp_out[v] = comp[v];
+    if (threadIdx.x == 0) *rounds_out = rounds;
+}
+
 // Section 6 (partitioned forest): contacts whose two cells share a leaf.
 __global__ void k_leaf_keep(const int32_t *__restrict__ ij, const int32_t *__restrict__ leaf, int64_t m,
                             int32_t *keep)
@@ -176,6 +256,18 @@ sgp_status msf_build(sgp_ctx *ctx, const sgp_matrix *M, const int32_t *leaf, sgp
     const int32_t *ij = bp<const int32_t>(M->ij);
     const double *w = bp<const double>(M->w);
 
+    if (n > 0 && n <= MSF_SMALL_N && m < INT32_MAX) {
+        // one block: every round without a launch or a host read
+        static int done_dev[64] = {0};
+        const size_t smem = (size_t)n * (8 + 4 + 4 + 4);
+        if (ctx->device >= 0 && ctx->device < 64 && !done_dev[ctx->device]) {
+            SGP_CUDA(ctx, cudaFuncSetAttribute(k_msf_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               20 * MSF_SMALL_N));
+            done_dev[ctx->device] = 1;
+        }
+        if (m > 0) SGP_CUDA(ctx, cudaMemsetAsync(intree, 0, (size_t)m, ctx->stream));
+        LAUNCH(ctx, k_msf_small, 1, 1024, smem, ij, w, m, (int32_t)n, leaf, intree, comp, any + 2);
+    } else {
     LAUNCH(ctx, k_init_comp, grid_for(n, SGP_BLOCK), SGP_BLOCK, 0, comp, n);
     if (m > 0) SGP_CUDA(ctx, cudaMemsetAsync(intree, 0, (size_t)m, ctx->stream));
     int64_t nlive = m;
@@ -216,6 +308,7 @@ sgp_status msf_build(sgp_ctx *ctx, const sgp_matrix *M, const int32_t *leaf, sgp
         std::swap(liveA, liveB);
         nlive = h[1];
         if (!h[0]) break;
+    }
     }
     // tree edge ids, ascending
     LAUNCH(ctx, k_u8_to_i32, grid_for(m, SGP_BLOCK), SGP_BLOCK, 0, (const uint8_t *)intree, keep, m);
