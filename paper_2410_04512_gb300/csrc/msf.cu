@@ -128,7 +128,7 @@ __global__ void k_u8_to_i32(const uint8_t *__restrict__ a, int32_t *b, int64_t n
 // strict order and the hooking rule are those above (the forest is the
 // same).  Each round visits every kept edge.  The final labels go to
 // comp_out, as the multi-launch rounds leave them in the tree.
-constexpr int MSF_SMALL_N = 8192;
+constexpr int MSF_SMALL_N = 11264;   // 20 bytes of shared memory per cell: 220 KB
 __global__ void __launch_bounds__(1024) k_msf_small(const int32_t *__restrict__ ij, const double *__restrict__ w,
                                                     int64_t m, int32_t n, const int32_t *__restrict__ leaf,
                                                     uint8_t *intree, int32_t *comp_out, int *rounds_out)
