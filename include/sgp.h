@@ -270,7 +270,12 @@ void sgp_factor_destroy(sgp_factor *factor);
  * H is P^{-1} from `factor` (required for SGP_PRECOND_TREE), the block-Jacobi
  * inverse (computed inside the call) or I.  MIXED runs FP64 iterative
  * refinement: r = F - Gamma v in FP64, an FP32 inner PCG on r/|r| to
- * inner_tol (FP64 dot products), v += |r| d, until |r| <= tol |F|.
+ * inner_tol (FP64 dot products), v += |r| d, until |r| <= tol |F|.  A
+ * MIXED tree-preconditioned solve of a small system (every contraction level
+ * in the factor's one-block tail and its vectors within one block's shared
+ * memory: about a thousand cells) runs the whole refinement in one launch
+ * of one thread block; the results are those of the same algorithm
+ * (dot products summed in FP32 within a warp, in FP64 across warps).
  * F_dev, v_dev: n x 3 float64.  A zero F returns v = 0 after 0 iterations.
  * On NO_CONVERGENCE v holds the last iterate and info is filled.
  * info (host, may be NULL) receives the statistics.  Synchronises. */
