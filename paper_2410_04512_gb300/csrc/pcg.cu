@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(RB) k_fcg_upd(int64_t n3, const double *__rest
 // FP32 records and FP64 blocks for the product, the tail's level solve with
 // FP32 L and D^-1, FP64 accumulators for the dot products.
 // ---------------------------------------------------------------------------
-constexpr int SB = 1024;
+constexpr int SB = 512;
 
 struct SmallOut {
     long long it;
@@ -631,7 +631,7 @@ __device__ __forceinline__ double small_red32(float x, double *shd)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x < 32) {
-        t = shd[threadIdx.x];
+        t = threadIdx.x < SB / 32 ? shd[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     }
@@ -645,7 +645,7 @@ __device__ __forceinline__ double small_red64(double x, double *shd)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x < 32) {
-        t = shd[threadIdx.x];
+        t = threadIdx.x < SB / 32 ? shd[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     }
