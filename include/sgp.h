@@ -195,6 +195,8 @@ void sgp_matrix_destroy(sgp_matrix *matrix);
  * order (weight descending, then edge index ascending); under that order the
  * maximum spanning forest is unique.  A disconnected graph gives a forest
  * (one tree per connected component; isolated cells are single-vertex trees).
+ * Up to 11264 cells every round runs in one thread block (one launch);
+ * beyond, one round of launches at a time.  The forest is the same.
  * Synchronises (the round count is data dependent). */
 sgp_status sgp_max_spanning_tree(sgp_ctx *ctx, const sgp_matrix *matrix, sgp_tree **tree);
 /* Number of tree edges (n - components), the number of components and the
